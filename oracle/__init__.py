@@ -1,0 +1,178 @@
+"""CPU oracle for the fractional Adams-Bashforth-Moulton method -- TEST INFRASTRUCTURE.
+
+A plain, slow FP64 restatement of the predictor-corrector of Section 2 of
+arXiv:1710.01133 (Eq. abm and the corrector/weight formulas that follow it),
+compiled from ``fabm_oracle.c`` with gcc and loaded with ctypes.  Only the tests,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package; the CUDA library never does, and the two share no code.
+
+Right-hand sides are named by string; the oracle keeps its own numbering.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fabm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# name -> (oracle id, dim or None for "any", number of params, default params)
+RHS = {
+    "const": (0, None, 1, (1.0,)),
+    "time": (1, None, 0, ()),
+    "linear": (2, None, 1, (1.0,)),
+    "lorenz": (3, 3, 3, (10.0, 28.0, 8.0 / 3.0)),
+    "duffing": (4, 2, 3, (0.1, 1.2, 1.0)),
+    "manufactured": (5, 1, 2, None),
+    "lcr": (6, 2, 5, (1.015, 0.55, -1.02, -0.58, 0.0)),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (idempotent).  Returns its path."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+        P = ctypes.POINTER
+        lib.fabm_oracle_weights.argtypes = [d, i64, P(d), P(d), P(d)]
+        lib.fabm_oracle_constants.argtypes = [d, d, P(d), P(d)]
+        lib.fabm_oracle_rhs.argtypes = [i, i, d, P(d), P(d), i, P(d)]
+        lib.fabm_oracle_solve.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), i]
+        lib.fabm_oracle_solve_w.argtypes = [i, d, i64, i, P(d), i, P(d), P(d), P(d), d, d,
+                                            P(d), P(d), i]
+        lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d),
+                                                P(ctypes.c_int64), P(d), i, i]
+        for f in ("fabm_oracle_weights", "fabm_oracle_constants", "fabm_oracle_rhs",
+                  "fabm_oracle_solve", "fabm_oracle_solve_w", "fabm_oracle_solve_batch"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def _rhs(name, dim, params):
+    rid, rdim, npar, dflt = RHS[name]
+    if rdim is not None and dim != rdim:
+        raise ValueError(f"rhs {name!r} needs dim {rdim}, got {dim}")
+    if params is None:
+        if dflt is None:
+            raise ValueError(f"rhs {name!r} needs explicit params")
+        params = dflt
+    params = _f64(params).reshape(-1)
+    if params.size < npar:
+        raise ValueError(f"rhs {name!r} needs {npar} params")
+    if params.size == 0:
+        params = np.zeros(1)
+    return rid, params
+
+
+def weights(alpha: float, n: int):
+    """(b, a, c), each of length n: the weights b_j, a_j, c_j, j = 0..n-1."""
+    b, a, c = np.empty(n), np.empty(n), np.empty(n)
+    _check(_load().fabm_oracle_weights(alpha, n, _dp(b), _dp(a), _dp(c)), "weights")
+    return b, a, c
+
+
+def constants(alpha: float, h: float):
+    """(h^alpha, 1/Gamma(alpha+2))."""
+    ha, ig = ctypes.c_double(), ctypes.c_double()
+    _check(_load().fabm_oracle_constants(alpha, h, ctypes.byref(ha), ctypes.byref(ig)),
+           "constants")
+    return ha.value, ig.value
+
+
+def rhs_eval(name: str, t: float, y, params=None):
+    y = _f64(y).reshape(-1)
+    rid, p = _rhs(name, y.size, params)
+    out = np.empty_like(y)
+    _check(_load().fabm_oracle_rhs(rid, y.size, t, _dp(y), _dp(p), p.size, _dp(out)), "rhs")
+    return out
+
+
+def solve(name: str, alpha: float, h: float, N: int, y0, params=None,
+          compensated: bool = True):
+    """One trajectory: returns y_0..y_N as an (N+1, dim) array."""
+    y0 = _f64(y0).reshape(-1)
+    rid, p = _rhs(name, y0.size, params)
+    out = np.empty((N + 1, y0.size))
+    _check(_load().fabm_oracle_solve(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
+                                     _dp(out), int(compensated)), "solve")
+    return out
+
+
+def solve_with_weights(name: str, h: float, N: int, y0, b, a, c, h_alpha: float,
+                       inv_gamma2: float, params=None, compensated: bool = True):
+    """One trajectory with caller-supplied weight vectors (length >= N)."""
+    y0 = _f64(y0).reshape(-1)
+    rid, p = _rhs(name, y0.size, params)
+    b, a, c = _f64(b), _f64(a), _f64(c)
+    if min(b.size, a.size, c.size) < N:
+        raise ValueError("weight vectors shorter than N")
+    out = np.empty((N + 1, y0.size))
+    _check(_load().fabm_oracle_solve_w(y0.size, h, N, rid, _dp(p), p.size, _dp(b), _dp(a),
+                                       _dp(c), h_alpha, inv_gamma2, _dp(y0), _dp(out),
+                                       int(compensated)), "solve_w")
+    return out
+
+
+def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
+                traj_params=None, N_each=None, threads: int | None = None,
+                compensated: bool = True, out=None):
+    """B trajectories: y0 is (B, dim); returns (B, N+1, dim).  Rows of trajectory t
+    past N_each[t] are left as they were in ``out`` (NaN when out is None)."""
+    y0 = _f64(y0)
+    B, dim = y0.shape
+    rid, p = _rhs(name, dim, params)
+    tp = None
+    if traj_params is not None:
+        tp = _f64(traj_params).reshape(B, -1)
+        if tp.shape[1] != p.size:
+            raise ValueError("traj_params rows must have as many entries as params")
+    ne = None
+    if N_each is not None:
+        ne = np.ascontiguousarray(np.asarray(N_each, dtype=np.int64))
+    if out is None:
+        out = np.full((B, N + 1, dim), np.nan)
+    threads = threads or os.cpu_count() or 1
+    _check(_load().fabm_oracle_solve_batch(
+        dim, alpha, h, N, rid, _dp(p), p.size, B, _dp(y0), _dp(tp),
+        None if ne is None else ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(out), int(threads), int(compensated)), "solve_batch")
+    return out

@@ -1,0 +1,370 @@
+/*
+ * fabm_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+ *
+ * Plain, slow, CPU-only restatement of the fractional Adams-Bashforth-Moulton
+ * (ABM) predictor-corrector for Caputo systems D^alpha y = f(t, y), as stated in
+ * Section 2 of Bonchis, Kaslik, Rosu, "HPC optimal parallel communication
+ * algorithm for the simulation of fractional-order systems" (arXiv:1710.01133):
+ *
+ *   grid            t_n = n h, n = 0..N, f_n = f(t_n, y_n)            (Sec. 2)
+ *   predictor       y^P_{n+1} = y_0 + h^a sum_{k=0}^{n} b_{n-k} f_k     (Eq. abm)
+ *   corrector       y_{n+1}   = y_0 + h^a ( c_n f_0
+ *                               + sum_{k=1}^{n} a_{n-k} f_k
+ *                               + f(t_{n+1}, y^P_{n+1}) / Gamma(a+2) )  (Sec. 2)
+ *   weights         b_n = ((n+1)^a - n^a) / Gamma(a+1)                  (Eq. abm)
+ *                   a_n = ((n+2)^{a+1} - 2(n+1)^{a+1} + n^{a+1}) / Gamma(a+2)
+ *                   c_n = (n^{a+1} - (n-a)(n+1)^a) / Gamma(a+2)         (Sec. 2)
+ *   systems         componentwise                                      (Sec. 2)
+ *
+ * Readings of the paper taken here (each is listed with its reason in the
+ * design notes of the repository):
+ *   - b_n is printed with "+" between the two powers; the scheme the paper
+ *     cites (Diethelm's fractional Adams method) has "-", which is also the only
+ *     sign for which the weights telescope to (n+1)^a / Gamma(a+1) and the
+ *     scheme reproduces constant right-hand sides.  "-" is used.
+ *   - 0^p = 0 for p > 0, so b_0 = 1/Gamma(a+1) and c_0 = a/Gamma(a+2).
+ *   - one predictor and one corrector evaluation per step (PECE); f_{n+1} is
+ *     evaluated at the corrected value, as the grid definition says.
+ *   - 0 < a < 1 only, so the Taylor part of both formulas is y_0.
+ *
+ * Precision.  The weights are evaluated from the direct formulas above in
+ * binary128 (_Float128) and rounded once to double: the second difference in
+ * a_n cancels about 2 log2(n) bits, which binary128 absorbs for every n this
+ * code is used with.  Every history sum is a compensated dot product (Dot2 of
+ * Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+ * 26 (2005), Algorithm 5.3), i.e. as accurate as if it were evaluated in twice
+ * the working precision and then rounded.  The sums run in the order the
+ * formulas write them (k ascending); nothing is blocked or reordered.
+ *
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the bench
+ * load this file.  It shares no code with the CUDA library.
+ */
+#define __STDC_WANT_IEC_60559_TYPES_EXT__ 1
+#define _GNU_SOURCE
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef _Float128 q128;
+
+/* Right-hand sides known to the oracle (its own numbering; the Python wrapper
+ * maps names to these). */
+enum {
+    ORC_CONST = 0,        /* f_i = p0                                       */
+    ORC_TIME = 1,         /* f_i = t                                        */
+    ORC_LINEAR = 2,       /* f_i = -p0 * y_i                                */
+    ORC_LORENZ = 3,       /* fractional Lorenz-type system, dim 3           */
+    ORC_DUFFING = 4,      /* forced oscillator with cubic capacitor, dim 2  */
+    ORC_MANUFACTURED = 5, /* f = p0 t^p1 + t^2 - y (solution t^2), dim 1    */
+    ORC_LCR = 6           /* the paper's forced series LCR system (Sec. 5)  */
+};
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
+
+/* ---------------------------------------------------------------- RHS --- */
+
+/* Piecewise-linear characteristic g of the LCR system (Sec. 5). */
+static double orc_lcr_g(double x, double a, double b)
+{
+    if (x <= -1.0) return b * x - a + b;
+    if (x >= 1.0) return b * x + a - b;
+    return a * x;
+}
+
+/* f(t, y) for one state vector; params as documented per right-hand side. */
+static void orc_rhs(int rhs, int dim, double t, const double *y, const double *p, double *out)
+{
+    switch (rhs) {
+    case ORC_CONST:
+        for (int i = 0; i < dim; ++i) out[i] = p[0];
+        break;
+    case ORC_TIME:
+        for (int i = 0; i < dim; ++i) out[i] = t;
+        break;
+    case ORC_LINEAR:
+        for (int i = 0; i < dim; ++i) out[i] = -p[0] * y[i];
+        break;
+    case ORC_LORENZ: /* p = (sigma, rho, beta) */
+        out[0] = p[0] * (y[1] - y[0]);
+        out[1] = y[0] * (p[1] - y[2]) - y[1];
+        out[2] = y[0] * y[1] - p[2] * y[2];
+        break;
+    case ORC_DUFFING: /* p = (damping gamma, forcing frequency omega, amplitude F) */
+        out[0] = y[1];
+        out[1] = -p[0] * y[1] - y[0] - y[0] * y[0] * y[0] + p[2] * cos(p[1] * t);
+        break;
+    case ORC_MANUFACTURED: /* p = (kappa, q): f = kappa t^q + t^2 - y */
+        out[0] = p[0] * pow(t, p[1]) + t * t - y[0];
+        break;
+    case ORC_LCR: /* p = (sigma, omega, a, b, f), Eq. sys.LRC */
+        out[0] = y[1] - orc_lcr_g(y[0], p[2], p[3]);
+        out[1] = -p[0] * y[1] - y[0] + p[4] * sin(p[1] * t);
+        break;
+    default:
+        for (int i = 0; i < dim; ++i) out[i] = NAN;
+    }
+}
+
+static int orc_rhs_dim_ok(int rhs, int dim, int np)
+{
+    switch (rhs) {
+    case ORC_CONST: return dim >= 1 && np >= 1;
+    case ORC_TIME: return dim >= 1;
+    case ORC_LINEAR: return dim >= 1 && np >= 1;
+    case ORC_LORENZ: return dim == 3 && np >= 3;
+    case ORC_DUFFING: return dim == 2 && np >= 3;
+    case ORC_MANUFACTURED: return dim == 1 && np >= 2;
+    case ORC_LCR: return dim == 2 && np >= 5;
+    default: return 0;
+    }
+}
+
+int fabm_oracle_rhs(int rhs, int dim, double t, const double *y, const double *params,
+                    int n_params, double *out)
+{
+    if (!orc_rhs_dim_ok(rhs, dim, n_params)) return ORC_EINVAL;
+    orc_rhs(rhs, dim, t, y, params, out);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------ weights --- */
+
+/* x^p in binary128 with the convention 0^p = 0 for p > 0. */
+static q128 orc_powq(q128 x, q128 p)
+{
+    if (x == 0) return 0;
+    return powf128(x, p);
+}
+
+/* b_j, a_j, c_j for j = 0..n-1 (Sec. 2), each rounded once from binary128.
+ * Uses P[j] = j^alpha and j^{alpha+1} = j * P[j]. */
+int fabm_oracle_weights(double alpha, int64_t n, double *b, double *a, double *c)
+{
+    if (!(alpha > 0.0 && alpha < 1.0) || n < 1) return ORC_EINVAL;
+    q128 *P = (q128 *)malloc((size_t)(n + 2) * sizeof(q128));
+    if (!P) return ORC_ENOMEM;
+    const q128 al = (q128)alpha;
+    for (int64_t j = 0; j < n + 2; ++j) P[j] = orc_powq((q128)j, al);
+    const q128 g1 = tgammaf128(al + 1);
+    const q128 g2 = tgammaf128(al + 2);
+    for (int64_t j = 0; j < n; ++j) {
+        const q128 j0 = (q128)j, j1 = (q128)(j + 1), j2 = (q128)(j + 2);
+        if (b) b[j] = (double)((P[j + 1] - P[j]) / g1);
+        if (a) a[j] = (double)((j2 * P[j + 2] - 2 * (j1 * P[j + 1]) + j0 * P[j]) / g2);
+        if (c) c[j] = (double)((j0 * P[j] - (j0 - al) * P[j + 1]) / g2);
+    }
+    free(P);
+    return ORC_OK;
+}
+
+/* h^alpha, 1/Gamma(alpha+2) rounded once from binary128. */
+int fabm_oracle_constants(double alpha, double h, double *h_alpha, double *inv_gamma2)
+{
+    if (!(alpha > 0.0 && alpha < 1.0) || !(h > 0.0)) return ORC_EINVAL;
+    if (h_alpha) *h_alpha = (double)powf128((q128)h, (q128)alpha);
+    if (inv_gamma2) *inv_gamma2 = (double)(1 / tgammaf128((q128)alpha + 2));
+    return ORC_OK;
+}
+
+/* --------------------------------------------------------------- sums --- */
+
+/* Knuth's TwoSum: s + e == a + b exactly. */
+static inline void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+
+/* sum_{k=k0}^{k1} w[n-k] * f[k*stride], compensated (Dot2, Ogita-Rump-Oishi)
+ * or plain, k ascending. */
+static double orc_hist_dot(const double *w, int64_t n, const double *f, int64_t stride,
+                           int64_t k0, int64_t k1, int compensated)
+{
+    if (k1 < k0) return 0.0;
+    if (!compensated) {
+        double s = 0.0;
+        for (int64_t k = k0; k <= k1; ++k) s += w[n - k] * f[k * stride];
+        return s;
+    }
+    double p = w[n - k0] * f[k0 * stride];
+    double s = fma(w[n - k0], f[k0 * stride], -p);
+    for (int64_t k = k0 + 1; k <= k1; ++k) {
+        double x = w[n - k], y = f[k * stride];
+        double hp = x * y;
+        double r = fma(x, y, -hp);
+        double q;
+        two_sum(p, hp, &p, &q);
+        s += q + r;
+    }
+    return p + s;
+}
+
+/* --------------------------------------------------------------- solve --- */
+
+/* One trajectory with caller-given weights (b, a, c of length >= N) and
+ * constants; out holds (N+1) x dim values, row n = y_n. f_work holds
+ * (N+1) x dim doubles of scratch. */
+static int orc_solve_one(int dim, double h, int64_t N, int rhs, const double *p,
+                         const double *b, const double *a, const double *c, double h_alpha,
+                         double inv_gamma2, const double *y0, double *out, double *fw,
+                         int compensated)
+{
+    double yp[8], fp[8], yc[8];
+    for (int i = 0; i < dim; ++i) out[i] = y0[i];
+    orc_rhs(rhs, dim, 0.0, y0, p, fw);
+    for (int64_t n = 0; n < N; ++n) {
+        const double t1 = (double)(n + 1) * h;
+        /* predictor, Eq. abm */
+        for (int i = 0; i < dim; ++i) {
+            double sp = orc_hist_dot(b, n, fw + i, dim, 0, n, compensated);
+            yp[i] = y0[i] + h_alpha * sp;
+        }
+        orc_rhs(rhs, dim, t1, yp, p, fp);
+        /* corrector */
+        for (int i = 0; i < dim; ++i) {
+            double sc = orc_hist_dot(a, n, fw + i, dim, 1, n, compensated);
+            if (compensated) {
+                double s, e, pr = c[n] * fw[i], pe = fma(c[n], fw[i], -pr);
+                two_sum(pr, sc, &s, &e);
+                sc = s + (e + pe);
+            } else {
+                sc = c[n] * fw[i] + sc;
+            }
+            yc[i] = y0[i] + h_alpha * (sc + fp[i] * inv_gamma2);
+        }
+        for (int i = 0; i < dim; ++i) out[(n + 1) * dim + i] = yc[i];
+        orc_rhs(rhs, dim, t1, yc, p, fw + (n + 1) * dim);
+    }
+    return ORC_OK;
+}
+
+/* Solve with explicit weight vectors (b, a, c each of length >= N). */
+int fabm_oracle_solve_w(int dim, double h, int64_t N, int rhs, const double *params, int n_params,
+                        const double *b, const double *a, const double *c, double h_alpha,
+                        double inv_gamma2, const double *y0, double *out, int compensated)
+{
+    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !orc_rhs_dim_ok(rhs, dim, n_params))
+        return ORC_EINVAL;
+    double *fw = (double *)malloc((size_t)(N + 1) * dim * sizeof(double));
+    if (!fw) return ORC_ENOMEM;
+    int st = orc_solve_one(dim, h, N, rhs, params, b, a, c, h_alpha, inv_gamma2, y0, out, fw,
+                           compensated);
+    free(fw);
+    return st;
+}
+
+int fabm_oracle_solve(int dim, double alpha, double h, int64_t N, int rhs, const double *params,
+                      int n_params, const double *y0, double *out, int compensated)
+{
+    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !(alpha > 0.0 && alpha < 1.0) ||
+        !orc_rhs_dim_ok(rhs, dim, n_params))
+        return ORC_EINVAL;
+    double *w = (double *)malloc((size_t)3 * N * sizeof(double));
+    if (!w) return ORC_ENOMEM;
+    double ha, ig2;
+    int st = fabm_oracle_weights(alpha, N, w, w + N, w + 2 * N);
+    if (st == ORC_OK) st = fabm_oracle_constants(alpha, h, &ha, &ig2);
+    if (st == ORC_OK)
+        st = fabm_oracle_solve_w(dim, h, N, rhs, params, n_params, w, w + N, w + 2 * N, ha, ig2,
+                                 y0, out, compensated);
+    free(w);
+    return st;
+}
+
+/* ------------------------------------------------------------- batches --- */
+
+typedef struct {
+    int dim, rhs, n_params, compensated, tid, nthreads;
+    double h, h_alpha, inv_gamma2;
+    int64_t N, B;
+    const double *params, *traj_params, *y0, *w;
+    const int64_t *N_each;
+    double *out;
+    int status;
+} orc_batch_job;
+
+static void *orc_batch_worker(void *arg)
+{
+    orc_batch_job *j = (orc_batch_job *)arg;
+    double *fw = (double *)malloc((size_t)(j->N + 1) * j->dim * sizeof(double));
+    if (!fw) {
+        j->status = ORC_ENOMEM;
+        return NULL;
+    }
+    for (int64_t t = j->tid; t < j->B; t += j->nthreads) {
+        const int64_t Nt = j->N_each ? j->N_each[t] : j->N;
+        const double *p = j->traj_params ? j->traj_params + t * j->n_params : j->params;
+        orc_solve_one(j->dim, j->h, Nt, j->rhs, p, j->w, j->w + j->N, j->w + 2 * j->N, j->h_alpha,
+                      j->inv_gamma2, j->y0 + t * j->dim, j->out + t * (j->N + 1) * j->dim, fw,
+                      j->compensated);
+    }
+    free(fw);
+    return NULL;
+}
+
+/* B independent trajectories sharing (dim, alpha, h, rhs); trajectory t runs
+ * N_each[t] <= N steps (all N when N_each is NULL) with its own parameter row
+ * traj_params[t*n_params ..] (params for all when NULL).  out is B x (N+1) x
+ * dim; rows past N_each[t] are left untouched.  Trajectories are spread over
+ * n_threads POSIX threads; each trajectory is computed exactly as a single
+ * solve would compute it. */
+int fabm_oracle_solve_batch(int dim, double alpha, double h, int64_t N, int rhs,
+                            const double *params, int n_params, int64_t B, const double *y0,
+                            const double *traj_params, const int64_t *N_each, double *out,
+                            int n_threads, int compensated)
+{
+    if (dim < 1 || dim > 8 || N < 1 || B < 0 || !(h > 0.0) || !(alpha > 0.0 && alpha < 1.0) ||
+        !orc_rhs_dim_ok(rhs, dim, n_params))
+        return ORC_EINVAL;
+    if (N_each)
+        for (int64_t t = 0; t < B; ++t)
+            if (N_each[t] < 1 || N_each[t] > N) return ORC_EINVAL;
+    if (B == 0) return ORC_OK;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > B) n_threads = (int)B;
+    double *w = (double *)malloc((size_t)3 * N * sizeof(double));
+    if (!w) return ORC_ENOMEM;
+    double ha, ig2;
+    int st = fabm_oracle_weights(alpha, N, w, w + N, w + 2 * N);
+    if (st == ORC_OK) st = fabm_oracle_constants(alpha, h, &ha, &ig2);
+    if (st != ORC_OK) {
+        free(w);
+        return st;
+    }
+    orc_batch_job *jobs = (orc_batch_job *)calloc((size_t)n_threads, sizeof(orc_batch_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(w);
+        free(jobs);
+        free(th);
+        return ORC_ENOMEM;
+    }
+    for (int i = 0; i < n_threads; ++i) {
+        orc_batch_job *j = &jobs[i];
+        j->dim = dim, j->rhs = rhs, j->n_params = n_params, j->compensated = compensated;
+        j->tid = i, j->nthreads = n_threads, j->h = h, j->h_alpha = ha, j->inv_gamma2 = ig2;
+        j->N = N, j->B = B, j->params = params, j->traj_params = traj_params, j->y0 = y0;
+        j->w = w, j->N_each = N_each, j->out = out, j->status = ORC_OK;
+    }
+    for (int i = 1; i < n_threads; ++i)
+        if (pthread_create(&th[i], NULL, orc_batch_worker, &jobs[i]) != 0) jobs[i].status = -1;
+    orc_batch_worker(&jobs[0]);
+    for (int i = 1; i < n_threads; ++i) {
+        if (jobs[i].status == -1) { /* thread could not start: run its share here */
+            jobs[i].status = ORC_OK;
+            orc_batch_worker(&jobs[i]);
+        } else {
+            pthread_join(th[i], NULL);
+        }
+    }
+    for (int i = 0; i < n_threads; ++i)
+        if (jobs[i].status != ORC_OK) st = jobs[i].status;
+    free(w);
+    free(jobs);
+    free(th);
+    return st;
+}
