@@ -1,0 +1,160 @@
+/*
+ * fabm.h -- C ABI of the GB300 fractional Adams-Bashforth-Moulton engine.
+ *
+ * The engine solves Caputo systems  D^alpha y = f(t, y),  y(0) = y0,  0 < alpha < 1,
+ * on the uniform grid t_n = n h, n = 0..N, with the predictor-corrector of
+ * Section 2 of Bonchis, Kaslik, Rosu, arXiv:1710.01133 (Eq. abm for the
+ * predictor, the corrector and its weights a_n, c_n right after it).  For each
+ * step n -> n+1 it forms the two hereditary sums over all previous
+ * f_k = f(t_k, y_k),
+ *     S^P_{n+1} = sum_{k=0}^{n} b_{n-k} f_k
+ *     S^C_{n+1} = c_n f_0 + sum_{k=1}^{n} a_{n-k} f_k,
+ * then y^P_{n+1} = y0 + h^alpha S^P_{n+1},
+ *      y_{n+1}   = y0 + h^alpha (S^C_{n+1} + f(t_{n+1}, y^P_{n+1}) / Gamma(alpha+2)).
+ * b_n is taken with a minus sign, ((n+1)^alpha - n^alpha)/Gamma(alpha+1): the
+ * paper prints "+", which does not reproduce constant right-hand sides.
+ * A system is solved componentwise (Sec. 2, last paragraph).
+ *
+ * Conventions for every call:
+ *   - All pointers are plain host pointers unless a parameter says otherwise.
+ *     Host buffers stay owned by the caller; the library copies what it keeps.
+ *   - Device memory (history, weights, work space) is owned by the solver and
+ *     released by fabm_destroy.
+ *   - No call aborts the process.  Every call returns a fabm_status; on failure
+ *     fabm_last_error() gives a message for the calling thread.
+ *   - A solver may be used by one host thread at a time (FABM_EBUSY otherwise).
+ *   - The library runs on the CUDA device that is current when fabm_create is
+ *     called, and keeps using it.
+ */
+#ifndef FABM_H
+#define FABM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fabm_solver fabm_solver;
+
+typedef enum {
+    FABM_OK = 0,
+    FABM_EINVAL = 1,     /* invalid argument (message names it)                     */
+    FABM_ENOMEM = 2,     /* host or device allocation failed                        */
+    FABM_ECUDA = 3,      /* a CUDA call failed (message has the CUDA error)         */
+    FABM_ENONFINITE = 4, /* a solution value became NaN/Inf; message gives
+                            trajectory and step, rows up to that step are valid     */
+    FABM_ETIMEOUT = 5,   /* a bounded device-side wait gave up (status word set)    */
+    FABM_EBUSY = 6       /* solver in use by another thread                         */
+} fabm_status;
+
+/* Arithmetic of the history sums. */
+enum {
+    FABM_FP64 = 0,  /* every step in IEEE double                                   */
+    FABM_SPLIT = 1  /* history sums on tensor cores from a three-term bf16 split of
+                       f and of the weights; the weights, the per-step predictor and
+                       corrector updates and the running history accumulator stay in
+                       double */
+};
+
+/* Right-hand sides f(t, y) (params in this order; dim as stated). */
+enum {
+    FABM_RHS_CONST = 0,        /* f_i = p0                      dim >= 1, 1 param   */
+    FABM_RHS_TIME = 1,         /* f_i = t                       dim >= 1, 0 params  */
+    FABM_RHS_LINEAR = 2,       /* f_i = -p0 y_i                 dim >= 1, 1 param   */
+    FABM_RHS_LORENZ = 3,       /* Lorenz-type: p = (sigma, rho, beta), dim 3
+                                  f = (s(y-x), x(r-z)-y, xy-bz)                      */
+    FABM_RHS_DUFFING = 4,      /* forced oscillator with cubic capacitor, dim 2,
+                                  p = (gamma, omega, F):
+                                  f = (y, -gamma y - x - x^3 + F cos(omega t))       */
+    FABM_RHS_MANUFACTURED = 5, /* f = p0 t^p1 + t^2 - y, dim 1 (solution t^2 when
+                                  p0 = 2/Gamma(3-alpha), p1 = 2-alpha, y0 = 0)       */
+    FABM_RHS_LCR = 6           /* forced series LCR circuit, Sec. 5, Eq. sys.LRC,
+                                  dim 2, p = (sigma, omega, a, b, f):
+                                  f = (y - g(x), -sigma y - x + f sin(omega t)),
+                                  g piecewise linear with slopes a (|x|<1), b       */
+};
+
+#define FABM_MAX_DIM 4
+#define FABM_MAX_PARAMS 8
+
+/* Create a solver for D^alpha y = f(t, y) on t_n = n h, n = 0..N (Sec. 2).
+ *   dim        number of components (must match rhs_id, 1..FABM_MAX_DIM)
+ *   alpha      fractional order, 0 < alpha < 1
+ *   h          step size, h > 0 (T = N h)
+ *   N          number of steps, 1 <= N <= 2^31
+ *   rhs_id     one of FABM_RHS_*
+ *   params     n_params doubles (copied), the rhs parameters
+ *   precision  FABM_FP64 or FABM_SPLIT
+ *   out        receives the solver handle
+ * Computes the weights b, a, c on the device.  Errors: FABM_EINVAL for any
+ * argument out of range, FABM_ENOMEM, FABM_ECUDA. */
+fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
+                        const double *params, int n_params, int precision, fabm_solver **out);
+
+/* Solve one trajectory.  y0: dim doubles.  out: (N+1) x dim doubles, row n = y_n,
+ * row 0 = y0, caller-allocated host memory.  Synchronous. */
+fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out);
+
+/* Solve B independent trajectories that share (dim, alpha, h, rhs).
+ *   y0           B x dim doubles (host)
+ *   traj_params  B x n_params doubles (host) replacing params per trajectory, or NULL
+ *   N_each       B step counts 1 <= N_each[b] <= N (host), or NULL for N
+ *   out          B x (N+1) x dim doubles, trajectory-major; rows past N_each[b]
+ *                are not written.  Host memory, or device memory (allocated by
+ *                the caller on the solver's device) when out_on_device != 0.
+ * Synchronous.  B = 0 is allowed and does nothing. */
+fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
+                             const int64_t *N_each, double *out, int out_on_device);
+
+/* Release the solver and its device memory.  NULL is allowed. */
+fabm_status fabm_destroy(fabm_solver *s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *fabm_last_error(void);
+
+/* Time-block length L (targets per block; a multiple of 32, 32..1024).  Blocks
+ * of L steps are the unit of the history kernels; it changes the order of
+ * summation only.  Default chosen per precision; fabm_autotune picks one. */
+fabm_status fabm_set_block(fabm_solver *s, int L);
+int fabm_get_block(const fabm_solver *s);
+
+/* Copy the first n device weights of the solver to host arrays (n <= N+1):
+ *   B[d] = b_{d-1}, A[d] = a_{d-1} (d >= 1; index 0 holds 0),
+ *   D[m] = c_{m-1} - a_{m-1}       (m >= 1; index 0 holds 0),
+ * the predictor weights of Eq. abm and the corrector weights of Sec. 2 in the
+ * distance form d = (n+1) - k used by the kernels.  Any of B, A, D may be NULL. */
+fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D);
+
+/* Number of kernel launches made by the last solve call on this solver. */
+int64_t fabm_last_launch_count(const fabm_solver *s);
+
+/* Kernel classes for fabm_kernel_stats. */
+enum {
+    FABM_KERNEL_WEIGHTS = 0,     /* weight generation (fabm_create)                    */
+    FABM_KERNEL_INIT = 1,        /* y_0, f_0                                           */
+    FABM_KERNEL_HISTORY = 2,     /* far-history sums (the O(N^2) part)                 */
+    FABM_KERNEL_COMBINE = 3,     /* fixed-order combination of history partial sums    */
+    FABM_KERNEL_RECURRENCE = 4,  /* in-block predictor/corrector steps                 */
+    FABM_KERNEL_KINDS = 5
+};
+
+/* Enable (1) or disable (0) per-launch timing: with timing on, every launch
+ * is bracketed by CUDA events recorded on the stream it runs on, and the
+ * elapsed times are added up when the solve call returns.  Enabling resets
+ * the counters. */
+fabm_status fabm_set_timing(fabm_solver *s, int enable);
+
+/* Counters since timing was enabled, for one kernel class:
+ *   launches  number of launches
+ *   total_ms  sum of their CUDA-event durations
+ *   flops     algorithmic floating-point operations they performed (2 per
+ *             multiply-add of a history term; 0 for classes with no history
+ *             terms).  Any output pointer may be NULL. */
+fabm_status fabm_kernel_stats(const fabm_solver *s, int kind, int64_t *launches, double *total_ms,
+                              double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FABM_H */

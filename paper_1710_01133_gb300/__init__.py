@@ -1,0 +1,233 @@
+"""Python binding of the GB300 fractional Adams-Bashforth-Moulton engine.
+
+Thin ctypes marshalling over ``libfabm.so`` (the C ABI in include/fabm.h):
+the functions below carry the C names and only convert arguments.  Every step
+of a solve runs in the library's CUDA kernels; there is no CPU fallback, and
+``load()`` raises if the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, FABM_EBUSY = range(7)
+FABM_FP64, FABM_SPLIT = 0, 1
+RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
+       "lcr": 6}
+PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
+_EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
+            "fabm_last_error", "fabm_set_block", "fabm_get_block", "fabm_last_launch_count",
+            "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats")
+KERNEL_KINDS = ("weights", "init", "history", "combine", "recurrence")
+
+_lib = None
+
+
+class FabmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fabm status {status}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfabm.so (building it first if needed); raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfabm.so not found at {path}; run paper_1710_01133_gb300.build")
+    lib = ctypes.CDLL(path)
+    d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    P = ctypes.POINTER
+    lib.fabm_create.argtypes = [i, d, d, i64, i, P(d), i, i, P(vp)]
+    lib.fabm_solve.argtypes = [vp, P(d), P(d)]
+    lib.fabm_solve_batch.argtypes = [vp, i64, P(d), P(d), P(i64), vp, i]
+    lib.fabm_destroy.argtypes = [vp]
+    lib.fabm_last_error.argtypes = []
+    lib.fabm_last_error.restype = ctypes.c_char_p
+    lib.fabm_set_block.argtypes = [vp, i]
+    lib.fabm_get_block.argtypes = [vp]
+    lib.fabm_last_launch_count.argtypes = [vp]
+    lib.fabm_last_launch_count.restype = i64
+    lib.fabm_copy_weights.argtypes = [vp, i64, P(d), P(d), P(d)]
+    lib.fabm_set_timing.argtypes = [vp, i]
+    lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
+    for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
+              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats"):
+        getattr(lib, f).restype = i
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(st: int):
+    if st != FABM_OK:
+        raise FabmError(st, fabm_last_error())
+
+
+# ------------------------------------------------------------- C names ---
+
+def fabm_last_error() -> str:
+    return load().fabm_last_error().decode()
+
+
+def fabm_create(dim, alpha, h, N, rhs_id, params, precision=FABM_FP64):
+    p = _f64(params if params is not None else []).reshape(-1)
+    handle = ctypes.c_void_p()
+    _check(load().fabm_create(int(dim), float(alpha), float(h), int(N), int(rhs_id),
+                              _dp(p) if p.size else None, int(p.size), int(precision),
+                              ctypes.byref(handle)))
+    return handle
+
+
+def fabm_solve(handle, y0, out):
+    _check(load().fabm_solve(handle, _dp(y0), _dp(out)))
+
+
+def fabm_solve_batch(handle, B, y0, traj_params, N_each, out_ptr, out_on_device):
+    ne = None
+    if N_each is not None:
+        ne = N_each.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(load().fabm_solve_batch(handle, int(B), _dp(y0), _dp(traj_params), ne,
+                                   ctypes.c_void_p(out_ptr), int(out_on_device)))
+
+
+def fabm_destroy(handle):
+    _check(load().fabm_destroy(handle))
+
+
+def fabm_set_block(handle, L):
+    _check(load().fabm_set_block(handle, int(L)))
+
+
+def fabm_get_block(handle) -> int:
+    return load().fabm_get_block(handle)
+
+
+def fabm_copy_weights(handle, n):
+    """(B, A, D) device weights, n entries each (see include/fabm.h)."""
+    B, A, D = np.empty(n), np.empty(n), np.empty(n)
+    _check(load().fabm_copy_weights(handle, int(n), _dp(B), _dp(A), _dp(D)))
+    return B, A, D
+
+
+def fabm_last_launch_count(handle) -> int:
+    return load().fabm_last_launch_count(handle)
+
+
+def fabm_set_timing(handle, enable: bool):
+    _check(load().fabm_set_timing(handle, int(bool(enable))))
+
+
+def fabm_kernel_stats(handle, kind):
+    """(launches, total_ms, flops) of one kernel class (name or id)."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    n, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(load().fabm_kernel_stats(handle, k, ctypes.byref(n), ctypes.byref(ms),
+                                    ctypes.byref(fl)))
+    return n.value, ms.value, fl.value
+
+
+# ---------------------------------------------------------- convenience ---
+
+class Solver:
+    """Owns one fabm_solver.  ``rhs`` and ``precision`` are names or ids."""
+
+    def __init__(self, rhs, dim, alpha, h, N, params=None, precision="fp64", block=None):
+        self.rhs = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+        self.dim, self.alpha, self.h, self.N = int(dim), float(alpha), float(h), int(N)
+        self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self.params = _f64(params if params is not None else []).reshape(-1)
+        self.handle = fabm_create(dim, alpha, h, N, self.rhs, self.params, self.precision)
+        if block is not None:
+            fabm_set_block(self.handle, block)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            fabm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def block(self) -> int:
+        return fabm_get_block(self.handle)
+
+    @block.setter
+    def block(self, L: int):
+        fabm_set_block(self.handle, L)
+
+    def weights(self, n=None):
+        return fabm_copy_weights(self.handle, self.N + 1 if n is None else n)
+
+    @property
+    def last_launch_count(self) -> int:
+        return fabm_last_launch_count(self.handle)
+
+    def set_timing(self, enable: bool = True):
+        fabm_set_timing(self.handle, enable)
+
+    def kernel_stats(self) -> dict:
+        return {k: dict(zip(("launches", "ms", "flops"), fabm_kernel_stats(self.handle, k)))
+                for k in KERNEL_KINDS}
+
+    def solve(self, y0) -> np.ndarray:
+        y0 = _f64(y0).reshape(-1)
+        if y0.size != self.dim:
+            raise ValueError("y0 must have dim entries")
+        out = np.empty((self.N + 1, self.dim))
+        fabm_solve(self.handle, y0, out)
+        return out
+
+    def solve_batch(self, y0, traj_params=None, N_each=None, out=None):
+        """y0: (B, dim).  out: None (a new host array), a host float64 array of
+        shape (B, N+1, dim), or a CUDA tensor of that shape (written in place on
+        the device).  Returns out."""
+        y0 = _f64(y0).reshape(-1, self.dim)
+        B = y0.shape[0]
+        tp = None if traj_params is None else _f64(traj_params).reshape(B, -1)
+        ne = None if N_each is None else np.ascontiguousarray(np.asarray(N_each, np.int64))
+        if out is None:
+            out = np.full((B, self.N + 1, self.dim), np.nan)
+        on_dev = 0
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != B * (self.N + 1) * self.dim:
+                raise ValueError("out must be a C-contiguous float64 array of shape (B, N+1, dim)")
+            ptr = out.ctypes.data
+        else:  # a torch tensor (host or CUDA)
+            if not out.is_contiguous() or out.numel() != B * (self.N + 1) * self.dim:
+                raise ValueError("out must be contiguous with B*(N+1)*dim elements")
+            if str(out.dtype) != "torch.float64":
+                raise ValueError("out must be float64")
+            ptr = out.data_ptr()
+            on_dev = 1 if out.is_cuda else 0
+        fabm_solve_batch(self.handle, B, y0, tp, ne, ptr, on_dev)
+        return out

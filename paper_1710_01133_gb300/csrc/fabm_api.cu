@@ -1,0 +1,511 @@
+// C ABI (include/fabm.h): solver state, argument checks, device memory, and
+// the block-by-block schedule of the kernels.
+//
+// Schedule of one solve (Sec. 2 of arXiv:1710.01133 evaluated block by block):
+//   init                      y_0, f_0
+//   for each block c of L targets:
+//     stream G:  wait R(c-2); history(c) over k < (c-1)L; combine -> G[c%2]
+//     stream R:  wait G(c);   recurrence(c)
+// The history of block c+1 therefore runs while the recurrence of block c
+// runs; the recurrence adds the lag-1 block itself.  This replaces the
+// per-step MPI_Allreduce of the paper's Algorithm 1 by one hand-off per block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fabm_internal.cuh"
+#include "rhs.cuh"
+
+using namespace fabm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fabm_status fail(fabm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define FABM_CUDA_TRY(expr)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? FABM_ENOMEM : FABM_ECUDA,          \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,    \
+                        __LINE__);                                                           \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= n) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            return e;
+        }
+        n = want;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+constexpr int kMaxBlockL = 1024;
+constexpr int kEvRing = 4;
+
+}  // namespace
+
+struct fabm_solver {
+    int device = 0;
+    int dim = 0;
+    double alpha = 0, h = 0;
+    int64_t N = 0;
+    int rhs = 0;
+    int n_params = 0;
+    double params[kMaxParams] = {};
+    int precision = FABM_FP64;
+    int L = kRecurL;
+    StepConsts k{};
+    int64_t w_ext = 0;  // weights valid for index 0..w_ext
+    DevBuf<double> wB, wA, wD;
+    // per-batch workspace
+    DevBuf<double> F, Ystage, G, part, y0, par;
+    DevBuf<int64_t> nEach;
+    DevBuf<unsigned long long> status;
+    cudaStream_t sR = nullptr, sG = nullptr;
+    cudaEvent_t evR[kEvRing] = {}, evG[2] = {};
+    std::mutex busy;
+    int64_t launches = 0;
+    // per-launch timing (fabm_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
+    std::vector<int> ev_kind;          // kind of each used pair
+    int64_t k_launches[FABM_KERNEL_KINDS] = {};
+    double k_ms[FABM_KERNEL_KINDS] = {};
+    double k_flops[FABM_KERNEL_KINDS] = {};
+
+    ~fabm_solver()
+    {
+        wB.release(), wA.release(), wD.release();
+        F.release(), Ystage.release(), G.release(), part.release();
+        y0.release(), par.release(), nEach.release(), status.release();
+        for (auto &e : evR)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : evG)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : ev_pool) cudaEventDestroy(e);
+        if (sR) cudaStreamDestroy(sR);
+        if (sG) cudaStreamDestroy(sG);
+    }
+};
+
+namespace {
+
+// Chunking of the far history of block c over the points k < (c-1)L.
+void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int *n_chunks, int64_t *kc)
+{
+    const int col_tiles = (cols + 3) / 4;
+    const int64_t want_ctas = 152 * 12;
+    int64_t n = (want_ctas + col_tiles - 1) / col_tiles;
+    const int64_t min_kc = 64;
+    n = std::min<int64_t>(n, (k_end + min_kc - 1) / min_kc);
+    n = std::min<int64_t>(n, max_chunks);
+    n = std::max<int64_t>(n, 1);
+    int64_t c = (k_end + n - 1) / n;
+    c = (c + 31) / 32 * 32;
+    *kc = c;
+    *n_chunks = (int)((k_end + c - 1) / c);
+}
+
+fabm_status check_rhs(int rhs, int dim, int n_params)
+{
+    const int np = rhs_n_params(rhs);
+    if (np < 0) return fail(FABM_EINVAL, "unknown rhs_id %d", rhs);
+    if (!rhs_supports_dim(rhs, dim)) return fail(FABM_EINVAL, "rhs_id %d does not support dim %d", rhs, dim);
+    if (n_params < np || n_params > kMaxParams)
+        return fail(FABM_EINVAL, "rhs_id %d needs %d params (got %d, max %d)", rhs, np, n_params,
+                    kMaxParams);
+    return FABM_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Runs launch() on stream st; counts it, and with timing on brackets it with a
+// pair of CUDA events on st.
+template <class Fn>
+cudaError_t timed_launch(fabm_solver *s, int kind, cudaStream_t st, double flops, Fn &&launch)
+{
+    ++s->launches;
+    if (!s->timing) return launch();
+    const size_t pair = s->ev_kind.size();
+    while (s->ev_pool.size() < 2 * (pair + 1)) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        s->ev_pool.push_back(e);
+    }
+    cudaError_t err = cudaEventRecord(s->ev_pool[2 * pair], st);
+    if (err != cudaSuccess) return err;
+    err = launch();
+    if (err != cudaSuccess) return err;
+    err = cudaEventRecord(s->ev_pool[2 * pair + 1], st);
+    if (err != cudaSuccess) return err;
+    s->ev_kind.push_back(kind);
+    s->k_launches[kind] += 1;
+    s->k_flops[kind] += flops;
+    return cudaSuccess;
+}
+
+// After the streams are idle: add up the recorded event pairs.
+cudaError_t collect_timing(fabm_solver *s)
+{
+    for (size_t i = 0; i < s->ev_kind.size(); ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
+        if (e != cudaSuccess) return e;
+        s->k_ms[s->ev_kind[i]] += ms;
+    }
+    s->ev_kind.clear();
+    return cudaSuccess;
+}
+
+fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
+                      const int64_t *N_each, double *out, int out_on_device)
+{
+    const int dim = s->dim;
+    const int64_t cols = B * dim;
+    const int64_t N = s->N;
+    const int L = s->L;
+    s->launches = 0;
+    s->ev_kind.clear();
+
+    // host-side inputs: per-trajectory steps and parameter rows
+    std::vector<int64_t> ne(B);
+    int64_t Nmax = 0;
+    bool all_full = true;
+    for (int64_t b = 0; b < B; ++b) {
+        ne[b] = N_each ? N_each[b] : N;
+        if (ne[b] < 1 || ne[b] > N)
+            return fail(FABM_EINVAL, "N_each[%lld] = %lld outside 1..N=%lld", (long long)b,
+                        (long long)ne[b], (long long)N);
+        Nmax = std::max(Nmax, ne[b]);
+        all_full = all_full && ne[b] == N;
+    }
+    std::vector<double> par((size_t)B * kMaxParams, 0.0);
+    for (int64_t b = 0; b < B; ++b)
+        for (int i = 0; i < s->n_params; ++i)
+            par[b * kMaxParams + i] = traj_params ? traj_params[b * s->n_params + i] : s->params[i];
+    for (int64_t i = 0; i < B * dim; ++i)
+        if (!std::isfinite(y0[i])) return fail(FABM_EINVAL, "y0[%lld] is not finite", (long long)i);
+
+    // workspace
+    const int64_t nblk = (Nmax + L - 1) / L;
+    const size_t f_elems = (size_t)(N + 1) * cols;
+    const int64_t part_per_chunk = 2LL * L * cols;
+    int64_t max_chunks = std::max<int64_t>(1, (int64_t)(64ull << 20) / (part_per_chunk * 8));
+    max_chunks = std::min<int64_t>(max_chunks, 4096);
+    FABM_CUDA_TRY(s->F.ensure(f_elems));
+    FABM_CUDA_TRY(s->G.ensure((size_t)2 * 2 * L * cols));
+    FABM_CUDA_TRY(s->part.ensure((size_t)max_chunks * part_per_chunk));
+    FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim));
+    FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
+    FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
+    FABM_CUDA_TRY(s->status.ensure(1));
+    double *Y = out;
+    if (!out_on_device) {
+        FABM_CUDA_TRY(s->Ystage.ensure((size_t)B * (N + 1) * dim));
+        Y = s->Ystage.p;
+    }
+    FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p, y0, sizeof(double) * B * dim, cudaMemcpyHostToDevice, s->sR));
+    FABM_CUDA_TRY(cudaMemcpyAsync(s->par.p, par.data(), sizeof(double) * par.size(),
+                                  cudaMemcpyHostToDevice, s->sR));
+    FABM_CUDA_TRY(cudaMemcpyAsync(s->nEach.p, ne.data(), sizeof(int64_t) * B,
+                                  cudaMemcpyHostToDevice, s->sR));
+    FABM_CUDA_TRY(cudaMemsetAsync(s->status.p, 0xff, sizeof(unsigned long long), s->sR));
+
+    DevBatch bt{};
+    bt.dim = dim;
+    bt.B = (int)B;
+    bt.cols = (int)cols;
+    bt.N = N;
+    bt.N_each = s->nEach.p;
+    bt.y0 = s->y0.p;
+    bt.params = s->par.p;
+    bt.F = s->F.p;
+    bt.ldF = cols;
+    bt.Y = Y;
+    bt.status = s->status.p;
+    DevWeights w{s->wB.p, s->wA.p, s->wD.p, s->w_ext};
+
+    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
+                               [&] { return launch_init(s->rhs, bt, s->sR); }));
+    for (int64_t c = 0; c < nblk; ++c) {
+        const double *Gc = nullptr;
+        if (c >= 2) {
+            double *Gbuf = s->G.p + (size_t)(c % 2) * 2 * L * cols;
+            int n_chunks;
+            int64_t kc;
+            const int64_t k_end = (c - 1) * L;
+            plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
+            // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
+            const double flops = 4.0 * L * (double)k_end * (double)cols;
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                return launch_hist_fp64(bt, w, c, L, n_chunks, kc, s->part.p, s->sG);
+            }));
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
+                return launch_hist_reduce(s->part.p, n_chunks, L, (int)cols, Gbuf, s->sG);
+            }));
+            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 2], s->sG));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 2], 0));
+            Gc = Gbuf;
+        }
+        // lag-1 block and in-block triangle: per target up to 2L points
+        const int64_t lo = c * L, hi = std::min<int64_t>((c + 1) * L, Nmax);
+        const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
+                              ((c >= 1 ? L : 0) + 0.5 * (double)(hi - lo + 1));
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
+            return launch_recur_fp64(s->rhs, bt, w, s->k, c, Gc, s->sR);
+        }));
+        FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
+    }
+    FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
+    FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
+    FABM_CUDA_TRY(collect_timing(s));
+
+    unsigned long long st = 0;
+    FABM_CUDA_TRY(cudaMemcpy(&st, s->status.p, sizeof st, cudaMemcpyDeviceToHost));
+
+    if (!out_on_device) {
+        const size_t row = (size_t)(N + 1) * dim;
+        if (all_full) {
+            FABM_CUDA_TRY(cudaMemcpy(out, Y, sizeof(double) * row * B, cudaMemcpyDeviceToHost));
+        } else {
+            // copy only the rows each trajectory owns; runs of full-length
+            // trajectories go in one copy
+            int64_t b = 0;
+            while (b < B) {
+                if (ne[b] == N) {
+                    int64_t e = b;
+                    while (e < B && ne[e] == N) ++e;
+                    FABM_CUDA_TRY(cudaMemcpy(out + b * row, Y + b * row,
+                                             sizeof(double) * row * (e - b),
+                                             cudaMemcpyDeviceToHost));
+                    b = e;
+                } else {
+                    FABM_CUDA_TRY(cudaMemcpy(out + b * row, Y + b * row,
+                                             sizeof(double) * (ne[b] + 1) * dim,
+                                             cudaMemcpyDeviceToHost));
+                    ++b;
+                }
+            }
+        }
+    }
+    if (st != ~0ull)
+        return fail(FABM_ENONFINITE, "non-finite value at trajectory %llu, step %llu",
+                    st & 0xffffffull, st >> 24);
+    return FABM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fabm_last_error(void) { return g_last_error.c_str(); }
+
+fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
+                        const double *params, int n_params, int precision, fabm_solver **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(FABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dim < 1 || dim > FABM_MAX_DIM) return fail(FABM_EINVAL, "dim %d outside 1..%d", dim, FABM_MAX_DIM);
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(FABM_EINVAL, "alpha %g outside (0, 1)", alpha);
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(FABM_EINVAL, "h %g must be positive", h);
+    if (N < 1 || N > (1LL << 31)) return fail(FABM_EINVAL, "N %lld outside 1..2^31", (long long)N);
+    if (precision != FABM_FP64)
+        return fail(FABM_EINVAL, "precision %d not available in this build", precision);
+    fabm_status st = check_rhs(rhs_id, dim, n_params);
+    if (st != FABM_OK) return st;
+    if (n_params > 0 && !params) return fail(FABM_EINVAL, "params is NULL");
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return fail(FABM_EINVAL, "params[%d] is not finite", i);
+
+    fabm_solver *s = new (std::nothrow) fabm_solver();
+    if (!s) return fail(FABM_ENOMEM, "host allocation failed");
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return fail(FABM_ECUDA, "no CUDA device");
+    }
+    s->dim = dim, s->alpha = alpha, s->h = h, s->N = N, s->rhs = rhs_id;
+    s->n_params = n_params, s->precision = precision;
+    for (int i = 0; i < n_params; ++i) s->params[i] = params[i];
+    s->k.h = h;
+    s->k.h_alpha = std::pow(h, alpha);
+    s->k.inv_gamma2 = 1.0 / std::tgamma(alpha + 2.0);
+    const double inv_g1 = 1.0 / std::tgamma(alpha + 1.0);
+
+    auto cleanup = [&](fabm_status e) {
+        delete s;
+        return e;
+    };
+    // weights for every distance a history kernel can ask for: block padding
+    // beyond N plus the lag-1 window
+    s->w_ext = (N + kMaxBlockL - 1) / kMaxBlockL * kMaxBlockL + 2 * kMaxBlockL;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = s->wB.ensure(s->w_ext + 1);
+    if (e == cudaSuccess) e = s->wA.ensure(s->w_ext + 1);
+    if (e == cudaSuccess) e = s->wD.ensure(s->w_ext + 1);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sR, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG, cudaStreamNonBlocking);
+    for (auto &ev : s->evR)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (auto &ev : s->evG)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        s->timing = true;  // the weight launch is always timed
+        e = timed_launch(s, FABM_KERNEL_WEIGHTS, s->sR, 0.0, [&] {
+            return launch_weights(alpha, s->w_ext, inv_g1, s->k.inv_gamma2, s->wB.p, s->wA.p,
+                                  s->wD.p, s->sR);
+        });
+        s->timing = false;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->sR);
+    if (e == cudaSuccess) e = collect_timing(s);
+    if (e != cudaSuccess)
+        return cleanup(fail(e == cudaErrorMemoryAllocation ? FABM_ENOMEM : FABM_ECUDA,
+                            "fabm_create: %s", cudaGetErrorString(e)));
+    *out = s;
+    return FABM_OK;
+}
+
+fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
+                             const int64_t *N_each, double *out, int out_on_device)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (B < 0 || B > (1LL << 24)) return fail(FABM_EINVAL, "B %lld outside 0..2^24", (long long)B);
+    if (B == 0) return FABM_OK;
+    if (!y0 || !out) return fail(FABM_EINVAL, "y0 and out must not be NULL");
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    if (traj_params)
+        for (int64_t i = 0; i < B * s->n_params; ++i)
+            if (!std::isfinite(traj_params[i]))
+                return fail(FABM_EINVAL, "traj_params[%lld] is not finite", (long long)i);
+    DeviceGuard g(s->device);
+    return run_batch(s, B, y0, traj_params, N_each, out, out_on_device);
+}
+
+fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out)
+{
+    return fabm_solve_batch(s, 1, y0, nullptr, nullptr, out, 0);
+}
+
+fabm_status fabm_destroy(fabm_solver *s)
+{
+    g_last_error.clear();
+    if (!s) return FABM_OK;
+    {
+        std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+        if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    }
+    DeviceGuard g(s->device);
+    delete s;
+    return FABM_OK;
+}
+
+fabm_status fabm_set_block(fabm_solver *s, int L)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (L % 32 != 0 || L < 32 || L > kMaxBlockL)
+        return fail(FABM_EINVAL, "block length %d must be a multiple of 32 in 32..%d", L, kMaxBlockL);
+    if (s->precision == FABM_FP64 && L != kRecurL)
+        return fail(FABM_EINVAL, "the FP64 path uses blocks of %d targets", kRecurL);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->L = L;
+    return FABM_OK;
+}
+
+int fabm_get_block(const fabm_solver *s) { return s ? s->L : 0; }
+
+fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (n < 0 || n > s->N + 1) return fail(FABM_EINVAL, "n %lld outside 0..N+1", (long long)n);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    DeviceGuard g(s->device);
+    if (B) FABM_CUDA_TRY(cudaMemcpy(B, s->wB.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (A) FABM_CUDA_TRY(cudaMemcpy(A, s->wA.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (D) FABM_CUDA_TRY(cudaMemcpy(D, s->wD.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return FABM_OK;
+}
+
+int64_t fabm_last_launch_count(const fabm_solver *s) { return s ? s->launches : 0; }
+
+fabm_status fabm_set_timing(fabm_solver *s, int enable)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->timing = enable != 0;
+    if (s->timing)
+        for (int k = 0; k < FABM_KERNEL_KINDS; ++k)
+            if (k != FABM_KERNEL_WEIGHTS) s->k_launches[k] = 0, s->k_ms[k] = 0, s->k_flops[k] = 0;
+    return FABM_OK;
+}
+
+fabm_status fabm_kernel_stats(const fabm_solver *s, int kind, int64_t *launches, double *total_ms,
+                              double *flops)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (kind < 0 || kind >= FABM_KERNEL_KINDS) return fail(FABM_EINVAL, "kind %d unknown", kind);
+    if (launches) *launches = s->k_launches[kind];
+    if (total_ms) *total_ms = s->k_ms[kind];
+    if (flops) *flops = s->k_flops[kind];
+    return FABM_OK;
+}
+
+}  // extern "C"

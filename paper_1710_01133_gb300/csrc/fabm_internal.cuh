@@ -1,0 +1,82 @@
+// Internal interfaces of the fractional ABM engine (not part of the C ABI).
+//
+// Index conventions used throughout the CUDA sources.  For the step that
+// produces y_m (target m = n+1 in the paper's notation) and a past point k the
+// distance is d = m - k >= 1, and the weights of Sec. 2 become
+//   B(d) = b_{d-1} = (d^a - (d-1)^a) / Gamma(a+1)                     predictor
+//   A(d) = a_{d-1} = ((d+1)^{a+1} - 2 d^{a+1} + (d-1)^{a+1}) / Gamma(a+2)  corrector
+//   C(m-1) = c_{m-1}                                        corrector, k = 0 term
+// so that  S^P_m = sum_{k<m} B(m-k) f_k  and
+//          S^C_m = sum_{k<m} A(m-k) f_k + (C(m-1) - A(m)) f_0.
+// The last form lets every history kernel treat k = 0 like any other point;
+// the recurrence adds the correction D(m) = C(m-1) - A(m) times f_0.
+//
+// Time is cut into blocks of L targets: block c holds m = cL+1 .. cL+L.  The
+// history kernels sum the "far" part (k < (c-1)L) of every block while the
+// recurrence kernel of the previous block runs; the recurrence adds the lag-1
+// block and the block's own triangle, step by step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fabm.h"
+
+namespace fabm {
+
+constexpr int kWarp = 32;
+constexpr int kRecurL = 32;        // targets per block in the recurrence kernels
+constexpr int kMaxParams = FABM_MAX_PARAMS;
+
+// Weight vectors on the device, index 0..N.  B[0] = A[0] = D[0] = 0.
+struct DevWeights {
+    const double *B;
+    const double *A;
+    const double *D;   // D[m] = C(m-1) - A(m)
+    int64_t N;
+};
+
+// One batch of B trajectories of one solver, as the kernels see it.
+struct DevBatch {
+    int dim;
+    int B;                 // trajectories
+    int cols;              // B * dim; column of (b, i) is b*dim + i
+    int64_t N;             // steps of the longest trajectory
+    const int64_t *N_each; // per-trajectory steps (device)
+    const double *y0;      // B x dim
+    const double *params;  // B x kMaxParams
+    double *F;             // history f_k, (N+1) x ldF, row k = time k
+    int64_t ldF;           // row stride of F (>= cols)
+    double *Y;             // output, B x (N+1) x dim (trajectory-major)
+    unsigned long long *status;  // [0] = first non-finite (step << 24 | traj), ~0 if none
+};
+
+struct StepConsts {
+    double h;
+    double h_alpha;     // h^alpha
+    double inv_gamma2;  // 1/Gamma(alpha+2)
+};
+
+// a1: weights B(d), A(d), D(m) for d, m = 0..N.
+cudaError_t launch_weights(double alpha, int64_t N, double inv_g1, double inv_g2, double *B,
+                           double *A, double *D, cudaStream_t st);
+
+// y_0 into Y, f_0 = f(0, y_0) into F row 0.
+cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st);
+
+// a2 (FP64): partial far-history sums of target block c from the points
+// k in [0, (c-1)L), split into n_chunks chunks of kc points.
+// part: n_chunks x 2 x L x cols (P then C).
+cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L,
+                             int n_chunks, int64_t kc, double *part, cudaStream_t st);
+
+// a3: G[pc][a][col] = sum over chunks of part (fixed order).
+cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols, double *G,
+                               cudaStream_t st);
+
+// a4 + a5 (FP64): steps of block c for every trajectory; G holds the far
+// history of block c (2 x L x cols) or is NULL when c < 2.
+cudaError_t launch_recur_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
+                              const StepConsts &k, int64_t c, const double *G, cudaStream_t st);
+
+}  // namespace fabm

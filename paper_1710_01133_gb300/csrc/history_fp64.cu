@@ -1,0 +1,134 @@
+// a2 + a3 in double: the far part of the hereditary sums of Sec. 2 of
+// arXiv:1710.01133 (the k-loop of Algorithm 1, which is all of the O(N^2)
+// work), for one block of L targets, split over the points k in chunks.
+//
+// For target block c (targets m = cL+1+a, a < L) and the points k < (c-1)L:
+//   GP[a][col] = sum_k B(m-k) F[k][col],   GC[a][col] = sum_k A(m-k) F[k][col].
+// The weights depend on m-k only (Toeplitz), so a chunk of kc points needs
+// kc+L-1 consecutive weights, staged in shared memory with the chunk of F.
+//
+// GB300 executes a double-precision FMA for a whole warp in one 64-cycle slot
+// of a sub-partition's FP64 unit, whatever the number of active lanes, so this
+// kernel is bound by that unit: it keeps every issued DFMA busy on 32 lanes
+// (lane = target, warp = column) and gives each sub-partition at least one
+// warp.  The chunks are summed afterwards in a fixed order (a3), so results do
+// not depend on scheduling.
+#include "fabm_internal.cuh"
+
+namespace fabm {
+namespace {
+
+constexpr int kColsPerCta = 4;  // one warp per column
+constexpr int kTile = 256;      // points staged in shared memory at a time
+constexpr int kL = kRecurL;     // targets per block (one per lane)
+
+// grid = (n_chunks, ceil(cols / kColsPerCta)); block = 32 * kColsPerCta.
+// Chunk ch covers the points k in [ch*kc, min((ch+1)*kc, k_end)).
+__global__ void __launch_bounds__(kWarp *kColsPerCta)
+    hist_fp64_kernel(const double *__restrict__ F, int64_t ldF, int cols,
+                     const double *__restrict__ WB, const double *__restrict__ WA, int64_t c,
+                     int64_t kc, int64_t k_end, double *__restrict__ part)
+{
+    __shared__ double sF[kTile * kColsPerCta];
+    __shared__ double sB[kTile + kL], sA[kTile + kL];
+    const int64_t chunk = blockIdx.x;
+    const int64_t k0 = chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
+    const int col0 = blockIdx.y * kColsPerCta;
+    const int ncol = min(kColsPerCta, cols - col0);
+    const int w = threadIdx.x / kWarp;
+    const int a = threadIdx.x % kWarp;  // target m = cL+1+a
+    double sp = 0.0, sc = 0.0;
+
+    for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
+        const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
+        const int nk = (int)(t1 - t0);
+        // weights for d = m - k, m in [cL+1, cL+L], k in [t0, t1):
+        // window index i <-> d = cL+2-t1 + i, i < nk+L-1
+        const int64_t d_min = c * kL + 2 - t1;
+        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
+            sB[i] = WB[d_min + i];
+            sA[i] = WA[d_min + i];
+        }
+        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
+            const int k = i / kColsPerCta, j = i % kColsPerCta;
+            sF[i] = j < ncol ? F[(t0 + k) * ldF + col0 + j] : 0.0;
+        }
+        __syncthreads();
+        if (w < ncol) {
+            // d - d_min = (cL+1+a - (t0+j)) - (cL+2-t1) = a + nk-1-j
+            const double *fb = sF + w;
+            const int base = a + nk - 1;
+#pragma unroll 4
+            for (int j = 0; j < nk; ++j) {
+                const double f = fb[j * kColsPerCta];
+                sp = fma(sB[base - j], f, sp);
+                sc = fma(sA[base - j], f, sc);
+            }
+        }
+        __syncthreads();
+    }
+    if (w < ncol) {
+        double *out = part + ((chunk * 2) * kL + a) * (int64_t)cols + col0 + w;
+        out[0] = sp;
+        out[(int64_t)kL * cols] = sc;
+    }
+}
+
+// a3: G[pc][a][col] = sum_{chunk} part[chunk][pc][a][col], chunk ascending
+// within each lane's strided subset, then a fixed xor tree over the R lanes of
+// a group.  grid-stride over the 2*L*cols outputs.
+template <int R>
+__global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks, int64_t n_out,
+                                   double *__restrict__ G)
+{
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = (int)(gtid % R);
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / R;
+    // every thread runs the same number of rounds, so the shuffles below
+    // always see full warps
+    for (int64_t base = 0; base < n_out; base += groups) {
+        const int64_t o = base + gtid / R;
+        double s = 0.0;
+        if (o < n_out)
+            for (int ch = r; ch < n_chunks; ch += R) s += part[(int64_t)ch * n_out + o];
+#pragma unroll
+        for (int off = R / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (r == 0 && o < n_out) G[o] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L,
+                             int n_chunks, int64_t kc, double *part, cudaStream_t st)
+{
+    const int64_t k_end = (c - 1) * L;
+    if (L != kL) return cudaErrorInvalidValue;
+    if (c < 2 || k_end <= 0) return cudaSuccess;
+    dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + kColsPerCta - 1) / kColsPerCta));
+    hist_fp64_kernel<<<grid, kWarp * kColsPerCta, 0, st>>>(bt.F, bt.ldF, bt.cols, w.B, w.A, c,
+                                                          kc, k_end, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols, double *G,
+                               cudaStream_t st)
+{
+    const int64_t n_out = 2LL * L * cols;
+    const int threads = 256;
+    auto blocks_for = [&](int R) {
+        int64_t b = (n_out * R + threads - 1) / threads;
+        return (unsigned)(b > 152 * 16 ? 152 * 16 : b);
+    };
+    if (n_chunks >= 256) {
+        hist_reduce_kernel<32><<<blocks_for(32), threads, 0, st>>>(part, n_chunks, n_out, G);
+    } else if (n_chunks >= 32) {
+        hist_reduce_kernel<8><<<blocks_for(8), threads, 0, st>>>(part, n_chunks, n_out, G);
+    } else {
+        hist_reduce_kernel<1><<<blocks_for(1), threads, 0, st>>>(part, n_chunks, n_out, G);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fabm

@@ -1,0 +1,153 @@
+// a5: right-hand sides f(t, y) of the FDE D^a y = f(t, y) (Sec. 2, Eq. fde),
+// as device functors.  Each has the dimension and parameter layout documented
+// for FABM_RHS_* in fabm.h.  All arithmetic is double.
+#pragma once
+
+#include "fabm_internal.cuh"
+
+namespace fabm {
+
+struct RhsConst {  // f_i = p0
+    template <int D>
+    __device__ static void eval(double, const double *, const double *p, double *f)
+    {
+#pragma unroll
+        for (int i = 0; i < D; ++i) f[i] = p[0];
+    }
+};
+
+struct RhsTime {  // f_i = t
+    template <int D>
+    __device__ static void eval(double t, const double *, const double *, double *f)
+    {
+#pragma unroll
+        for (int i = 0; i < D; ++i) f[i] = t;
+    }
+};
+
+struct RhsLinear {  // f_i = -p0 y_i
+    template <int D>
+    __device__ static void eval(double, const double *y, const double *p, double *f)
+    {
+#pragma unroll
+        for (int i = 0; i < D; ++i) f[i] = -p[0] * y[i];
+    }
+};
+
+struct RhsLorenz {  // p = (sigma, rho, beta)
+    template <int D>
+    __device__ static void eval(double, const double *y, const double *p, double *f)
+    {
+        f[0] = p[0] * (y[1] - y[0]);
+        f[1] = y[0] * (p[1] - y[2]) - y[1];
+        f[2] = y[0] * y[1] - p[2] * y[2];
+    }
+};
+
+struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 + F cos(omega t)
+    template <int D>
+    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    {
+        const double x = y[0];
+        f[0] = y[1];
+        f[1] = p[2] * cos(p[1] * t) - (p[0] * y[1] + x * (1.0 + x * x));
+    }
+};
+
+struct RhsManufactured {  // f = p0 t^p1 + t^2 - y
+    template <int D>
+    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    {
+        f[0] = p[0] * pow(t, p[1]) + (t * t - y[0]);
+    }
+};
+
+struct RhsLcr {  // Sec. 5, Eq. sys.LRC; p = (sigma, omega, a, b, f)
+    template <int D>
+    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    {
+        const double x = y[0], a = p[2], b = p[3];
+        double g;
+        if (x <= -1.0)
+            g = b * x - a + b;
+        else if (x >= 1.0)
+            g = b * x + a - b;
+        else
+            g = a * x;
+        f[0] = y[1] - g;
+        f[1] = p[4] * sin(p[1] * t) - (p[0] * y[1] + x);
+    }
+};
+
+// Calls fn.template operator()<Rhs, D>() for the (rhs, dim) pair; returns false
+// if the pair is not supported.
+template <class Fn>
+bool dispatch_rhs(int rhs, int dim, Fn &&fn)
+{
+    switch (rhs) {
+    case FABM_RHS_CONST:
+    case FABM_RHS_TIME:
+    case FABM_RHS_LINEAR:
+        switch (dim) {
+#define FABM_CASE_D(D)                                                                      \
+    case D:                                                                                 \
+        if (rhs == FABM_RHS_CONST) fn.template operator()<RhsConst, D>();                   \
+        else if (rhs == FABM_RHS_TIME) fn.template operator()<RhsTime, D>();                \
+        else fn.template operator()<RhsLinear, D>();                                        \
+        return true;
+            FABM_CASE_D(1)
+            FABM_CASE_D(2)
+            FABM_CASE_D(3)
+            FABM_CASE_D(4)
+#undef FABM_CASE_D
+        default: return false;
+        }
+    case FABM_RHS_LORENZ:
+        if (dim != 3) return false;
+        fn.template operator()<RhsLorenz, 3>();
+        return true;
+    case FABM_RHS_DUFFING:
+        if (dim != 2) return false;
+        fn.template operator()<RhsDuffing, 2>();
+        return true;
+    case FABM_RHS_MANUFACTURED:
+        if (dim != 1) return false;
+        fn.template operator()<RhsManufactured, 1>();
+        return true;
+    case FABM_RHS_LCR:
+        if (dim != 2) return false;
+        fn.template operator()<RhsLcr, 2>();
+        return true;
+    default: return false;
+    }
+}
+
+inline bool rhs_supports_dim(int rhs, int dim)
+{
+    switch (rhs) {
+    case FABM_RHS_CONST:
+    case FABM_RHS_TIME:
+    case FABM_RHS_LINEAR: return dim >= 1 && dim <= 4;
+    case FABM_RHS_LORENZ: return dim == 3;
+    case FABM_RHS_DUFFING:
+    case FABM_RHS_LCR: return dim == 2;
+    case FABM_RHS_MANUFACTURED: return dim == 1;
+    default: return false;
+    }
+}
+
+inline int rhs_n_params(int rhs)
+{
+    switch (rhs) {
+    case FABM_RHS_CONST: return 1;
+    case FABM_RHS_TIME: return 0;
+    case FABM_RHS_LINEAR: return 1;
+    case FABM_RHS_LORENZ: return 3;
+    case FABM_RHS_DUFFING: return 3;
+    case FABM_RHS_MANUFACTURED: return 2;
+    case FABM_RHS_LCR: return 5;
+    default: return -1;
+    }
+}
+
+}  // namespace fabm
