@@ -1,0 +1,350 @@
+"""Throughput of the fractional ABM engine on one synthetic workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fabm|reference]
+                    [--workload NAME] [--precision fp64|split]
+
+One "step" is one whole solve of the workload (every block of the history
+sums, the recurrence, initial values) through the C ABI.  The default
+workload is the 3-dim Lorenz-type system, alpha = 0.98, h = 5e-4, N = 2^18
+steps, one trajectory, plain FP64.
+
+Timing: W untimed warm-up solves, then K timed solves, each bracketed by CUDA
+events, with a 256 MiB buffer written between them to flush L2.  The library
+times its own kernels with CUDA events on the streams they run on (the
+history kernel's numbers give the roofline line).  ``e2e`` repeats the solve
+with host buffers, the host->device and device->host copies inside the timed
+region.  ``cpu_baseline`` times the CPU oracle on a bounded prefix of the same
+workload and extrapolates by N^2.
+
+Under torchrun with N > 1 ranks every rank solves its own replica (the method
+has no exchange step across trajectories); rank 0 prints the line.
+``--impl reference`` times the CPU oracle instead, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import fabm_workloads as wl  # noqa: E402
+
+WORKLOADS = {
+    "lorenz-single": lambda: wl.lorenz_single(),
+    "ml-scalar": lambda: wl.ml_scalar(),
+    "duffing-sweep": lambda: wl.duffing_sweep(),
+    "lorenz-long": lambda: wl.lorenz_long(),
+}
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and local_rank < len(ids) and ids[local_rank].strip().isdigit():
+        return int(ids[local_rank])
+    return local_rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc = gpu, None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _profile_traffic(kernel_src: str, name: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (sha256 of the .cu file must match)."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_sha and m_tr):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+
+
+def cpu_baseline(w, target_s=12.0):
+    """The oracle on a prefix of the workload (1 trajectory, or as many
+    trajectories as the host has cores), extrapolated to the full workload by
+    sum N^2; returns a dict for the JSON line."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ntraj = 1 if w.B == 1 else min(w.B, cores)
+    sub = w.subset(np.arange(ntraj))
+    # calibrate on a short prefix, then size the sample for ~target_s
+    n0 = min(w.N, 2000)
+    t0 = time.perf_counter()
+    oracle.solve_batch(sub.rhs, sub.alpha, sub.h, n0, sub.y0, params=sub.params,
+                       traj_params=sub.traj_params, threads=ntraj)
+    dt0 = max(time.perf_counter() - t0, 1e-4)
+    n = int(min(w.N, n0 * np.sqrt(target_s / dt0)))
+    t0 = time.perf_counter()
+    oracle.solve_batch(sub.rhs, sub.alpha, sub.h, n, sub.y0, params=sub.params,
+                       traj_params=sub.traj_params, threads=ntraj)
+    dt = time.perf_counter() - t0
+    full_time = dt * (w.N / n) ** 2 * (w.B / ntraj)
+    return {"value": w.steps_traj() / full_time, "unit": "steps*traj/s", "cores": ntraj,
+            "kind": "oracle",
+            "sample": f"{ntraj} trajectory(ies) x first {n} of {w.N} steps in {dt:.2f} s, "
+                      f"extrapolated to {w.B} x {w.N} by N^2 (host has {cores} cores)",
+            "history_gmac_s": w.history_macs() / full_time / 1e9}
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ntraj = 1 if w.B == 1 else min(w.B, cores)
+    sub = w.subset(np.arange(ntraj))
+    n0 = min(w.N, 2000)
+    t0 = time.perf_counter()
+    oracle.solve_batch(sub.rhs, sub.alpha, sub.h, n0, sub.y0, params=sub.params,
+                       traj_params=sub.traj_params, threads=ntraj)
+    dt0 = max(time.perf_counter() - t0, 1e-4)
+    n = int(min(w.N, n0 * np.sqrt(4.0 / dt0)))  # ~4 s per step
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.solve_batch(sub.rhs, sub.alpha, sub.h, n, sub.y0, params=sub.params,
+                           traj_params=sub.traj_params, threads=ntraj)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = float(np.mean(times))
+    full_time = dt * (w.N / n) ** 2 * (w.B / ntraj)
+    value = w.steps_traj() / full_time
+    line = {
+        "impl": "reference", "metric": "steps_traj_per_s", "value": value,
+        "unit": "steps*traj/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": full_time * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w, args),
+        "history_gmac_s": w.history_macs() / full_time / 1e9,
+        "cpu_baseline": {"value": value, "unit": "steps*traj/s", "cores": ntraj,
+                         "kind": "oracle",
+                         "sample": f"each step: {ntraj} trajectory(ies) x first {n} of {w.N} "
+                                   f"steps ({dt:.2f} s), extrapolated by N^2"},
+        "e2e": {"value": value, "unit": "steps*traj/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def _config(w, args):
+    return {"workload": w.name, "precision": args.precision, "rhs": w.rhs, "dim": w.dim,
+            "alpha": w.alpha, "h": w.h, "steps_N": w.N, "trajectories": w.B,
+            "l2": "flushed between timed solves (256 MiB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fabm", choices=["fabm", "reference"])
+    ap.add_argument("--workload", default="lorenz-single", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "split"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]()
+    if args.precision is None:
+        args.precision = w.precision
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1710_01133_gb300 as fabm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fabm.load()
+    solver = fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision=args.precision)
+    wstats = solver.kernel_stats()["weights"]
+
+    out_dev = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve_dev():
+        solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solve_dev()
+    barrier()
+
+    solver.set_timing(True)
+    launches = 0
+    times = []
+    with ClockSampler(_gpu_index(local)) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            solve_dev()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            launches += solver.last_launch_count
+    barrier()
+    kstats = solver.kernel_stats()
+    solver.set_timing(False)
+    step_ms = float(np.mean(times))
+    if ws > 1:
+        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # end to end: host y0 in, host trajectory out (pinned), copies timed
+    out_host = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, pin_memory=True)
+    solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_host)
+    e2e_times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_host)
+        e1.record()
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_times))
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    finite = bool(torch.isfinite(out_dev).all().item())
+
+    if rank == 0:
+        units = w.steps_traj() * ws
+        clocks = clk.summary()
+        dom = max(("history", "recurrence", "combine", "init"), key=lambda k: kstats[k]["ms"])
+        ks = kstats[dom]
+        sm_max = clocks["sm_max_mhz"] or 2070.0
+        peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9  # GFLOP/s
+        achieved = ks["flops"] / (ks["ms"] * 1e-3) / 1e9 if ks["ms"] > 0 else 0.0
+        src = os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", "history_fp64.cu")
+        traffic = _profile_traffic(src, "history_fp64_lorenz") if dom == "history" else None
+        h2d = w.B * w.dim * 8 + w.B * 8 * 8 + w.B * 8
+        d2h = w.B * (w.N + 1) * w.dim * 8 + 8
+        line = {
+            "metric": "steps_traj_per_s",
+            "value": units / (step_ms * 1e-3),
+            "unit": "steps*traj/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, args),
+            "history_gmac_s": w.history_macs() * ws / (step_ms * 1e-3) / 1e9,
+            "roofline": {
+                "kernel": f"{dom} ({args.precision})", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak if peak else None,
+                "traffic": (traffic / ks["launches"] if traffic and ks["launches"] else None),
+                "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
+                             "(measured 1.19 TFLOP/s at 1.96 GHz)",
+                "launches": ks["launches"], "avg_launch_us": ks["ms"] * 1e3 / max(ks["launches"], 1),
+            },
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                        for k, v in kstats.items() if k != "weights"},
+            "weights_ms": wstats["ms"],
+            "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "steps*traj/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "output_finite": finite,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    solver.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -119,6 +119,13 @@ const char *fabm_last_error(void);
 fabm_status fabm_set_block(fabm_solver *s, int L);
 int fabm_get_block(const fabm_solver *s);
 
+/* Record each solve's launch sequence (both streams) as a CUDA graph and
+ * replay it while the batch size, the longest trajectory and the buffers stay
+ * the same (1, the default), or launch kernel by kernel (0).  Inputs (y0,
+ * parameters, per-trajectory lengths) are read from device memory by the
+ * kernels, so a cached graph serves any inputs of the same shape. */
+fabm_status fabm_set_graphs(fabm_solver *s, int enable);
+
 /* Copy the first n device weights of the solver to host arrays (n <= N+1):
  *   B[d] = b_{d-1}, A[d] = a_{d-1} (d >= 1; index 0 holds 0),
  *   D[m] = c_{m-1} - a_{m-1}       (m >= 1; index 0 holds 0),
@@ -136,7 +143,8 @@ enum {
     FABM_KERNEL_HISTORY = 2,     /* far-history sums (the O(N^2) part)                 */
     FABM_KERNEL_COMBINE = 3,     /* fixed-order combination of history partial sums    */
     FABM_KERNEL_RECURRENCE = 4,  /* in-block predictor/corrector steps                 */
-    FABM_KERNEL_KINDS = 5
+    FABM_KERNEL_SLICE = 5,       /* split path: f of a finished block -> bf16 slices   */
+    FABM_KERNEL_KINDS = 6
 };
 
 /* Enable (1) or disable (0) per-launch timing: with timing on, every launch

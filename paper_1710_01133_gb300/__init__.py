@@ -21,8 +21,8 @@ RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactu
 PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
 _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_last_error", "fabm_set_block", "fabm_get_block", "fabm_last_launch_count",
-            "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats")
-KERNEL_KINDS = ("weights", "init", "history", "combine", "recurrence")
+            "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs")
+KERNEL_KINDS = ("weights", "init", "history", "combine", "recurrence", "slice")
 
 _lib = None
 
@@ -62,9 +62,10 @@ def load(build_if_missing: bool = True):
     lib.fabm_last_launch_count.restype = i64
     lib.fabm_copy_weights.argtypes = [vp, i64, P(d), P(d), P(d)]
     lib.fabm_set_timing.argtypes = [vp, i]
+    lib.fabm_set_graphs.argtypes = [vp, i]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
-              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats"):
+              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -133,6 +134,10 @@ def fabm_last_launch_count(handle) -> int:
     return load().fabm_last_launch_count(handle)
 
 
+def fabm_set_graphs(handle, enable: bool):
+    _check(load().fabm_set_graphs(handle, int(bool(enable))))
+
+
 def fabm_set_timing(handle, enable: bool):
     _check(load().fabm_set_timing(handle, int(bool(enable))))
 
@@ -191,6 +196,9 @@ class Solver:
     @property
     def last_launch_count(self) -> int:
         return fabm_last_launch_count(self.handle)
+
+    def set_graphs(self, enable: bool = True):
+        fabm_set_graphs(self.handle, enable)
 
     def set_timing(self, enable: bool = True):
         fabm_set_timing(self.handle, enable)

@@ -92,31 +92,53 @@ struct fabm_solver {
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
     DevBuf<double> wB, wA, wD;
+    // split path: Hankel weight tiles per lag, their exponents
+    DevBuf<__nv_bfloat16> wH;
+    DevBuf<int> wHe;
+    int64_t g_max = 0;
     // per-batch workspace
     DevBuf<double> F, Ystage, G, part, y0, par;
+    DevBuf<__nv_bfloat16> Fs;  // split: f slices
+    DevBuf<int> Fe;            // split: f exponents
+    DevBuf<float2> spart;      // split: float-float partials
+    DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
     DevBuf<unsigned long long> status;
     cudaStream_t sR = nullptr, sG = nullptr;
-    cudaEvent_t evR[kEvRing] = {}, evG[2] = {};
+    cudaEvent_t evR[kEvRing] = {}, evG[2] = {}, evFork = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
     bool timing = false;
+    bool capturing = false;
     std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
-    std::vector<int> ev_kind;          // kind of each used pair
+    struct Rec {
+        int kind;
+        double flops;
+    };
+    std::vector<Rec> recs;             // one per timed launch, pair i = ev_pool[2i], [2i+1]
+    // CUDA graph of the last solve's launch sequence (fabm_set_graphs)
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uintptr_t> gkey;
+    std::vector<Rec> grecs;
+    int64_t glaunches = 0;
     int64_t k_launches[FABM_KERNEL_KINDS] = {};
     double k_ms[FABM_KERNEL_KINDS] = {};
     double k_flops[FABM_KERNEL_KINDS] = {};
 
     ~fabm_solver()
     {
-        wB.release(), wA.release(), wD.release();
+        wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
         F.release(), Ystage.release(), G.release(), part.release();
+        Fs.release(), Fe.release(), spart.release(), err.release();
         y0.release(), par.release(), nEach.release(), status.release();
         for (auto &e : evR)
             if (e) cudaEventDestroy(e);
         for (auto &e : evG)
             if (e) cudaEventDestroy(e);
+        if (evFork) cudaEventDestroy(evFork);
+        if (gexec) cudaGraphExecDestroy(gexec);
         for (auto &e : ev_pool) cudaEventDestroy(e);
         if (sR) cudaStreamDestroy(sR);
         if (sG) cudaStreamDestroy(sG);
@@ -129,7 +151,7 @@ namespace {
 void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int *n_chunks, int64_t *kc)
 {
     const int col_tiles = (cols + 3) / 4;
-    const int64_t want_ctas = 152 * 12;
+    const int64_t want_ctas = 152 * 4;  // 4 CTAs of up to 4 column warps per SM
     int64_t n = (want_ctas + col_tiles - 1) / col_tiles;
     const int64_t min_kc = 64;
     n = std::min<int64_t>(n, (k_end + min_kc - 1) / min_kc);
@@ -167,42 +189,104 @@ struct DeviceGuard {
 };
 
 // Runs launch() on stream st; counts it, and with timing on brackets it with a
-// pair of CUDA events on st.
+// pair of CUDA events on st (captured as event nodes when a graph is being
+// recorded).
 template <class Fn>
 cudaError_t timed_launch(fabm_solver *s, int kind, cudaStream_t st, double flops, Fn &&launch)
 {
     ++s->launches;
     if (!s->timing) return launch();
-    const size_t pair = s->ev_kind.size();
+    const size_t pair = s->recs.size();
     while (s->ev_pool.size() < 2 * (pair + 1)) {
         cudaEvent_t e;
         cudaError_t err = cudaEventCreate(&e);
         if (err != cudaSuccess) return err;
         s->ev_pool.push_back(e);
     }
-    cudaError_t err = cudaEventRecord(s->ev_pool[2 * pair], st);
+    const unsigned flags = s->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaError_t err = cudaEventRecordWithFlags(s->ev_pool[2 * pair], st, flags);
     if (err != cudaSuccess) return err;
     err = launch();
     if (err != cudaSuccess) return err;
-    err = cudaEventRecord(s->ev_pool[2 * pair + 1], st);
+    err = cudaEventRecordWithFlags(s->ev_pool[2 * pair + 1], st, flags);
     if (err != cudaSuccess) return err;
-    s->ev_kind.push_back(kind);
-    s->k_launches[kind] += 1;
-    s->k_flops[kind] += flops;
+    s->recs.push_back({kind, flops});
     return cudaSuccess;
 }
 
-// After the streams are idle: add up the recorded event pairs.
-cudaError_t collect_timing(fabm_solver *s)
+// After the streams are idle: add up the event pairs of the given records.
+cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &recs)
 {
-    for (size_t i = 0; i < s->ev_kind.size(); ++i) {
+    for (size_t i = 0; i < recs.size(); ++i) {
         float ms = 0.f;
         cudaError_t e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
         if (e != cudaSuccess) return e;
-        s->k_ms[s->ev_kind[i]] += ms;
+        s->k_ms[recs[i].kind] += ms;
+        s->k_launches[recs[i].kind] += 1;
+        s->k_flops[recs[i].kind] += recs[i].flops;
     }
-    s->ev_kind.clear();
     return cudaSuccess;
+}
+
+// Enqueues one solve on the solver's two streams (or records it into the
+// graph being captured): init, then per block the far history on stream G and
+// the recurrence (and, split path, the slicing of the finished segment) on
+// stream R.
+fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &w, int64_t nblk,
+                          int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks)
+{
+    const int L = s->L;
+    const int64_t cols = bt.cols;
+    const bool split = s->precision == FABM_SPLIT;
+    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
+                               [&] { return launch_init(s->rhs, bt, s->sR); }));
+    for (int64_t c = 0; c < nblk; ++c) {
+        const double *Gc = nullptr;
+        if (c >= 2) {
+            double *Gbuf = s->G.p + (size_t)(c % 2) * 2 * L * cols;
+            int n_chunks;
+            int64_t kc;
+            const int64_t k_end = (c - 1) * L;
+            // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
+            const double flops = 4.0 * L * (double)k_end * (double)cols;
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
+            if (split) {
+                n_chunks = (int)std::min<int64_t>(c - 1, split_chunks);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                    return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, n_ct,
+                                             (int)cols, n_chunks, s->spart.p, s->err.p, s->sG);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
+                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, Gbuf, s->sG);
+                }));
+            } else {
+                plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                    return launch_hist_fp64(bt, w, c, L, n_chunks, kc, s->part.p, s->sG);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
+                    return launch_hist_reduce(s->part.p, n_chunks, L, (int)cols, Gbuf, s->sG);
+                }));
+            }
+            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 2], s->sG));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 2], 0));
+            Gc = Gbuf;
+        }
+        // lag-1 block and in-block triangle: per target up to 2L points
+        const int64_t lo = c * L, hi = std::min<int64_t>((c + 1) * L, Nmax);
+        const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
+                              ((c >= 1 ? L : 0) + 0.5 * (double)(hi - lo + 1));
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
+            return launch_recur(s->rhs, bt, w, s->k, c, L, Gc, s->sR);
+        }));
+        if (split && c + 2 < nblk) {  // segment c is read by the blocks c+2 ..
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0, [&] {
+                return launch_slice_f(bt, n_ct, c, s->Fs.p, s->Fe.p, s->sR);
+            }));
+        }
+        FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
+    }
+    return FABM_OK;
 }
 
 fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
@@ -213,7 +297,6 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int64_t N = s->N;
     const int L = s->L;
     s->launches = 0;
-    s->ev_kind.clear();
 
     // host-side inputs: per-trajectory steps and parameter rows
     std::vector<int64_t> ne(B);
@@ -234,6 +317,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     for (int64_t i = 0; i < B * dim; ++i)
         if (!std::isfinite(y0[i])) return fail(FABM_EINVAL, "y0[%lld] is not finite", (long long)i);
 
+    const bool split = s->precision == FABM_SPLIT;
     // workspace
     const int64_t nblk = (Nmax + L - 1) / L;
     const size_t f_elems = (size_t)(N + 1) * cols;
@@ -247,6 +331,16 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
     FABM_CUDA_TRY(s->status.ensure(1));
+    const int n_ct = (int)((cols + 127) / 128);
+    int split_chunks = 1;
+    if (split) {
+        split_chunks = std::max(1, 148 / n_ct);
+        FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
+        FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
+        FABM_CUDA_TRY(s->spart.ensure(split_part_elems(split_chunks, (int)cols)));
+        FABM_CUDA_TRY(s->err.ensure(1));
+        FABM_CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(unsigned int), s->sR));
+    }
     double *Y = out;
     if (!out_on_device) {
         FABM_CUDA_TRY(s->Ystage.ensure((size_t)B * (N + 1) * dim));
@@ -273,44 +367,67 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     bt.status = s->status.p;
     DevWeights w{s->wB.p, s->wA.p, s->wD.p, s->w_ext};
 
-    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
-                               [&] { return launch_init(s->rhs, bt, s->sR); }));
-    for (int64_t c = 0; c < nblk; ++c) {
-        const double *Gc = nullptr;
-        if (c >= 2) {
-            double *Gbuf = s->G.p + (size_t)(c % 2) * 2 * L * cols;
-            int n_chunks;
-            int64_t kc;
-            const int64_t k_end = (c - 1) * L;
-            plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
-            // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
-            const double flops = 4.0 * L * (double)k_end * (double)cols;
-            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
-            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
-                return launch_hist_fp64(bt, w, c, L, n_chunks, kc, s->part.p, s->sG);
-            }));
-            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
-                return launch_hist_reduce(s->part.p, n_chunks, L, (int)cols, Gbuf, s->sG);
-            }));
-            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 2], s->sG));
-            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 2], 0));
-            Gc = Gbuf;
+    const std::vector<uintptr_t> key = {
+        (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing, (uintptr_t)Y,
+        (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
+        (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
+        (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p};
+    auto enqueue = [&]() -> fabm_status {
+        return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks);
+    };
+    if (!s->use_graphs) {
+        s->recs.clear();
+        fabm_status est = enqueue();
+        if (est != FABM_OK) return est;
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
+        FABM_CUDA_TRY(collect_timing(s, s->recs));
+    } else {
+        if (!s->gexec || s->gkey != key) {
+            if (s->gexec) cudaGraphExecDestroy(s->gexec);
+            s->gexec = nullptr;
+            s->recs.clear();
+            cudaGraph_t graph = nullptr;
+            FABM_CUDA_TRY(cudaStreamBeginCapture(s->sR, cudaStreamCaptureModeThreadLocal));
+            s->capturing = true;
+            cudaError_t e = cudaEventRecord(s->evFork, s->sR);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG, s->evFork, 0);
+            fabm_status est = e == cudaSuccess ? enqueue() : FABM_ECUDA;
+            if (est == FABM_OK) {
+                e = cudaEventRecord(s->evFork, s->sG);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evFork, 0);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(s->sR, &graph);
+            s->capturing = false;
+            if (est != FABM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return est;
+            }
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                s->gexec = nullptr;
+                return fail(FABM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            }
+            s->gkey = key;
+            s->grecs = s->recs;
+            s->glaunches = s->launches;
         }
-        // lag-1 block and in-block triangle: per target up to 2L points
-        const int64_t lo = c * L, hi = std::min<int64_t>((c + 1) * L, Nmax);
-        const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
-                              ((c >= 1 ? L : 0) + 0.5 * (double)(hi - lo + 1));
-        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
-            return launch_recur_fp64(s->rhs, bt, w, s->k, c, Gc, s->sR);
-        }));
-        FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
+        FABM_CUDA_TRY(cudaGraphLaunch(s->gexec, s->sR));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
+        s->launches = s->glaunches;
+        FABM_CUDA_TRY(collect_timing(s, s->grecs));
     }
-    FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
-    FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
-    FABM_CUDA_TRY(collect_timing(s));
+
 
     unsigned long long st = 0;
     FABM_CUDA_TRY(cudaMemcpy(&st, s->status.p, sizeof st, cudaMemcpyDeviceToHost));
+    if (split) {
+        unsigned int tout = 0;
+        FABM_CUDA_TRY(cudaMemcpy(&tout, s->err.p, sizeof tout, cudaMemcpyDeviceToHost));
+        if (tout) return fail(FABM_ETIMEOUT, "a history kernel gave up waiting on a barrier");
+    }
 
     if (!out_on_device) {
         const size_t row = (size_t)(N + 1) * dim;
@@ -359,8 +476,8 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(FABM_EINVAL, "alpha %g outside (0, 1)", alpha);
     if (!(h > 0.0) || !std::isfinite(h)) return fail(FABM_EINVAL, "h %g must be positive", h);
     if (N < 1 || N > (1LL << 31)) return fail(FABM_EINVAL, "N %lld outside 1..2^31", (long long)N);
-    if (precision != FABM_FP64)
-        return fail(FABM_EINVAL, "precision %d not available in this build", precision);
+    if (precision != FABM_FP64 && precision != FABM_SPLIT)
+        return fail(FABM_EINVAL, "precision %d unknown", precision);
     fabm_status st = check_rhs(rhs_id, dim, n_params);
     if (st != FABM_OK) return st;
     if (n_params > 0 && !params) return fail(FABM_EINVAL, "params is NULL");
@@ -398,16 +515,30 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto &ev : s->evG)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evFork, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
+        s->recs.clear();
         e = timed_launch(s, FABM_KERNEL_WEIGHTS, s->sR, 0.0, [&] {
             return launch_weights(alpha, s->w_ext, inv_g1, s->k.inv_gamma2, s->wB.p, s->wA.p,
                                   s->wD.p, s->sR);
         });
         s->timing = false;
     }
+    if (e == cudaSuccess && precision == FABM_SPLIT) {
+        s->L = kSplitSeg;
+        e = prepare_hist_split();
+        s->g_max = (N + kSplitSeg - 1) / kSplitSeg - 1;
+        if (e == cudaSuccess && s->g_max >= 2) {
+            e = s->wH.ensure((size_t)(s->g_max + 1) * 2 * 3 * 15 * 64);
+            if (e == cudaSuccess) e = s->wHe.ensure((size_t)(s->g_max + 1) * 2);
+            if (e == cudaSuccess)
+                e = launch_hankel_weights(s->wB.p, s->wA.p, s->g_max, s->wH.p, s->wHe.p, s->sR);
+        }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->sR);
-    if (e == cudaSuccess) e = collect_timing(s);
+    if (e == cudaSuccess) e = collect_timing(s, s->recs);
+    s->recs.clear();
     if (e != cudaSuccess)
         return cleanup(fail(e == cudaErrorMemoryAllocation ? FABM_ENOMEM : FABM_ECUDA,
                             "fabm_create: %s", cudaGetErrorString(e)));
@@ -457,8 +588,10 @@ fabm_status fabm_set_block(fabm_solver *s, int L)
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     if (L % 32 != 0 || L < 32 || L > kMaxBlockL)
         return fail(FABM_EINVAL, "block length %d must be a multiple of 32 in 32..%d", L, kMaxBlockL);
-    if (s->precision == FABM_FP64 && L != kRecurL)
-        return fail(FABM_EINVAL, "the FP64 path uses blocks of %d targets", kRecurL);
+    if (s->precision == FABM_SPLIT && L != kSplitSeg)
+        return fail(FABM_EINVAL, "the split path uses blocks of %d targets", kSplitSeg);
+    if (s->precision == FABM_FP64 && L != kRecurL && L != 2 * kRecurL)
+        return fail(FABM_EINVAL, "the FP64 path uses blocks of 32 or 64 targets");
     std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
     s->L = L;
@@ -482,6 +615,16 @@ fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, d
 }
 
 int64_t fabm_last_launch_count(const fabm_solver *s) { return s ? s->launches : 0; }
+
+fabm_status fabm_set_graphs(fabm_solver *s, int enable)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->use_graphs = enable != 0;
+    return FABM_OK;
+}
 
 fabm_status fabm_set_timing(fabm_solver *s, int enable)
 {

@@ -17,6 +17,7 @@
 // block and the block's own triangle, step by step.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,7 +26,8 @@
 namespace fabm {
 
 constexpr int kWarp = 32;
-constexpr int kRecurL = 32;        // targets per block in the recurrence kernels
+constexpr int kRecurL = 32;        // targets per block of the FP64 path
+constexpr int kSplitSeg = 64;      // targets per block (= points per segment) of the split path
 constexpr int kMaxParams = FABM_MAX_PARAMS;
 
 // Weight vectors on the device, index 0..N.  B[0] = A[0] = D[0] = 0.
@@ -74,9 +76,37 @@ cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c,
 cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols, double *G,
                                cudaStream_t st);
 
-// a4 + a5 (FP64): steps of block c for every trajectory; G holds the far
-// history of block c (2 x L x cols) or is NULL when c < 2.
-cudaError_t launch_recur_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
-                              const StepConsts &k, int64_t c, const double *G, cudaStream_t st);
+// a4 + a5: steps of block c (L = 32 or 64 targets) for every trajectory, in
+// double; G holds the far history of block c (2 x L x cols) or is NULL when
+// c < 2.
+cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
+                         int64_t c, int L, const double *G, cudaStream_t st);
+
+// ---- split path (history on tensor cores) ----
+
+// f of segment seg (64 points) -> bf16 slices Fs and per-column exponents Ef.
+cudaError_t launch_slice_f(const DevBatch &bt, int n_ct, int64_t seg, __nv_bfloat16 *Fs, int *Ef,
+                           cudaStream_t st);
+
+// Hankel weight tiles and exponents for the lags 2..g_max.
+cudaError_t launch_hankel_weights(const double *WB, const double *WA, int64_t g_max,
+                                  __nv_bfloat16 *WH, int *Ew, cudaStream_t st);
+
+// Kernel attributes of the tensor kernel (dynamic shared memory); call once
+// per device before the first launch (and outside any graph capture).
+cudaError_t prepare_hist_split();
+
+// float2 elements of the partial-sum buffer for n_chunks chunks.
+size_t split_part_elems(int n_chunks, int cols);
+
+// Far history of block c over segments 0..c-2 on tensor cores; n_chunks
+// chunks of segments (1 <= n_chunks <= c-1) per column tile of 128.
+cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
+                              const int *Ew, int64_t c, int n_ct, int cols, int n_chunks,
+                              float2 *part, unsigned int *err, cudaStream_t st);
+
+// G[kind][t][col] (double) = sum of the float-float partials over chunks.
+cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, double *G,
+                                 cudaStream_t st);
 
 }  // namespace fabm

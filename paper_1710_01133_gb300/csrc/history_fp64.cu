@@ -90,8 +90,21 @@ __global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks
     for (int64_t base = 0; base < n_out; base += groups) {
         const int64_t o = base + gtid / R;
         double s = 0.0;
-        if (o < n_out)
-            for (int ch = r; ch < n_chunks; ch += R) s += part[(int64_t)ch * n_out + o];
+        if (o < n_out) {
+            // independent loads in flight, summed in chunk order
+            int ch = r;
+            for (; ch + 3 * R < n_chunks; ch += 4 * R) {
+                const double v0 = part[(int64_t)ch * n_out + o];
+                const double v1 = part[(int64_t)(ch + R) * n_out + o];
+                const double v2 = part[(int64_t)(ch + 2 * R) * n_out + o];
+                const double v3 = part[(int64_t)(ch + 3 * R) * n_out + o];
+                s += v0;
+                s += v1;
+                s += v2;
+                s += v3;
+            }
+            for (; ch < n_chunks; ch += R) s += part[(int64_t)ch * n_out + o];
+        }
 #pragma unroll
         for (int off = R / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (r == 0 && o < n_out) G[o] = s;

@@ -1,0 +1,436 @@
+// a2 + a3 on tensor cores ("split" precision): the far part of the hereditary
+// sums of Sec. 2 of arXiv:1710.01133 as bf16 tcgen05 MMAs that are exact per
+// 64-point segment, accumulated across segments in compensated fp32 and
+// combined across CTAs in float-float, then rounded once to double.
+//
+// Number format.  Time is cut into segments of kSeg = 64 points (one
+// recurrence block each).  For a segment and a column, f is written on a
+// fixed-point grid: x = f 2^(8-E) with |x| < 256 (E from the segment's largest
+// |f|), then x = s0 + s1 + s2 with s0 an integer, s1 a multiple of 2^-8 and s2
+// of 2^-16, each with at most 8 significant bits, i.e. each an exact bf16.
+// The weight rows of a segment get the same treatment with one exponent per
+// weight kind (the weights decrease with the distance, so the first one is
+// the largest).  Dropping the products of order >= 3 and the rounding of the
+// last slice leave a representation error of at most 2^-25 of the segment's
+// largest |f| (and weight).
+//
+// Exactness.  Level-0 products s0*t0 are integers below 2^16 in magnitude, so
+// their sum over the 64 points of a segment (< 2^22) is exact in the fp32
+// accumulator whatever order or truncation the tensor core uses.  The other
+// five products (levels 1 and 2) go to a second accumulator whose rounding is
+// below 2^-32 of the result.  Per segment each value is then v = L0 + L12
+// (one fp32 rounding), scaled by 2^(E_f + E_w - 16) (exact) and added with
+// Kahan compensation.
+//
+// Toeplitz weights without an N x N matrix.  Inside a segment the points are
+// taken in reverse order j' = 63 - j, which turns the weight tile into a Hankel
+// matrix W(D0 + n + j'), D0 = (c - seg) 64 - 62.  A no-swizzle K-major operand
+// is a grid of 8x8 core matrices addressed as base + LBO*k1 + SBO*n1; with
+// LBO = SBO = 128 bytes, core matrix (n1, k1) is stored once at index n1 + k1,
+// so a 64 x 64 weight tile needs 15 core matrices (1920 bytes) per kind and
+// slice instead of 8 KB.  These tiles depend only on the lag c - seg and are
+// built once per solver.
+//
+// CTA layout (1 CTA per SM, 320 threads): warp 0 streams segments into a
+// 3-stage shared-memory ring with bulk copies; warp 1 issues the MMAs into one
+// of two TMEM accumulator sets (512 columns); warps 2..9 drain the other set,
+// each warp one TMEM lane quadrant (its columns) and the 64 targets of one
+// kind, with Kahan-compensated fp32 sums held in registers.
+// Every wait is bounded; on timeout the CTA sets an error flag, waits for its
+// own copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "fabm_internal.cuh"
+#include "sm100_ptx.cuh"
+
+namespace fabm {
+namespace {
+
+using namespace ptx;
+
+constexpr int kSeg = kSplitSeg;      // 64 points per segment = targets per block
+constexpr int kMC = 128;             // columns per CTA (TMEM lanes)
+constexpr int kStages = 3;
+constexpr int kHk = 15;              // Hankel core matrices per (kind, slice)
+constexpr int kFBytes = 3 * kMC * kSeg * 2;          // 49152: 3 slices of 128 x 64 bf16
+constexpr int kWBytes = 2 * 3 * kHk * 128;           // 11520
+constexpr int kStageStride = 61440;                  // F + W, padded to 1 KB
+constexpr int kThreads = 320;     // warp 0: copies, warp 1: MMAs, warps 2..9: drain
+constexpr int kEpiWarps = 8;
+constexpr int kEpiT = 64;         // targets per drain thread
+constexpr size_t kSmemBytes = (size_t)kStages * kStageStride + 1024;
+constexpr long long kWaitCycles = 4000000000LL;      // ~2 s at 2 GHz
+
+__device__ __forceinline__ int exp_clamp(int e) { return e < -126 ? -126 : (e > 127 ? 127 : e); }
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((exp_clamp(e) + 127) << 23); }
+
+// --------------------------------------------------------- f slicing ---
+
+// f of segment `seg` (points seg*64 .. seg*64+63) -> three bf16 slices in the
+// operand layout [seg][ct][slice][k1 = j'/8][col 128][j'%8], j' = 63 - j, and
+// the exponent E per column in Ef[seg][ct][col].  grid = cols_pad/32, block =
+// 256 = 32 columns x 8 groups of 8 points.
+__global__ void __launch_bounds__(256) slice_f_kernel(const double *__restrict__ F, int64_t ldF,
+                                                      int64_t n_rows, int cols, int n_ct,
+                                                      int64_t seg,
+                                                      __nv_bfloat16 *__restrict__ Fs,
+                                                      int *__restrict__ Ef)
+{
+    __shared__ float smax[8][32];
+    const int cl = threadIdx.x % 32, k1 = threadIdx.x / 32;
+    const int col = blockIdx.x * 32 + cl;
+    float hi[8], lo[8];
+    float m = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < 8; ++k0) {
+        const int j = 63 - (8 * k1 + k0);
+        const int64_t row = seg * kSeg + j;
+        double f = (col < cols && row < n_rows) ? F[row * ldF + col] : 0.0;
+        hi[k0] = (float)f;
+        lo[k0] = (float)(f - (double)hi[k0]);
+        m = fmaxf(m, fabsf(hi[k0]));
+    }
+    smax[k1][cl] = m;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m = fmaxf(m, smax[i][cl]);
+    int E = 0;
+    if (m > 0.f && m <= 3.0e38f) E = ilogbf(m) + 1;
+    if (E < -100) E = -100;
+    const float sc = pow2f(8 - E);
+    uint32_t w[3][4];
+#pragma unroll
+    for (int k0 = 0; k0 < 8; k0 += 2) {
+        float t[3][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float xh = hi[k0 + u] * sc, xl = lo[k0 + u] * sc;
+            const float t0 = rintf(xh);
+            const float r = ((xh - t0) + xl) * 256.f;
+            const float t1 = rintf(r);
+            const float t2 = rintf((r - t1) * 256.f);
+            t[0][u] = t0, t[1][u] = t1 * 0x1p-8f, t[2][u] = t2 * 0x1p-16f;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            __nv_bfloat162 p = __floats2bfloat162_rn(t[q][0], t[q][1]);
+            w[q][k0 / 2] = *reinterpret_cast<uint32_t *>(&p);
+        }
+    }
+    const int ct = col / kMC, cloc = col % kMC;
+    if (col < n_ct * kMC) {
+        __nv_bfloat16 *base = Fs + ((seg * n_ct + ct) * 3) * (int64_t)(kMC * kSeg);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            *reinterpret_cast<uint4 *>(base + q * (kMC * kSeg) + k1 * (kMC * 8) + cloc * 8) =
+                make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+        if (k1 == 0) Ef[(seg * n_ct + ct) * kMC + cloc] = E;
+    }
+}
+
+// ------------------------------------------------- Hankel weight tiles ---
+
+// For every lag g in [2, g_max]: D0 = 64 g - 62, exponent E_w = ilogb(W(D0)) + 1
+// per kind, and the Hankel core matrices of the three slices of W(D0 + t),
+// t = 8h + r0 + c0.  WH[g][kind][slice][h][r0][c0]; Ew[g][kind].
+// One thread per (g, kind, h, r0) row.
+__global__ void hankel_weights_kernel(const double *__restrict__ WB, const double *__restrict__ WA,
+                                      int64_t g_max, __nv_bfloat16 *__restrict__ WH,
+                                      int *__restrict__ Ew)
+{
+    const int64_t rows = (g_max + 1) * 2 * kHk * 8;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int r0 = (int)(r % 8), h = (int)((r / 8) % kHk), kind = (int)((r / (8 * kHk)) % 2);
+        const int64_t g = r / (8 * kHk * 2);
+        if (g < 2) continue;
+        const double *W = kind ? WA : WB;
+        const int64_t D0 = 64 * g - 62;
+        const int E = ilogb(W[D0]) + 1;
+        if (h == 0 && r0 == 0) Ew[g * 2 + kind] = E;
+        const double sc = ldexp(1.0, 8 - E);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int c0 = 0; c0 < 8; c0 += 2) {
+            float t[3][2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const double x = W[D0 + 8 * h + r0 + c0 + u] * sc;
+                const double t0 = rint(x);
+                const double rr = (x - t0) * 256.0;
+                const double t1 = rint(rr);
+                const double t2 = rint((rr - t1) * 256.0);
+                t[0][u] = (float)t0, t[1][u] = (float)(t1 * 0x1p-8), t[2][u] = (float)(t2 * 0x1p-16);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                __nv_bfloat162 p = __floats2bfloat162_rn(t[q][0], t[q][1]);
+                w[q][c0 / 2] = *reinterpret_cast<uint32_t *>(&p);
+            }
+        }
+        __nv_bfloat16 *base = WH + g * (kWBytes / 2) + (int64_t)kind * 3 * kHk * 64;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            *reinterpret_cast<uint4 *>(base + q * kHk * 64 + h * 64 + r0 * 8) =
+                make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// --------------------------------------------------- the tensor kernel ---
+
+struct SplitArgs {
+    const __nv_bfloat16 *Fs;  // [seg][ct][3][8][128][8]
+    const int *Ef;            // [seg][ct][128]
+    const __nv_bfloat16 *WH;  // [g][2][3][15][8][8]
+    const int *Ew;            // [g][2]
+    int64_t c;                // target block: m = 64c+1 .. 64c+64
+    int n_ct;
+    int cols;
+    int n_seg;                // segments 0 .. n_seg-1 (= c-1)
+    int n_chunks;             // gridDim.y
+    float2 *part;             // [chunk][2][64][cols] (sum, -compensation)
+    unsigned int *err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageStride);
+    uint64_t *empty = full + kStages;
+    uint64_t *acc_full = empty + kStages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *done = acc_empty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ct = blockIdx.x, ch = blockIdx.y;
+    const int s_lo = (int)((int64_t)ch * a.n_seg / a.n_chunks);
+    const int s_hi = (int)((int64_t)(ch + 1) * a.n_seg / a.n_chunks);
+    const int nseg = s_hi - s_lo;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1), mbar_init(&empty[i], 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], kEpiWarps);
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < nseg && ok; ++i) {
+                const int st = i % kStages;
+                const uint32_t ph = (i / kStages) & 1;
+                if (!mbar_wait(&empty[st], ph ^ 1, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                const int64_t seg = s_lo + i;
+                const int64_t g = a.c - seg;
+                uint8_t *dst = smem + st * kStageStride;
+                mbar_arrive_expect_tx(&full[st], kFBytes + kWBytes);
+                bulk_g2s(dst, a.Fs + (seg * a.n_ct + ct) * (int64_t)(kFBytes / 2), kFBytes, &full[st]);
+                bulk_g2s(dst + kFBytes, a.WH + g * (int64_t)(kWBytes / 2), kWBytes, &full[st]);
+                issued = i + 1;
+            }
+            // copies still in flight complete their stage's phase: wait for them
+            for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+                mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitCycles);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(kMC, kSeg);
+            for (int i = 0; i < nseg && ok; ++i) {
+                const int st = i % kStages;
+                const uint32_t ph = (i / kStages) & 1;
+                const int b = i & 1;
+                const uint32_t bph = (i >> 1) & 1;
+                if (!mbar_wait(&full[st], ph, kWaitCycles) ||
+                    !mbar_wait(&acc_empty[b], bph ^ 1, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sF = smem_u32(smem + st * kStageStride);
+                const uint32_t sW = sF + kFBytes;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t d0 = tmem + b * 256 + k * 64;  // level 0
+                    const uint32_t d12 = d0 + 128;                // levels 1 and 2
+#pragma unroll
+                    for (int s = 0; s < kSeg / 16; ++s) {
+                        uint64_t A[3], Bw[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            A[q] = smem_desc(sF + q * (kFBytes / 3) + s * 4096, 2048, 128);
+                            Bw[q] = smem_desc(sW + (k * 3 + q) * (kHk * 128) + s * 256, 128, 128);
+                        }
+                        mma_bf16(d0, A[0], Bw[0], idesc, s > 0);
+                        mma_bf16(d12, A[0], Bw[1], idesc, s > 0);
+                        mma_bf16(d12, A[1], Bw[0], idesc, 1);
+                        mma_bf16(d12, A[0], Bw[2], idesc, 1);
+                        mma_bf16(d12, A[1], Bw[1], idesc, 1);
+                        mma_bf16(d12, A[2], Bw[0], idesc, 1);
+                    }
+                }
+                mma_commit(&empty[st]);
+                mma_commit(&acc_full[b]);
+            }
+            mma_commit(done);
+            if (!mbar_wait(done, 0, kWaitCycles)) ok = false;
+        }
+    } else {
+        // drain: warp w reads TMEM lanes 32*(w%4).. (its columns) and the 64
+        // targets of one kind.  Kahan sums in fp32; the compensation terms are
+        // kept as packed bf16 pairs (fp32's exponent range, 2^-9 relative error
+        // on a term that is itself below half an ulp of the sum).
+        const int q = warp % 4, kind = (warp - 2) / 4, t0 = 0;
+        const int cloc = q * 32 + lane;
+        const int64_t col = (int64_t)ct * kMC + cloc;
+        float sum[kEpiT];
+        uint32_t cmp2[kEpiT / 2];
+#pragma unroll
+        for (int t = 0; t < kEpiT; ++t) sum[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kEpiT / 2; ++t) cmp2[t] = 0u;
+        for (int i = 0; i < nseg; ++i) {
+            const int b = i & 1;
+            const uint32_t bph = (i >> 1) & 1;
+            if (!mbar_wait(&acc_full[b], bph, kWaitCycles)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int64_t seg = s_lo + i;
+            const int ef = a.Ef[(seg * a.n_ct + ct) * kMC + cloc];
+            const int ew = a.Ew[(a.c - seg) * 2 + kind];
+            const float scale = pow2f(ef + ew - 16);
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + kind * 64 + t0;
+#pragma unroll
+            for (int p = 0; p < kEpiT / 8; ++p) {
+                float v0[8], v1[8];
+                tmem_ld8x2(base + p * 8, base + 128 + p * 8, v0, v1);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    const int t = p * 8 + j;
+                    const uint32_t cw = cmp2[t / 2];
+                    float cnew[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float c = __uint_as_float(u ? (cw & 0xffff0000u) : (cw << 16));
+                        const float y = (v0[j + u] + v1[j + u]) * scale - c;
+                        const float s2 = sum[t + u] + y;
+                        cnew[u] = (s2 - sum[t + u]) - y;
+                        sum[t + u] = s2;
+                    }
+                    __nv_bfloat162 pk = __floats2bfloat162_rn(cnew[0], cnew[1]);
+                    cmp2[t / 2] = *reinterpret_cast<uint32_t *>(&pk);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (ok && col < a.cols) {
+            float2 *out = a.part + ((int64_t)(ch * 2 + kind) * kSeg + t0) * a.cols + col;
+#pragma unroll
+            for (int t = 0; t < kEpiT; ++t) {
+                const uint32_t cw = cmp2[t / 2];
+                const float c = __uint_as_float((t & 1) ? (cw & 0xffff0000u) : (cw << 16));
+                out[(int64_t)t * a.cols] = make_float2(sum[t], -c);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (!ok) atomicOr(a.err, 1u);
+}
+
+// a3: G[kind][t][col] = sum over chunks of (hi + lo), in float-float, chunk
+// ascending; rounded once to double.
+__global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chunks, int64_t n_out,
+                                     double *__restrict__ G)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        float hi = 0.f, lo = 0.f;
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            const float2 v = part[(int64_t)ch * n_out + o];
+            // two-sum of hi + v.x, then fold in the low parts
+            const float s = hi + v.x;
+            const float bb = s - hi;
+            const float e = (hi - (s - bb)) + (v.x - bb);
+            lo += e + v.y;
+            hi = s + lo;
+            lo = lo - (hi - s);
+        }
+        G[o] = (double)hi + (double)lo;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_slice_f(const DevBatch &bt, int n_ct, int64_t seg, __nv_bfloat16 *Fs, int *Ef,
+                           cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)(n_ct * kMC / 32);
+    slice_f_kernel<<<blocks, 256, 0, st>>>(bt.F, bt.ldF, bt.N + 1, bt.cols, n_ct, seg, Fs, Ef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hankel_weights(const double *WB, const double *WA, int64_t g_max,
+                                  __nv_bfloat16 *WH, int *Ew, cudaStream_t st)
+{
+    const int64_t rows = (g_max + 1) * 2 * kHk * 8;
+    int64_t blocks = (rows + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    hankel_weights_kernel<<<(unsigned)blocks, 256, 0, st>>>(WB, WA, g_max, WH, Ew);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_hist_split()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, hist_split_kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs * kThreads > 65536) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(hist_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes);
+}
+
+size_t split_part_elems(int n_chunks, int cols) { return (size_t)n_chunks * 2 * kSeg * cols; }
+
+cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
+                              const int *Ew, int64_t c, int n_ct, int cols, int n_chunks,
+                              float2 *part, unsigned int *err, cudaStream_t st)
+{
+    const int n_seg = (int)(c - 1);
+    if (c < 2 || n_seg < 1) return cudaSuccess;
+    if (n_chunks < 1 || n_chunks > n_seg) return cudaErrorInvalidValue;
+    SplitArgs a{Fs, Ef, WH, Ew, c, n_ct, cols, n_seg, n_chunks, part, err};
+    hist_split_kernel<<<dim3((unsigned)n_ct, (unsigned)n_chunks), kThreads, kSmemBytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, double *G,
+                                 cudaStream_t st)
+{
+    const int64_t n_out = 2LL * kSeg * cols;
+    int64_t blocks = (n_out + 127) / 128;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    combine_split_kernel<<<(unsigned)blocks, 128, 0, st>>>(part, n_chunks, n_out, G);
+    return cudaGetLastError();
+}
+
+}  // namespace fabm

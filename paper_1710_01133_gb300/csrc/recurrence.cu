@@ -1,0 +1,179 @@
+// a4 + a5 in double: the sequential predictor -> f -> corrector -> f chain of
+// Sec. 2 of arXiv:1710.01133 (Eq. abm, the corrector after it) inside one
+// block of L = 32*TPL targets.  One CTA per trajectory, one warp per
+// component.
+//
+// Warp i keeps, in lane a + 32t, the running predictor and corrector sums of
+// component i for target m = cL+1+a+32t:
+//   start   far part from the history kernels (points k < (c-1)L) and the
+//           k = 0 correction D(m) f_0;
+//   lag 1   the L points of block c-1, all known when the block starts;
+//   steps   for s = 0..L-1 the point k = cL+s becomes known; every pending
+//           target adds its term, and the owner of target k+1 then has the
+//           whole sum and runs the step: y^P_i, exchange of y^P across the
+//           component warps, f_i(t, y^P), y_i, exchange of y, f_i(t, y).
+// GB300 runs a double-precision warp instruction in one 64-cycle slot of its
+// sub-partition's FP64 unit whatever the number of active lanes, so one warp
+// per component spreads the serial chain over the FP64 units of several
+// sub-partitions, and adding f_k to all pending targets of a lane costs one
+// instruction.  The time-only part of f (forcing) is evaluated for every target
+// at block start, off the chain.
+#include "rhs.cuh"
+
+namespace fabm {
+namespace {
+
+__device__ inline void report_nonfinite(unsigned long long *status, int64_t step, int traj)
+{
+    atomicMin(status, ((unsigned long long)step << 24) | (unsigned long long)traj);
+}
+
+// Finite test on the exponent bits (no floating-point compare).
+__device__ inline bool finite_bits(double x)
+{
+    return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+
+template <class Rhs, int D>
+__global__ void init_kernel(DevBatch bt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= bt.B) return;
+    double y[D], p[kMaxParams];
+#pragma unroll
+    for (int i = 0; i < kMaxParams; ++i) p[i] = bt.params[(int64_t)b * kMaxParams + i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i] = bt.y0[(int64_t)b * D + i];
+    const double aux = Rhs::aux(0.0, p);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const double f = Rhs::template one<D>(i, y, p, aux);
+        bt.Y[(int64_t)b * (bt.N + 1) * D + i] = y[i];
+        bt.F[(int64_t)b * D + i] = f;
+        ok = ok && finite_bits(y[i]) && finite_bits(f);
+    }
+    if (!ok) report_nonfinite(bt.status, 0, b);
+}
+
+template <class Rhs, int D, int TPL>
+__global__ void __launch_bounds__(D *kWarp)
+    recur_kernel(DevBatch bt, DevWeights w, StepConsts kc, int64_t c, const double *G)
+{
+    constexpr int L = kWarp * TPL;
+    __shared__ double sB[2 * L + 1], sA[2 * L + 1];
+    __shared__ double sy[2][D];  // y^P and y of the current step, all components
+    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
+        sB[j] = w.B[j];
+        sA[j] = w.A[j];
+    }
+    const int b = blockIdx.x;
+    const int i = threadIdx.x / kWarp;  // component of this warp
+    const int lane = threadIdx.x % kWarp;
+    const int64_t Nb = bt.N_each[b];
+    const int64_t m0 = c * L;  // f_{m0} is the newest known point
+    __syncthreads();
+    if (m0 >= Nb) return;  // trajectory finished (uniform over the CTA)
+
+    double p[kMaxParams];
+#pragma unroll
+    for (int q = 0; q < kMaxParams; ++q) p[q] = bt.params[(int64_t)b * kMaxParams + q];
+    const double y0 = bt.y0[(int64_t)b * D + i];
+    const int64_t col = (int64_t)b * D + i;
+    const int64_t ldF = bt.ldF;
+    const double *F = bt.F;
+
+    double accP[TPL], accC[TPL], aux[TPL];
+    const double f0 = F[col];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int a = lane + kWarp * t;
+        const int64_t m = m0 + 1 + a;
+        aux[t] = Rhs::aux((double)m * kc.h, p);
+        accP[t] = G ? G[(int64_t)a * bt.cols + col] : 0.0;
+        accC[t] = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+    }
+    if (c >= 1) {  // lag-1 block: k = m0-L+j, d = m-k = L+1+a-j in [2, 2L]
+        for (int j = 0; j < L; ++j) {
+            const double fk = F[(m0 - L + j) * ldF + col];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const int d = L + 1 + lane + kWarp * t - j;
+                accP[t] = fma(sB[d], fk, accP[t]);
+                accC[t] = fma(sA[d], fk, accC[t]);
+            }
+        }
+    }
+
+    double fk = F[m0 * ldF + col];
+    const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
+    double *Yb = bt.Y + (int64_t)b * (bt.N + 1) * D;
+    for (int s = 0; s < steps; ++s) {
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int d = lane + kWarp * t - s + 1;  // distance from k = m0+s
+            const int dd = d > 0 ? d : 0;            // done targets add B(0) = A(0) = 0
+            accP[t] = fma(sB[dd], fk, accP[t]);
+            accC[t] = fma(sA[dd], fk, accC[t]);
+        }
+        const int owner = s % kWarp, slot = s / kWarp;  // uniform over the CTA
+        double aP = 0.0, aC = 0.0, ax = 0.0;
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (t == slot) aP = accP[t], aC = accC[t], ax = aux[t];
+        double fn = 0.0, yc = 0.0;
+        if (lane == owner) sy[0][i] = fma(kc.h_alpha, aP, y0);  // predictor
+        __syncthreads();
+        if (lane == owner) {
+            double y[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) y[q] = sy[0][q];
+            const double fp = Rhs::template one<D>(i, y, p, ax);
+            yc = fma(kc.h_alpha, fma(fp, kc.inv_gamma2, aC), y0);  // corrector
+            sy[1][i] = yc;
+        }
+        __syncthreads();
+        if (lane == owner) {
+            double y[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) y[q] = sy[1][q];
+            fn = Rhs::template one<D>(i, y, p, ax);
+            const int64_t mm = m0 + 1 + s;
+            Yb[mm * D + i] = yc;
+            bt.F[mm * ldF + col] = fn;
+            if (!(finite_bits(yc) && finite_bits(fn))) report_nonfinite(bt.status, mm, b);
+        }
+        fk = __shfl_sync(0xffffffffu, fn, owner);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st)
+{
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((bt.B + threads - 1) / threads);
+    bool ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
+        init_kernel<R, D><<<blocks, threads, 0, st>>>(bt);
+    });
+    return ok ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
+                         int64_t c, int L, const double *G, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)bt.B;
+    bool ok = false;
+    if (L == kWarp) {
+        ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
+            recur_kernel<R, D, 1><<<blocks, D * kWarp, 0, st>>>(bt, w, k, c, G);
+        });
+    } else if (L == 2 * kWarp) {
+        ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
+            recur_kernel<R, D, 2><<<blocks, D * kWarp, 0, st>>>(bt, w, k, c, G);
+        });
+    }
+    return ok ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+}  // namespace fabm

@@ -7,66 +7,74 @@
 
 namespace fabm {
 
+// Interface of a right-hand side functor:
+//   aux(t, p)            the part of f that depends on t only (a forcing term,
+//                        or 0); evaluated once per grid point, off the serial
+//                        chain of the recurrence
+//   one<D>(i, y, p, aux) component i of f(t, y) given aux = aux(t, p)
+// Component-wise evaluation lets the recurrence run the components of one
+// trajectory on different warps.
+
 struct RhsConst {  // f_i = p0
+    __device__ static double aux(double, const double *p) { return p[0]; }
     template <int D>
-    __device__ static void eval(double, const double *, const double *p, double *f)
-    {
-#pragma unroll
-        for (int i = 0; i < D; ++i) f[i] = p[0];
-    }
+    __device__ static double one(int, const double *, const double *, double aux) { return aux; }
 };
 
 struct RhsTime {  // f_i = t
+    __device__ static double aux(double t, const double *) { return t; }
     template <int D>
-    __device__ static void eval(double t, const double *, const double *, double *f)
-    {
-#pragma unroll
-        for (int i = 0; i < D; ++i) f[i] = t;
-    }
+    __device__ static double one(int, const double *, const double *, double aux) { return aux; }
 };
 
 struct RhsLinear {  // f_i = -p0 y_i
+    __device__ static double aux(double, const double *) { return 0.0; }
     template <int D>
-    __device__ static void eval(double, const double *y, const double *p, double *f)
+    __device__ static double one(int i, const double *y, const double *p, double)
     {
-#pragma unroll
-        for (int i = 0; i < D; ++i) f[i] = -p[0] * y[i];
+        return -p[0] * y[i];
     }
 };
 
 struct RhsLorenz {  // p = (sigma, rho, beta)
+    __device__ static double aux(double, const double *) { return 0.0; }
     template <int D>
-    __device__ static void eval(double, const double *y, const double *p, double *f)
+    __device__ static double one(int i, const double *y, const double *p, double)
     {
-        f[0] = p[0] * (y[1] - y[0]);
-        f[1] = y[0] * (p[1] - y[2]) - y[1];
-        f[2] = y[0] * y[1] - p[2] * y[2];
+        if (i == 0) return p[0] * (y[1] - y[0]);
+        if (i == 1) return y[0] * (p[1] - y[2]) - y[1];
+        return y[0] * y[1] - p[2] * y[2];
     }
 };
 
 struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 + F cos(omega t)
+    __device__ static double aux(double t, const double *p) { return p[2] * cos(p[1] * t); }
     template <int D>
-    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    __device__ static double one(int i, const double *y, const double *p, double aux)
     {
+        if (i == 0) return y[1];
         const double x = y[0];
-        f[0] = y[1];
-        f[1] = p[2] * cos(p[1] * t) - (p[0] * y[1] + x * (1.0 + x * x));
+        return aux - (p[0] * y[1] + x * (1.0 + x * x));
     }
 };
 
 struct RhsManufactured {  // f = p0 t^p1 + t^2 - y
+    __device__ static double aux(double t, const double *p) { return p[0] * pow(t, p[1]) + t * t; }
     template <int D>
-    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    __device__ static double one(int, const double *y, const double *, double aux)
     {
-        f[0] = p[0] * pow(t, p[1]) + (t * t - y[0]);
+        return aux - y[0];
     }
 };
 
 struct RhsLcr {  // Sec. 5, Eq. sys.LRC; p = (sigma, omega, a, b, f)
+    __device__ static double aux(double t, const double *p) { return p[4] * sin(p[1] * t); }
     template <int D>
-    __device__ static void eval(double t, const double *y, const double *p, double *f)
+    __device__ static double one(int i, const double *y, const double *p, double aux)
     {
-        const double x = y[0], a = p[2], b = p[3];
+        const double x = y[0];
+        if (i == 1) return aux - (p[0] * y[1] + x);
+        const double a = p[2], b = p[3];
         double g;
         if (x <= -1.0)
             g = b * x - a + b;
@@ -74,8 +82,7 @@ struct RhsLcr {  // Sec. 5, Eq. sys.LRC; p = (sigma, omega, a, b, f)
             g = b * x + a - b;
         else
             g = a * x;
-        f[0] = y[1] - g;
-        f[1] = p[4] * sin(p[1] * t) - (p[0] * y[1] + x);
+        return y[1] - g;
     }
 };
 

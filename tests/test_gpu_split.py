@@ -1,0 +1,93 @@
+"""GPU parity of the split (tensor-core) path against the CPU oracle.
+
+The history sums run as bf16 tcgen05 products of fixed-point slices; the bar
+is the mixed-precision one: max_n |y_gpu - y_oracle| / S_i <= 1e-6, S_i the
+largest |y_oracle| of component i of the trajectory.  Sizes span several
+64-point segments, several 128-column tiles and ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from fabm_workloads import (duffing_sweep, lcr_sweep, lorenz_long, lorenz_single, ml_scalar,
+                            uniform, SEED_BASE)
+
+pytestmark = pytest.mark.gpu
+TOL_SPLIT = 1e-6
+
+
+def rel_err(got, ref):
+    ref = np.asarray(ref)
+    scale = np.max(np.abs(ref), axis=-2, keepdims=True)
+    scale = np.where(scale == 0, 1.0, scale)
+    return float(np.max(np.abs(np.asarray(got) - ref) / scale))
+
+
+@pytest.mark.parametrize("N", [1, 63, 64, 65, 128, 129, 193, 1000])
+def test_split_constant_rhs_closed_form(gpu_lib, N):
+    alpha, h = 0.7, 0.01
+    with gpu_lib.Solver("const", 1, alpha, h, N, [1.5], precision="split") as s:
+        y = s.solve([0.25])
+    t = np.arange(N + 1) * h
+    ex = 0.25 + 1.5 * t ** alpha / math.gamma(alpha + 1)
+    assert np.max(np.abs(y[:, 0] - ex)) / np.max(np.abs(ex)) < TOL_SPLIT
+
+
+def test_split_mittag_leffler(gpu_lib):
+    w = ml_scalar()
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        got = s.solve(w.y0[0])
+    ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    assert rel_err(got, ref) <= TOL_SPLIT
+
+
+def test_split_lorenz_prefix(gpu_lib):
+    w = lorenz_single(N=20_000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        got = s.solve(w.y0[0])
+    ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    assert rel_err(got, ref) <= TOL_SPLIT
+
+
+def test_split_duffing_batch_several_column_tiles(gpu_lib):
+    """300 trajectories x 2 = 600 columns: five 128-column tiles, the last one
+    ragged; uneven lengths."""
+    w = duffing_sweep(B=300, N=3000)
+    ne = np.full(w.B, w.N, dtype=np.int64)
+    ne[::7] = 1777
+    ne[3] = 1
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        got = s.solve_batch(w.y0, traj_params=w.traj_params, N_each=ne)
+    idx = np.r_[0:8, 150:154, 292:300]
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
+                             traj_params=w.traj_params[idx], N_each=ne[idx])
+    for j, b in enumerate(idx):
+        n = ne[b]
+        assert rel_err(got[b, : n + 1], ref[j, : n + 1]) <= TOL_SPLIT, b
+
+
+def test_split_matches_fp64_gpu_on_lcr(gpu_lib):
+    w = lcr_sweep(B=16, N=4000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        sp = s.solve_batch(w.y0, traj_params=w.traj_params)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
+        dp = s.solve_batch(w.y0, traj_params=w.traj_params)
+    assert rel_err(sp, dp) <= TOL_SPLIT
+
+
+def test_split_lorenz_long_subset(gpu_lib):
+    w = lorenz_long().subset(np.arange(4), N=50_000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        got = s.solve_batch(w.y0)
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0, params=w.params)
+    assert rel_err(got, ref) <= TOL_SPLIT
+
+
+def test_split_deterministic(gpu_lib):
+    w = lorenz_single(N=3000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        a = s.solve(w.y0[0])
+        b = s.solve(w.y0[0])
+    assert np.array_equal(a, b)
