@@ -131,6 +131,49 @@ def _profile_traffic(kernel_src: str, name: str):
     return float(m_tr.group(1)) if sha == m_sha.group(1) else None
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "of measured"
+    except (OSError, ValueError):
+        return 6800.0, 1900.0, "of fallback"
+
+
+def roofline(kind, ks, precision, clocks, w):
+    """Roofline line for the dominant kernel class from the library's sampled
+    CUDA-event stats: achieved = algorithmic work of the timed launches /
+    their total duration."""
+    n, ms, flops = ks["launches"], ks["ms"], ks["flops"]
+    avg_us = ms * 1e3 / max(n, 1)
+    hbm, bf16, src = _measured_peaks()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    out = {"kernel": f"{kind} ({precision})", "launches_timed": n, "avg_launch_us": avg_us}
+    if kind == "history" and precision == "split":
+        # 6 bf16 products per algorithmic multiply-add (three-term split, order <= 2)
+        achieved = 6.0 * flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        out.update({"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": achieved / bf16 if bf16 else None,
+                    "peak_note": f"dense bf16 burst {src} (MEASURED_PEAKS.json); achieved counts "
+                                 "the 6 bf16 products per algorithmic multiply-add"})
+    else:
+        peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
+        achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                    "frac": achieved / peak if peak else None,
+                    "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
+                                 "(probe: 1.19 TFLOP/s at 1.96 GHz)"})
+    src_file = {"history": "history_split.cu" if precision == "split" else "history_fp64.cu",
+                "recurrence": "recurrence.cu"}.get(kind)
+    traffic = None
+    if src_file:
+        traffic = _profile_traffic(os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", src_file),
+                                   f"{kind}_{precision}_{w.name}")
+    out["traffic"] = traffic
+    return out
+
+
 def cpu_baseline(w, target_s=12.0):
     """The oracle on a prefix of the workload (1 trajectory, or as many
     trajectories as the host has cores), extrapolated to the full workload by
@@ -216,8 +259,17 @@ def main():
     ap.add_argument("--workload", default="lorenz-single", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-steps", type=int, default=None,
+                    help="override the workload's N (small cases for profiling)")
+    ap.add_argument("--n-traj", type=int, default=None,
+                    help="keep only the first n trajectories of the workload")
+    ap.add_argument("--timing-period", type=int, default=16,
+                    help="time the kernel launches of every k-th time block")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]()
+    if args.n_steps is not None or args.n_traj is not None:
+        idx = np.arange(min(args.n_traj or w.B, w.B))
+        w = w.subset(idx, N=args.n_steps or w.N)
     if args.precision is None:
         args.precision = w.precision
     args.warmup = max(args.warmup, 3)
@@ -255,7 +307,7 @@ def main():
         solve_dev()
     barrier()
 
-    solver.set_timing(True)
+    solver.set_timing(args.timing_period)
     launches = 0
     times = []
     with ClockSampler(_gpu_index(local)) as clk:
@@ -271,7 +323,7 @@ def main():
             launches += solver.last_launch_count
     barrier()
     kstats = solver.kernel_stats()
-    solver.set_timing(False)
+    solver.set_timing(0)
     step_ms = float(np.mean(times))
     if ws > 1:
         t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
@@ -302,13 +354,9 @@ def main():
     if rank == 0:
         units = w.steps_traj() * ws
         clocks = clk.summary()
-        dom = max(("history", "recurrence", "combine", "init"), key=lambda k: kstats[k]["ms"])
-        ks = kstats[dom]
-        sm_max = clocks["sm_max_mhz"] or 2070.0
-        peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9  # GFLOP/s
-        achieved = ks["flops"] / (ks["ms"] * 1e-3) / 1e9 if ks["ms"] > 0 else 0.0
-        src = os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", "history_fp64.cu")
-        traffic = _profile_traffic(src, "history_fp64_lorenz") if dom == "history" else None
+        dom = max(("history", "recurrence", "combine", "slice", "init"),
+                  key=lambda k: kstats[k]["ms"])
+        line_roof = roofline(dom, kstats[dom], args.precision, clocks, w)
         h2d = w.B * w.dim * 8 + w.B * 8 * 8 + w.B * 8
         d2h = w.B * (w.N + 1) * w.dim * 8 + 8
         line = {
@@ -320,16 +368,11 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(w, args),
             "history_gmac_s": w.history_macs() * ws / (step_ms * 1e-3) / 1e9,
-            "roofline": {
-                "kernel": f"{dom} ({args.precision})", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak if peak else None,
-                "traffic": (traffic / ks["launches"] if traffic and ks["launches"] else None),
-                "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
-                             "(measured 1.19 TFLOP/s at 1.96 GHz)",
-                "launches": ks["launches"], "avg_launch_us": ks["ms"] * 1e3 / max(ks["launches"], 1),
-            },
-            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+            "roofline": line_roof,
+            "kernels": {k: {"timed_launches": v["launches"], "ms": round(v["ms"], 3)}
                         for k, v in kstats.items() if k != "weights"},
+            "kernel_timing": f"CUDA events around the launches of every "
+                             f"{args.timing_period}th time block, inside the timed region",
             "weights_ms": wstats["ms"],
             "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "steps*traj/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -147,14 +147,16 @@ enum {
     FABM_KERNEL_KINDS = 6
 };
 
-/* Enable (1) or disable (0) per-launch timing: with timing on, every launch
- * is bracketed by CUDA events recorded on the stream it runs on, and the
- * elapsed times are added up when the solve call returns.  Enabling resets
- * the counters. */
-fabm_status fabm_set_timing(fabm_solver *s, int enable);
+/* Per-launch timing.  period > 0 enables it: the launches of every period-th
+ * time block (and the initial launch) are bracketed by CUDA events recorded on
+ * the stream they run on, and the elapsed times are added up when the solve
+ * call returns; period = 1 times every launch, a larger period samples the
+ * blocks uniformly and keeps the event overhead small.  period = 0 disables
+ * it.  Enabling resets the counters. */
+fabm_status fabm_set_timing(fabm_solver *s, int period);
 
-/* Counters since timing was enabled, for one kernel class:
- *   launches  number of launches
+/* Counters since timing was enabled, for one kernel class (timed launches only):
+ *   launches  number of timed launches
  *   total_ms  sum of their CUDA-event durations
  *   flops     algorithmic floating-point operations they performed (2 per
  *             multiply-add of a history term; 0 for classes with no history

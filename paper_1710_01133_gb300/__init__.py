@@ -138,8 +138,8 @@ def fabm_set_graphs(handle, enable: bool):
     _check(load().fabm_set_graphs(handle, int(bool(enable))))
 
 
-def fabm_set_timing(handle, enable: bool):
-    _check(load().fabm_set_timing(handle, int(bool(enable))))
+def fabm_set_timing(handle, period):
+    _check(load().fabm_set_timing(handle, int(period)))
 
 
 def fabm_kernel_stats(handle, kind):
@@ -200,8 +200,9 @@ class Solver:
     def set_graphs(self, enable: bool = True):
         fabm_set_graphs(self.handle, enable)
 
-    def set_timing(self, enable: bool = True):
-        fabm_set_timing(self.handle, enable)
+    def set_timing(self, period: int = 1):
+        """period > 0: time the launches of every period-th block; 0: off."""
+        fabm_set_timing(self.handle, int(period))
 
     def kernel_stats(self) -> dict:
         return {k: dict(zip(("launches", "ms", "flops"), fabm_kernel_stats(self.handle, k)))

@@ -110,6 +110,8 @@ struct fabm_solver {
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
     bool timing = false;
+    int timing_period = 1;    // time the launches of every k-th block
+    bool sample_now = true;   // the block being enqueued is timed
     bool capturing = false;
     std::vector<cudaEvent_t> ev_pool;  // pairs (start, stop)
     struct Rec {
@@ -195,7 +197,7 @@ template <class Fn>
 cudaError_t timed_launch(fabm_solver *s, int kind, cudaStream_t st, double flops, Fn &&launch)
 {
     ++s->launches;
-    if (!s->timing) return launch();
+    if (!s->timing || !s->sample_now) return launch();
     const size_t pair = s->recs.size();
     while (s->ev_pool.size() < 2 * (pair + 1)) {
         cudaEvent_t e;
@@ -238,9 +240,11 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
     const int L = s->L;
     const int64_t cols = bt.cols;
     const bool split = s->precision == FABM_SPLIT;
+    s->sample_now = true;
     FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
                                [&] { return launch_init(s->rhs, bt, s->sR); }));
     for (int64_t c = 0; c < nblk; ++c) {
+        s->sample_now = (c % s->timing_period) == 0;
         const double *Gc = nullptr;
         if (c >= 2) {
             double *Gbuf = s->G.p + (size_t)(c % 2) * 2 * L * cols;
@@ -286,6 +290,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
         }
         FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
     }
+    s->sample_now = true;
     return FABM_OK;
 }
 
@@ -368,7 +373,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     DevWeights w{s->wB.p, s->wA.p, s->wD.p, s->w_ext};
 
     const std::vector<uintptr_t> key = {
-        (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing, (uintptr_t)Y,
+        (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
+        (uintptr_t)s->timing_period, (uintptr_t)Y,
         (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p};
@@ -632,7 +638,8 @@ fabm_status fabm_set_timing(fabm_solver *s, int enable)
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
-    s->timing = enable != 0;
+    s->timing = enable > 0;
+    s->timing_period = enable > 0 ? enable : 1;
     if (s->timing)
         for (int k = 0; k < FABM_KERNEL_KINDS; ++k)
             if (k != FABM_KERNEL_WEIGHTS) s->k_launches[k] = 0, s->k_ms[k] = 0, s->k_flops[k] = 0;

@@ -299,23 +299,34 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
         for (int t = 0; t < kEpiT; ++t) sum[t] = 0.f;
 #pragma unroll
         for (int t = 0; t < kEpiT / 2; ++t) cmp2[t] = 0u;
+        // exponents of the first segment; later ones are fetched a segment ahead
+        int ef_next = a.Ef[((int64_t)s_lo * a.n_ct + ct) * kMC + cloc];
+        int ew_next = a.Ew[(a.c - s_lo) * 2 + kind];
         for (int i = 0; i < nseg; ++i) {
             const int b = i & 1;
             const uint32_t bph = (i >> 1) & 1;
+            const float scale = pow2f(ef_next + ew_next - 16);
+            if (i + 1 < nseg) {
+                const int64_t sn = s_lo + i + 1;
+                ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
+                ew_next = a.Ew[(a.c - sn) * 2 + kind];
+            }
             if (!mbar_wait(&acc_full[b], bph, kWaitCycles)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const int64_t seg = s_lo + i;
-            const int ef = a.Ef[(seg * a.n_ct + ct) * kMC + cloc];
-            const int ew = a.Ew[(a.c - seg) * 2 + kind];
-            const float scale = pow2f(ef + ew - 16);
             const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + kind * 64 + t0;
+            // software pipeline over 8 pieces of 8 targets: the load of piece
+            // p+1 is in flight while piece p is added
+            uint32_t ra[16], rb[16];
+            tmem_ld8x2_issue(base, base + 128, ra);
+            tmem_wait16(ra);
 #pragma unroll
             for (int p = 0; p < kEpiT / 8; ++p) {
-                float v0[8], v1[8];
-                tmem_ld8x2(base + p * 8, base + 128 + p * 8, v0, v1);
+                uint32_t(&cur)[16] = (p % 2 == 0) ? ra : rb;
+                uint32_t(&nxt)[16] = (p % 2 == 0) ? rb : ra;
+                if (p + 1 < kEpiT / 8) tmem_ld8x2_issue(base + (p + 1) * 8, base + 128 + (p + 1) * 8, nxt);
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                     const int t = p * 8 + j;
@@ -324,7 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const float c = __uint_as_float(u ? (cw & 0xffff0000u) : (cw << 16));
-                        const float y = (v0[j + u] + v1[j + u]) * scale - c;
+                        const float v = __uint_as_float(cur[j + u]) + __uint_as_float(cur[8 + j + u]);
+                        const float y = v * scale - c;
                         const float s2 = sum[t + u] + y;
                         cnew[u] = (s2 - sum[t + u]) - y;
                         sum[t + u] = s2;
@@ -332,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                     __nv_bfloat162 pk = __floats2bfloat162_rn(cnew[0], cnew[1]);
                     cmp2[t / 2] = *reinterpret_cast<uint32_t *>(&pk);
                 }
+                if (p + 1 < kEpiT / 8) tmem_wait16(nxt);
             }
             tc_fence_before();
             __syncwarp();

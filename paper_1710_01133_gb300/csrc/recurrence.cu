@@ -12,6 +12,10 @@
 //           target adds its term, and the owner of target k+1 then has the
 //           whole sum and runs the step: y^P_i, exchange of y^P across the
 //           component warps, f_i(t, y^P), y_i, exchange of y, f_i(t, y).
+// The accumulators hold y0 + h^alpha * (partial sum) and the weights are
+// pre-multiplied by h^alpha, so the owner's accumulate of the newest point is
+// already y^P (and y0 + h^alpha S^C): six dependent FP64 operations per step
+// for a Lorenz-type component (accumulate, f, corrector, f).
 // GB300 runs a double-precision warp instruction in one 64-cycle slot of its
 // sub-partition's FP64 unit whatever the number of active lanes, so one warp
 // per component spreads the serial chain over the FP64 units of several
@@ -61,41 +65,51 @@ __global__ void __launch_bounds__(D *kWarp)
     recur_kernel(DevBatch bt, DevWeights w, StepConsts kc, int64_t c, const double *G)
 {
     constexpr int L = kWarp * TPL;
+    // weights pre-multiplied by h^alpha: the accumulators hold y0 + h^alpha * sum,
+    // so adding the newest point to the owner's accumulator yields y^P directly
     __shared__ double sB[2 * L + 1], sA[2 * L + 1];
-    __shared__ double sy[2][D];  // y^P and y of the current step, all components
-    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
-        sB[j] = w.B[j];
-        sA[j] = w.A[j];
-    }
+    __shared__ double sy[2][D];      // y^P and y of the current step, all components
+    __shared__ double sF[L + 1][D];  // f of the lag-1 block and f_{m0}
     const int b = blockIdx.x;
     const int i = threadIdx.x / kWarp;  // component of this warp
     const int lane = threadIdx.x % kWarp;
     const int64_t Nb = bt.N_each[b];
     const int64_t m0 = c * L;  // f_{m0} is the newest known point
+    if (m0 >= Nb) return;      // trajectory finished (uniform over the CTA)
+    const double ha = kc.h_alpha;
+    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
+        sB[j] = ha * w.B[j];
+        sA[j] = ha * w.A[j];
+    }
+    // rows m0-L .. m0 of this trajectory's history, all loads in flight at once
+    for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
+        const int64_t row = m0 - L + j / D;
+        sF[j / D][j % D] = row >= 0 ? bt.F[row * bt.ldF + (int64_t)b * D + j % D] : 0.0;
+    }
     __syncthreads();
-    if (m0 >= Nb) return;  // trajectory finished (uniform over the CTA)
 
     double p[kMaxParams];
 #pragma unroll
     for (int q = 0; q < kMaxParams; ++q) p[q] = bt.params[(int64_t)b * kMaxParams + q];
     const double y0 = bt.y0[(int64_t)b * D + i];
     const int64_t col = (int64_t)b * D + i;
-    const int64_t ldF = bt.ldF;
-    const double *F = bt.F;
+    const double ha_ig2 = ha * kc.inv_gamma2;
 
     double accP[TPL], accC[TPL], aux[TPL];
-    const double f0 = F[col];
+    const double f0 = bt.F[col];
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
         const int a = lane + kWarp * t;
         const int64_t m = m0 + 1 + a;
         aux[t] = Rhs::aux((double)m * kc.h, p);
-        accP[t] = G ? G[(int64_t)a * bt.cols + col] : 0.0;
-        accC[t] = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+        const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
+        const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+        accP[t] = fma(ha, gP, y0);
+        accC[t] = fma(ha, gC, y0);
     }
     if (c >= 1) {  // lag-1 block: k = m0-L+j, d = m-k = L+1+a-j in [2, 2L]
         for (int j = 0; j < L; ++j) {
-            const double fk = F[(m0 - L + j) * ldF + col];
+            const double fk = sF[j][i];
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
                 const int d = L + 1 + lane + kWarp * t - j;
@@ -105,42 +119,54 @@ __global__ void __launch_bounds__(D *kWarp)
         }
     }
 
-    double fk = F[m0 * ldF + col];
+    double fk = sF[L][i];
     const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
     double *Yb = bt.Y + (int64_t)b * (bt.N + 1) * D;
     for (int s = 0; s < steps; ++s) {
+        // add the newest point k = m0+s; for the owner of target k+1 this
+        // completes y^P (accP) and y0 + h^a S^C (accC)
 #pragma unroll
         for (int t = 0; t < TPL; ++t) {
-            const int d = lane + kWarp * t - s + 1;  // distance from k = m0+s
-            const int dd = d > 0 ? d : 0;            // done targets add B(0) = A(0) = 0
+            const int d = lane + kWarp * t - s + 1;
+            const int dd = d > 0 ? d : 0;  // done targets add B(0) = A(0) = 0
             accP[t] = fma(sB[dd], fk, accP[t]);
             accC[t] = fma(sA[dd], fk, accC[t]);
         }
         const int owner = s % kWarp, slot = s / kWarp;  // uniform over the CTA
-        double aP = 0.0, aC = 0.0, ax = 0.0;
+        double yp = 0.0, aC = 0.0, ax = 0.0;
 #pragma unroll
         for (int t = 0; t < TPL; ++t)
-            if (t == slot) aP = accP[t], aC = accC[t], ax = aux[t];
+            if (t == slot) yp = accP[t], aC = accC[t], ax = aux[t];
         double fn = 0.0, yc = 0.0;
-        if (lane == owner) sy[0][i] = fma(kc.h_alpha, aP, y0);  // predictor
-        __syncthreads();
-        if (lane == owner) {
-            double y[D];
+        if constexpr (D == 1) {
+            if (lane == owner) {
+                const double fp = Rhs::template one<D>(0, &yp, p, ax);
+                yc = fma(ha_ig2, fp, aC);
+                fn = Rhs::template one<D>(0, &yc, p, ax);
+            }
+        } else {
+            if (lane == owner) sy[0][i] = yp;
+            __syncthreads();
+            if (lane == owner) {
+                double y[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) y[q] = sy[0][q];
-            const double fp = Rhs::template one<D>(i, y, p, ax);
-            yc = fma(kc.h_alpha, fma(fp, kc.inv_gamma2, aC), y0);  // corrector
-            sy[1][i] = yc;
+                for (int q = 0; q < D; ++q) y[q] = sy[0][q];
+                const double fp = Rhs::template one<D>(i, y, p, ax);
+                yc = fma(ha_ig2, fp, aC);  // corrector
+                sy[1][i] = yc;
+            }
+            __syncthreads();
+            if (lane == owner) {
+                double y[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) y[q] = sy[1][q];
+                fn = Rhs::template one<D>(i, y, p, ax);
+            }
         }
-        __syncthreads();
         if (lane == owner) {
-            double y[D];
-#pragma unroll
-            for (int q = 0; q < D; ++q) y[q] = sy[1][q];
-            fn = Rhs::template one<D>(i, y, p, ax);
             const int64_t mm = m0 + 1 + s;
             Yb[mm * D + i] = yc;
-            bt.F[mm * ldF + col] = fn;
+            bt.F[mm * bt.ldF + col] = fn;
             if (!(finite_bits(yc) && finite_bits(fn))) report_nonfinite(bt.status, mm, b);
         }
         fk = __shfl_sync(0xffffffffu, fn, owner);

@@ -163,5 +163,25 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t ta0, uint32_t ta1, float (&v
     }
 }
 
+// Issue two loads of 32 lanes x 8 consecutive 32-bit columns into r[0..7] and
+// r[8..15].  The registers are written asynchronously: they must not be read
+// (or copied) before tmem_wait16(r).
+__device__ __forceinline__ void tmem_ld8x2_issue(uint32_t ta0, uint32_t ta1, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta0), "r"(ta1)
+        : "memory");
+}
+
+// Wait for every tcgen05.ld this thread issued; r is passed through so that
+// its uses are ordered after the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]) : : "memory");
+}
+
 }  // namespace ptx
 }  // namespace fabm
