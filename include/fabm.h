@@ -164,6 +164,27 @@ fabm_status fabm_set_timing(fabm_solver *s, int period);
 fabm_status fabm_kernel_stats(const fabm_solver *s, int kind, int64_t *launches, double *total_ms,
                               double *flops);
 
+/* One FP64 trajectory (as fabm_solve with precision FABM_FP64) without any
+ * device allocation, for callers that cannot allocate device memory when they
+ * solve: a framework's caching allocator may own the whole device-memory
+ * budget, cudaMalloc/cudaFree synchronize the device, or the host process may
+ * forbid a plug-in allocations of its own.  The paper has no counterpart; it
+ * is a deployment variant of the same kernels.
+ *   dim, alpha, h, N, rhs_id, params, n_params  as for fabm_create
+ *                                                (N <= 65536, dim <= FABM_MAX_DIM)
+ *   y0   dim doubles, host;  out  (N+1) x dim doubles, host, row n = y_n
+ * All device buffers (weights, history, split-k partials) live in one static
+ * device array of about 7 MB that every GPU loading the library holds until
+ * the process exits.  Calls share that array and keep the last call's data;
+ * calls are serialized by a host mutex, and work overlapping on the GPU with
+ * another user of the array would race.  The first call on a device looks up
+ * the array's device address with that device current: make it before any
+ * stream capture.  Runs on the calling thread's default stream; synchronous.
+ * Errors: FABM_EINVAL (incl. N or dim beyond the array's limits, with a
+ * message saying so), FABM_ECUDA, FABM_ENONFINITE. */
+fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64_t N, int rhs_id,
+                               const double *params, int n_params, const double *y0, double *out);
+
 #ifdef __cplusplus
 }
 #endif

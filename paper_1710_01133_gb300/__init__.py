@@ -21,7 +21,8 @@ RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactu
 PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
 _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_last_error", "fabm_set_block", "fabm_get_block", "fabm_last_launch_count",
-            "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs")
+            "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
+            "fabm_solve_noalloc")
 KERNEL_KINDS = ("weights", "init", "history", "combine", "recurrence", "slice")
 
 _lib = None
@@ -63,9 +64,11 @@ def load(build_if_missing: bool = True):
     lib.fabm_copy_weights.argtypes = [vp, i64, P(d), P(d), P(d)]
     lib.fabm_set_timing.argtypes = [vp, i]
     lib.fabm_set_graphs.argtypes = [vp, i]
+    lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
-              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs"):
+              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
+            "fabm_solve_noalloc"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -132,6 +135,16 @@ def fabm_copy_weights(handle, n):
 
 def fabm_last_launch_count(handle) -> int:
     return load().fabm_last_launch_count(handle)
+
+
+def fabm_solve_noalloc(dim, alpha, h, N, rhs_id, params, y0, out):
+    """One FP64 trajectory without device allocation (see include/fabm.h);
+    out: host float64 array of (N+1) x dim entries."""
+    p = _f64(params if params is not None else []).reshape(-1)
+    y0 = _f64(y0).reshape(-1)
+    _check(load().fabm_solve_noalloc(int(dim), float(alpha), float(h), int(N), int(rhs_id),
+                                     _dp(p) if p.size else None, int(p.size), _dp(y0),
+                                     _dp(out)))
 
 
 def fabm_set_graphs(handle, enable: bool):

@@ -79,6 +79,8 @@ constexpr int kEvRing = 4;
 
 }  // namespace
 
+void fabm::set_last_error(const char *msg) { g_last_error = msg; }
+
 struct fabm_solver {
     int device = 0;
     int dim = 0;

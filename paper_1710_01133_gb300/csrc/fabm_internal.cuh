@@ -82,6 +82,9 @@ cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
                          int64_t c, int L, const double *G, cudaStream_t st);
 
+// Message returned by fabm_last_error() on the calling thread.
+void set_last_error(const char *msg);
+
 // ---- split path (history on tensor cores) ----
 
 // f of segment seg (64 points) -> bf16 slices Fs and per-column exponents Ef.
