@@ -29,6 +29,7 @@
 #ifndef FABM_H
 #define FABM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -51,10 +52,11 @@ typedef enum {
 /* Arithmetic of the history sums. */
 enum {
     FABM_FP64 = 0,  /* every step in IEEE double                                   */
-    FABM_SPLIT = 1  /* history sums on tensor cores from a three-term bf16 split of
-                       f and of the weights; the weights, the per-step predictor and
-                       corrector updates and the running history accumulator stay in
-                       double */
+    FABM_SPLIT = 1  /* history sums in compensated reduced precision: three-term bf16
+                       split on tensor cores (wide batches) or compensated fp32 on
+                       CUDA cores (narrow batches); the weights, the per-step
+                       predictor and corrector updates and the running history
+                       accumulator stay in double */
 };
 
 /* Right-hand sides f(t, y) (params in this order; dim as stated). */
@@ -113,9 +115,26 @@ fabm_status fabm_destroy(fabm_solver *s);
 /* Message of the last failed call on this thread ("" if none). */
 const char *fabm_last_error(void);
 
-/* Time-block length L (targets per block; a multiple of 32, 32..1024).  Blocks
- * of L steps are the unit of the history kernels; it changes the order of
- * summation only.  Default chosen per precision; fabm_autotune picks one. */
+/* History kernels (fabm_set_history_kernel). */
+enum {
+    FABM_HIST_AUTO = 0,    /* FP64 precision: FABM_HIST_FP64; split precision: tensor
+                              cores for batches of at least 64 columns, else FP32C   */
+    FABM_HIST_FP64 = 1,    /* double on CUDA cores (FP64 precision only)             */
+    FABM_HIST_TENSOR = 2,  /* three-term bf16 split on tcgen05 tensor cores, exact
+                              per 64-point segment (split precision)                  */
+    FABM_HIST_FP32C = 3    /* compensated fp32 on CUDA cores (split precision)       */
+};
+
+/* Choose the history kernel (one of FABM_HIST_*; must fit the precision).
+ * The block length follows from it: 64 targets for FABM_HIST_TENSOR, 32
+ * otherwise.  fabm_autotune measures the candidates and sets the fastest. */
+fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel);
+int fabm_get_history_kernel(const fabm_solver *s);
+
+/* Time-block length L of the last solve (or of the current choice before any
+ * solve).  fabm_set_block accepts only the length of an allowed history
+ * kernel (32 or 64) and selects that kernel; it changes the order of summation
+ * only. */
 fabm_status fabm_set_block(fabm_solver *s, int L);
 int fabm_get_block(const fabm_solver *s);
 
@@ -163,6 +182,54 @@ fabm_status fabm_set_timing(fabm_solver *s, int period);
  *             terms).  Any output pointer may be NULL. */
 fabm_status fabm_kernel_stats(const fabm_solver *s, int kind, int64_t *launches, double *total_ms,
                               double *flops);
+
+/* ------------------------------------------------------------ serving ---
+ * A continuous-batching server for independent solves that differ in right-
+ * hand side, dim, alpha, h and N.  Requests wait in arrival order and are
+ * admitted while the device memory they need (weights, history, output,
+ * partial sums: about (5 dim + 3) x 8 x N bytes) fits in the budget.  Each
+ * fabm_server_step advances every admitted request by one block of 32 steps
+ * with launches shared by all of them (the history of each request's next
+ * block beside the recurrence of its current block), frees finished requests
+ * and admits waiting ones.  A request's result does not depend on the other
+ * requests in flight.  Precision FABM_FP64 sums the history in double,
+ * FABM_SPLIT in compensated fp32 (requests have few columns, so tensor tiles
+ * would be mostly padding); per-step updates and accumulators are double in
+ * both.  Calls on one server are serialized by a mutex. */
+typedef struct fabm_server fabm_server;
+
+typedef struct {
+    int dim;               /* 1..FABM_MAX_DIM, matching rhs_id */
+    double alpha;          /* 0 < alpha < 1 */
+    double h;              /* step size > 0 */
+    int64_t N;             /* steps, 1..2^31 */
+    int rhs_id;            /* FABM_RHS_* */
+    const double *params;  /* n_params doubles, copied at submission */
+    int n_params;
+    const double *y0;      /* dim doubles, copied at submission */
+} fabm_request;
+
+enum { FABM_REQ_WAITING = 0, FABM_REQ_RUNNING = 1, FABM_REQ_DONE = 2, FABM_REQ_FAILED = 3 };
+
+/* budget_bytes: device memory the admitted requests may hold together;
+ * max_slots: most requests in flight at once. */
+fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots,
+                               fabm_server **out);
+/* Queue a request (copied); *ticket identifies it. */
+fabm_status fabm_server_submit(fabm_server *s, const fabm_request *req, int64_t *ticket);
+/* One scheduling step (synchronous): admit, advance all admitted requests by
+ * one block, retire finished ones.  Reports the requests in flight and waiting. */
+fabm_status fabm_server_step(fabm_server *s, int *n_active, int *n_waiting);
+/* State of a request: FABM_REQ_*. */
+fabm_status fabm_server_poll(fabm_server *s, int64_t ticket, int *state);
+/* Copy a finished request's y_0..y_N ((N+1) x dim doubles, host) and forget it.
+ * FABM_EBUSY if it has not finished; the request's own error if it failed
+ * (FABM_ENONFINITE, or FABM_ENOMEM when it can never fit the budget). */
+fabm_status fabm_server_result(fabm_server *s, int64_t ticket, double *out);
+/* Steps run, kernel launches made, device bytes held by admitted requests. */
+fabm_status fabm_server_stats(const fabm_server *s, int64_t *steps, int64_t *launches,
+                              size_t *bytes_in_use);
+fabm_status fabm_server_destroy(fabm_server *s);
 
 /* One FP64 trajectory (as fabm_solve with precision FABM_FP64) without any
  * device allocation, for callers that cannot allocate device memory when they

@@ -16,13 +16,25 @@ from . import build as _build
 
 FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, FABM_EBUSY = range(7)
 FABM_FP64, FABM_SPLIT = 0, 1
+FABM_HIST_AUTO, FABM_HIST_FP64, FABM_HIST_TENSOR, FABM_HIST_FP32C = range(4)
+HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3}
 RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
        "lcr": 6}
 PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
 _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_last_error", "fabm_set_block", "fabm_get_block", "fabm_last_launch_count",
             "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
-            "fabm_solve_noalloc")
+            "fabm_solve_noalloc", "fabm_set_history_kernel", "fabm_get_history_kernel",
+            "fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
+            "fabm_server_result", "fabm_server_stats", "fabm_server_destroy")
+FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
+
+
+class fabm_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("alpha", ctypes.c_double), ("h", ctypes.c_double),
+                ("N", ctypes.c_int64), ("rhs_id", ctypes.c_int),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("n_params", ctypes.c_int),
+                ("y0", ctypes.POINTER(ctypes.c_double))]
 KERNEL_KINDS = ("weights", "init", "history", "combine", "recurrence", "slice")
 
 _lib = None
@@ -64,11 +76,24 @@ def load(build_if_missing: bool = True):
     lib.fabm_copy_weights.argtypes = [vp, i64, P(d), P(d), P(d)]
     lib.fabm_set_timing.argtypes = [vp, i]
     lib.fabm_set_graphs.argtypes = [vp, i]
+    lib.fabm_server_create.argtypes = [ctypes.c_size_t, i, i, P(vp)]
+    lib.fabm_server_submit.argtypes = [vp, P(fabm_request), P(i64)]
+    lib.fabm_server_step.argtypes = [vp, P(i), P(i)]
+    lib.fabm_server_poll.argtypes = [vp, i64, P(i)]
+    lib.fabm_server_result.argtypes = [vp, i64, P(d)]
+    lib.fabm_server_stats.argtypes = [vp, P(i64), P(i64), P(ctypes.c_size_t)]
+    lib.fabm_server_destroy.argtypes = [vp]
+    for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
+              "fabm_server_result", "fabm_server_stats", "fabm_server_destroy"):
+        getattr(lib, f).restype = i
+    lib.fabm_set_history_kernel.argtypes = [vp, i]
+    lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
-              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
-            "fabm_solve_noalloc"):
+              "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
+              "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
+              "fabm_get_history_kernel"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -147,6 +172,15 @@ def fabm_solve_noalloc(dim, alpha, h, N, rhs_id, params, y0, out):
                                      _dp(out)))
 
 
+def fabm_set_history_kernel(handle, kernel):
+    k = HIST[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(load().fabm_set_history_kernel(handle, k))
+
+
+def fabm_get_history_kernel(handle) -> int:
+    return load().fabm_get_history_kernel(handle)
+
+
 def fabm_set_graphs(handle, enable: bool):
     _check(load().fabm_set_graphs(handle, int(bool(enable))))
 
@@ -169,7 +203,8 @@ def fabm_kernel_stats(handle, kind):
 class Solver:
     """Owns one fabm_solver.  ``rhs`` and ``precision`` are names or ids."""
 
-    def __init__(self, rhs, dim, alpha, h, N, params=None, precision="fp64", block=None):
+    def __init__(self, rhs, dim, alpha, h, N, params=None, precision="fp64", block=None,
+                 history=None):
         self.rhs = RHS[rhs] if isinstance(rhs, str) else int(rhs)
         self.dim, self.alpha, self.h, self.N = int(dim), float(alpha), float(h), int(N)
         self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -177,6 +212,8 @@ class Solver:
         self.handle = fabm_create(dim, alpha, h, N, self.rhs, self.params, self.precision)
         if block is not None:
             fabm_set_block(self.handle, block)
+        if history is not None:
+            fabm_set_history_kernel(self.handle, history)
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -253,3 +290,68 @@ class Solver:
             on_dev = 1 if out.is_cuda else 0
         fabm_solve_batch(self.handle, B, y0, tp, ne, ptr, on_dev)
         return out
+
+
+class Server:
+    """Owns one fabm_server (continuous batching of independent solves)."""
+
+    def __init__(self, budget_bytes, precision="fp64", max_slots=4096):
+        self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _check(load().fabm_server_create(int(budget_bytes), self.precision, int(max_slots),
+                                         ctypes.byref(h)))
+        self.handle = h
+        self._dims = {}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(load().fabm_server_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, rhs, dim, alpha, h, N, y0, params=None) -> int:
+        rid = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+        p = _f64(params if params is not None else []).reshape(-1)
+        y = _f64(y0).reshape(-1)
+        req = fabm_request(int(dim), float(alpha), float(h), int(N), rid,
+                           _dp(p) if p.size else None, int(p.size), _dp(y))
+        t = ctypes.c_int64()
+        _check(load().fabm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._dims[t.value] = (int(N), int(dim))
+        return t.value
+
+    def step(self):
+        a, w = ctypes.c_int(), ctypes.c_int()
+        _check(load().fabm_server_step(self.handle, ctypes.byref(a), ctypes.byref(w)))
+        return a.value, w.value
+
+    def poll(self, ticket) -> int:
+        st = ctypes.c_int()
+        _check(load().fabm_server_poll(self.handle, int(ticket), ctypes.byref(st)))
+        return st.value
+
+    def result(self, ticket) -> np.ndarray:
+        N, dim = self._dims[ticket]
+        out = np.empty((N + 1, dim))
+        st = load().fabm_server_result(self.handle, int(ticket), _dp(out))
+        if st != FABM_EBUSY:
+            self._dims.pop(ticket, None)
+        _check(st)
+        return out
+
+    def stats(self):
+        s, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(load().fabm_server_stats(self.handle, ctypes.byref(s), ctypes.byref(l),
+                                        ctypes.byref(b)))
+        return {"steps": s.value, "launches": l.value, "bytes_in_use": b.value}

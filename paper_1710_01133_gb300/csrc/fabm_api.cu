@@ -90,11 +90,14 @@ struct fabm_solver {
     int n_params = 0;
     double params[kMaxParams] = {};
     int precision = FABM_FP64;
-    int L = kRecurL;
+    int hist_kernel = FABM_HIST_AUTO;  // requested
+    int L = kRecurL;                   // block length of the last solve
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
     DevBuf<double> wB, wA, wD;
-    // split path: Hankel weight tiles per lag, their exponents
+    // split path: fp32 weights (narrow kernel), Hankel weight tiles per lag and
+    // their exponents (tensor kernel)
+    DevBuf<float> wBf, wAf;
     DevBuf<__nv_bfloat16> wH;
     DevBuf<int> wHe;
     int64_t g_max = 0;
@@ -134,6 +137,7 @@ struct fabm_solver {
     ~fabm_solver()
     {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
+        wBf.release(), wAf.release();
         F.release(), Ystage.release(), G.release(), part.release();
         Fs.release(), Fe.release(), spart.release(), err.release();
         y0.release(), par.release(), nEach.release(), status.release();
@@ -232,16 +236,25 @@ cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &
     return cudaSuccess;
 }
 
+// History kernel for a batch of `cols` columns.
+int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
+{
+    if (s->precision == FABM_FP64) return FABM_HIST_FP64;
+    if (s->hist_kernel == FABM_HIST_TENSOR || s->hist_kernel == FABM_HIST_FP32C)
+        return s->hist_kernel;
+    return cols >= 64 ? FABM_HIST_TENSOR : FABM_HIST_FP32C;
+}
+
 // Enqueues one solve on the solver's two streams (or records it into the
 // graph being captured): init, then per block the far history on stream G and
 // the recurrence (and, split path, the slicing of the finished segment) on
 // stream R.
 fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &w, int64_t nblk,
-                          int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks)
+                          int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks, int hk)
 {
     const int L = s->L;
     const int64_t cols = bt.cols;
-    const bool split = s->precision == FABM_SPLIT;
+    const bool split = hk == FABM_HIST_TENSOR;
     s->sample_now = true;
     FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
                                [&] { return launch_init(s->rhs, bt, s->sR); }));
@@ -263,7 +276,16 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                                              (int)cols, n_chunks, s->spart.p, s->err.p, s->sG);
                 }));
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
-                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, Gbuf, s->sG);
+                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
+                }));
+            } else if (hk == FABM_HIST_FP32C) {
+                plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                    return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, c, n_chunks, kc, s->spart.p,
+                                             s->sG);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
+                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
                 }));
             } else {
                 plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
@@ -302,7 +324,9 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int dim = s->dim;
     const int64_t cols = B * dim;
     const int64_t N = s->N;
-    const int L = s->L;
+    const int hk = resolve_hist_kernel(s, cols);
+    const int L = hk == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    s->L = L;
     s->launches = 0;
 
     // host-side inputs: per-trajectory steps and parameter rows
@@ -324,7 +348,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     for (int64_t i = 0; i < B * dim; ++i)
         if (!std::isfinite(y0[i])) return fail(FABM_EINVAL, "y0[%lld] is not finite", (long long)i);
 
-    const bool split = s->precision == FABM_SPLIT;
+    const bool split = hk == FABM_HIST_TENSOR;
     // workspace
     const int64_t nblk = (Nmax + L - 1) / L;
     const size_t f_elems = (size_t)(N + 1) * cols;
@@ -333,7 +357,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     max_chunks = std::min<int64_t>(max_chunks, 4096);
     FABM_CUDA_TRY(s->F.ensure(f_elems));
     FABM_CUDA_TRY(s->G.ensure((size_t)2 * 2 * L * cols));
-    FABM_CUDA_TRY(s->part.ensure((size_t)max_chunks * part_per_chunk));
+    if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)max_chunks * part_per_chunk));
+    if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)max_chunks * part_per_chunk));
     FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim));
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
@@ -376,12 +401,12 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
 
     const std::vector<uintptr_t> key = {
         (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
-        (uintptr_t)s->timing_period, (uintptr_t)Y,
+        (uintptr_t)s->timing_period, (uintptr_t)hk, (uintptr_t)Y,
         (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p};
     auto enqueue = [&]() -> fabm_status {
-        return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks);
+        return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk);
     };
     if (!s->use_graphs) {
         s->recs.clear();
@@ -431,7 +456,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
 
     unsigned long long st = 0;
     FABM_CUDA_TRY(cudaMemcpy(&st, s->status.p, sizeof st, cudaMemcpyDeviceToHost));
-    if (split) {
+    if (split) {  // tensor kernel's bounded waits
         unsigned int tout = 0;
         FABM_CUDA_TRY(cudaMemcpy(&tout, s->err.p, sizeof tout, cudaMemcpyDeviceToHost));
         if (tout) return fail(FABM_ETIMEOUT, "a history kernel gave up waiting on a barrier");
@@ -535,7 +560,11 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     }
     if (e == cudaSuccess && precision == FABM_SPLIT) {
         s->L = kSplitSeg;
-        e = prepare_hist_split();
+        e = s->wBf.ensure(s->w_ext + 1);
+        if (e == cudaSuccess) e = s->wAf.ensure(s->w_ext + 1);
+        if (e == cudaSuccess) e = launch_to_float(s->wB.p, s->w_ext + 1, s->wBf.p, s->sR);
+        if (e == cudaSuccess) e = launch_to_float(s->wA.p, s->w_ext + 1, s->wAf.p, s->sR);
+        if (e == cudaSuccess) e = prepare_hist_split();
         s->g_max = (N + kSplitSeg - 1) / kSplitSeg - 1;
         if (e == cudaSuccess && s->g_max >= 2) {
             e = s->wH.ensure((size_t)(s->g_max + 1) * 2 * 3 * 15 * 64);
@@ -594,17 +623,40 @@ fabm_status fabm_set_block(fabm_solver *s, int L)
 {
     g_last_error.clear();
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
-    if (L % 32 != 0 || L < 32 || L > kMaxBlockL)
-        return fail(FABM_EINVAL, "block length %d must be a multiple of 32 in 32..%d", L, kMaxBlockL);
-    if (s->precision == FABM_SPLIT && L != kSplitSeg)
-        return fail(FABM_EINVAL, "the split path uses blocks of %d targets", kSplitSeg);
-    if (s->precision == FABM_FP64 && L != kRecurL && L != 2 * kRecurL)
-        return fail(FABM_EINVAL, "the FP64 path uses blocks of 32 or 64 targets");
+    int hk;
+    if (L == kSplitSeg && s->precision == FABM_SPLIT)
+        hk = FABM_HIST_TENSOR;
+    else if (L == kRecurL)
+        hk = s->precision == FABM_SPLIT ? FABM_HIST_FP32C : FABM_HIST_FP64;
+    else
+        return fail(FABM_EINVAL,
+                    "block length %d: 32 (fp64 or fp32c history) or 64 (tensor history, split "
+                    "precision) are available",
+                    L);
     std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->hist_kernel = hk;
     s->L = L;
     return FABM_OK;
 }
+
+fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    const bool ok = kernel == FABM_HIST_AUTO ||
+                    (s->precision == FABM_FP64 && kernel == FABM_HIST_FP64) ||
+                    (s->precision == FABM_SPLIT &&
+                     (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_FP32C));
+    if (!ok) return fail(FABM_EINVAL, "history kernel %d does not fit precision %d", kernel, s->precision);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->hist_kernel = kernel;
+    s->L = kernel == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    return FABM_OK;
+}
+
+int fabm_get_history_kernel(const fabm_solver *s) { return s ? s->hist_kernel : -1; }
 
 int fabm_get_block(const fabm_solver *s) { return s ? s->L : 0; }
 

@@ -108,8 +108,19 @@ cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv
                               const int *Ew, int64_t c, int n_ct, int cols, int n_chunks,
                               float2 *part, unsigned int *err, cudaStream_t st);
 
-// G[kind][t][col] (double) = sum of the float-float partials over chunks.
-cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, double *G,
+// G[kind][t][col] (double) = sum of the float-float partials over chunks, for
+// blocks of L targets.
+cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
                                  cudaStream_t st);
+
+// ---- split path for narrow batches (compensated fp32 on CUDA cores) ----
+
+// y[i] = (float)x[i], i < n.
+cudaError_t launch_to_float(const double *x, int64_t n, float *y, cudaStream_t st);
+
+// Far history of block c (32 targets) over k < (c-1)*32 in compensated fp32;
+// partials as float2 (sum, -compensation), n_chunks x 2 x 32 x cols.
+cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf, int64_t c,
+                              int n_chunks, int64_t kc, float2 *part, cudaStream_t st);
 
 }  // namespace fabm

@@ -1,0 +1,150 @@
+// CTA-level bodies of the far-history kernels (a2), shared by the batch
+// kernels and the serving kernels.
+#pragma once
+
+#include "fabm_internal.cuh"
+
+namespace fabm {
+namespace hist {
+
+constexpr int kColsPerCta = 4;  // one warp per column
+constexpr int kL = kRecurL;     // targets per block (one per lane)
+
+namespace f64 {
+constexpr int kTile = 256;      // points staged in shared memory at a time
+
+// One CTA of 32 * kHistCols threads: chunk `chunk` (points k in
+// [chunk*kc, min((chunk+1)*kc, k_end))) of the far history of block c for the
+// columns col0 .. col0+3.
+__device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF, int cols,
+                                       const double *__restrict__ WB,
+                                       const double *__restrict__ WA, int64_t c, int64_t kc,
+                                       int64_t k_end, double *__restrict__ part, int64_t chunk,
+                                       int col0)
+{
+    __shared__ double sF[kTile * kColsPerCta];
+    __shared__ double sB[kTile + kL], sA[kTile + kL];
+    const int64_t k0 = chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
+    const int ncol = min(kColsPerCta, cols - col0);
+    const int w = threadIdx.x / kWarp;
+    const int a = threadIdx.x % kWarp;  // target m = cL+1+a
+    double sp = 0.0, sc = 0.0;
+
+    for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
+        const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
+        const int nk = (int)(t1 - t0);
+        // weights for d = m - k, m in [cL+1, cL+L], k in [t0, t1):
+        // window index i <-> d = cL+2-t1 + i, i < nk+L-1
+        const int64_t d_min = c * kL + 2 - t1;
+        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
+            sB[i] = WB[d_min + i];
+            sA[i] = WA[d_min + i];
+        }
+        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
+            const int k = i / kColsPerCta, j = i % kColsPerCta;
+            sF[i] = j < ncol ? F[(t0 + k) * ldF + col0 + j] : 0.0;
+        }
+        __syncthreads();
+        if (w < ncol) {
+            // d - d_min = (cL+1+a - (t0+j)) - (cL+2-t1) = a + nk-1-j
+            const double *fb = sF + w;
+            const int base = a + nk - 1;
+#pragma unroll 4
+            for (int j = 0; j < nk; ++j) {
+                const double f = fb[j * kColsPerCta];
+                sp = fma(sB[base - j], f, sp);
+                sc = fma(sA[base - j], f, sc);
+            }
+        }
+        __syncthreads();
+    }
+    if (w < ncol) {
+        double *out = part + ((chunk * 2) * kL + a) * (int64_t)cols + col0 + w;
+        out[0] = sp;
+        out[(int64_t)kL * cols] = sc;
+    }
+}
+
+}  // namespace f64
+
+namespace f32c {
+constexpr int kTile = 512;      // points staged in shared memory at a time
+constexpr int kGroup = 16;      // products added in plain fp32 before a Kahan step
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
+{
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// One CTA of 32 * kHistCols threads: chunk `chunk` of the far history of
+// block c for the columns col0 .. col0+3, in compensated fp32.
+__device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ldF, int cols,
+                                        const float *__restrict__ WB,
+                                        const float *__restrict__ WA, int64_t c, int64_t kc,
+                                        int64_t k_end, float2 *__restrict__ part, int64_t chunk,
+                                        int col0)
+{
+    __shared__ float sF[kTile * kColsPerCta];
+    __shared__ float sB[kTile + kL], sA[kTile + kL];
+    const int64_t k0 = chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
+    const int ncol = min(kColsPerCta, cols - col0);
+    const int w = threadIdx.x / kWarp;
+    const int a = threadIdx.x % kWarp;  // target m = cL+1+a
+    float sp = 0.f, cp = 0.f, sc = 0.f, cc = 0.f;
+
+    for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
+        const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
+        const int nk = (int)(t1 - t0);
+        // window index i <-> d = cL+2-t1 + i (see the double kernel)
+        const int64_t d_min = c * kL + 2 - t1;
+        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
+            sB[i] = WB[d_min + i];
+            sA[i] = WA[d_min + i];
+        }
+        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
+            const int k = i / kColsPerCta, j = i % kColsPerCta;
+            sF[i] = j < ncol ? (float)F[(t0 + k) * ldF + col0 + j] : 0.f;
+        }
+        __syncthreads();
+        if (w < ncol) {
+            const float *fb = sF + w;
+            const int base = a + nk - 1;
+            int j = 0;
+            for (; j + kGroup <= nk; j += kGroup) {
+                float gp = 0.f, gc = 0.f;
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    const float f = fb[(j + u) * kColsPerCta];
+                    gp = fmaf(sB[base - j - u], f, gp);
+                    gc = fmaf(sA[base - j - u], f, gc);
+                }
+                kahan_add(sp, cp, gp);
+                kahan_add(sc, cc, gc);
+            }
+            float gp = 0.f, gc = 0.f;
+            for (; j < nk; ++j) {
+                const float f = fb[j * kColsPerCta];
+                gp = fmaf(sB[base - j], f, gp);
+                gc = fmaf(sA[base - j], f, gc);
+            }
+            kahan_add(sp, cp, gp);
+            kahan_add(sc, cc, gc);
+        }
+        __syncthreads();
+    }
+    if (w < ncol) {
+        float2 *out = part + ((chunk * 2) * kL + a) * (int64_t)cols + col0 + w;
+        out[0] = make_float2(sp, -cp);
+        out[(int64_t)kL * cols] = make_float2(sc, -cc);
+    }
+}
+
+}  // namespace f32c
+
+}  // namespace hist
+}  // namespace fabm

@@ -13,66 +13,19 @@
 // (lane = target, warp = column) and gives each sub-partition at least one
 // warp.  The chunks are summed afterwards in a fixed order (a3), so results do
 // not depend on scheduling.
-#include "fabm_internal.cuh"
+#include "history_blocks.cuh"
 
 namespace fabm {
 namespace {
 
-constexpr int kColsPerCta = 4;  // one warp per column
-constexpr int kTile = 256;      // points staged in shared memory at a time
-constexpr int kL = kRecurL;     // targets per block (one per lane)
-
 // grid = (n_chunks, ceil(cols / kColsPerCta)); block = 32 * kColsPerCta.
-// Chunk ch covers the points k in [ch*kc, min((ch+1)*kc, k_end)).
-__global__ void __launch_bounds__(kWarp *kColsPerCta)
+__global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
     hist_fp64_kernel(const double *__restrict__ F, int64_t ldF, int cols,
                      const double *__restrict__ WB, const double *__restrict__ WA, int64_t c,
                      int64_t kc, int64_t k_end, double *__restrict__ part)
 {
-    __shared__ double sF[kTile * kColsPerCta];
-    __shared__ double sB[kTile + kL], sA[kTile + kL];
-    const int64_t chunk = blockIdx.x;
-    const int64_t k0 = chunk * kc;
-    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
-    const int col0 = blockIdx.y * kColsPerCta;
-    const int ncol = min(kColsPerCta, cols - col0);
-    const int w = threadIdx.x / kWarp;
-    const int a = threadIdx.x % kWarp;  // target m = cL+1+a
-    double sp = 0.0, sc = 0.0;
-
-    for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
-        const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
-        const int nk = (int)(t1 - t0);
-        // weights for d = m - k, m in [cL+1, cL+L], k in [t0, t1):
-        // window index i <-> d = cL+2-t1 + i, i < nk+L-1
-        const int64_t d_min = c * kL + 2 - t1;
-        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
-            sB[i] = WB[d_min + i];
-            sA[i] = WA[d_min + i];
-        }
-        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
-            const int k = i / kColsPerCta, j = i % kColsPerCta;
-            sF[i] = j < ncol ? F[(t0 + k) * ldF + col0 + j] : 0.0;
-        }
-        __syncthreads();
-        if (w < ncol) {
-            // d - d_min = (cL+1+a - (t0+j)) - (cL+2-t1) = a + nk-1-j
-            const double *fb = sF + w;
-            const int base = a + nk - 1;
-#pragma unroll 4
-            for (int j = 0; j < nk; ++j) {
-                const double f = fb[j * kColsPerCta];
-                sp = fma(sB[base - j], f, sp);
-                sc = fma(sA[base - j], f, sc);
-            }
-        }
-        __syncthreads();
-    }
-    if (w < ncol) {
-        double *out = part + ((chunk * 2) * kL + a) * (int64_t)cols + col0 + w;
-        out[0] = sp;
-        out[(int64_t)kL * cols] = sc;
-    }
+    hist::f64::hist_fp64_block(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
+                               blockIdx.y * hist::kColsPerCta);
 }
 
 // a3: G[pc][a][col] = sum_{chunk} part[chunk][pc][a][col], chunk ascending
@@ -117,10 +70,10 @@ cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c,
                              int n_chunks, int64_t kc, double *part, cudaStream_t st)
 {
     const int64_t k_end = (c - 1) * L;
-    if (L != kL) return cudaErrorInvalidValue;
+    if (L != hist::kL) return cudaErrorInvalidValue;
     if (c < 2 || k_end <= 0) return cudaSuccess;
-    dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + kColsPerCta - 1) / kColsPerCta));
-    hist_fp64_kernel<<<grid, kWarp * kColsPerCta, 0, st>>>(bt.F, bt.ldF, bt.cols, w.B, w.A, c,
+    dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
+    hist_fp64_kernel<<<grid, kWarp * hist::kColsPerCta, 0, st>>>(bt.F, bt.ldF, bt.cols, w.B, w.A, c,
                                                           kc, k_end, part);
     return cudaGetLastError();
 }

@@ -370,25 +370,56 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
     if (!ok) atomicOr(a.err, 1u);
 }
 
-// a3: G[kind][t][col] = sum over chunks of (hi + lo), in float-float, chunk
-// ascending; rounded once to double.
+// float-float (hi, lo) += (x, y): two-sum of the high parts, low parts folded
+// in, renormalized.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float x, float y)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    lo += e + y;
+    hi = s + lo;
+    lo = lo - (hi - s);
+}
+
+// a3: G[kind][t][col] = sum over chunks of (hi + lo), in float-float; R lanes
+// share one output, each summing chunks r, r+R, ... in ascending order, then a
+// fixed xor tree; rounded once to double.  Every thread runs the same number of
+// rounds, so the shuffles always see full warps.
+template <int R>
 __global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chunks, int64_t n_out,
                                      double *__restrict__ G)
 {
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out;
-         o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = (int)(gtid % R);
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / R;
+    for (int64_t base = 0; base < n_out; base += groups) {
+        const int64_t o = base + gtid / R;
         float hi = 0.f, lo = 0.f;
-        for (int ch = 0; ch < n_chunks; ++ch) {
-            const float2 v = part[(int64_t)ch * n_out + o];
-            // two-sum of hi + v.x, then fold in the low parts
-            const float s = hi + v.x;
-            const float bb = s - hi;
-            const float e = (hi - (s - bb)) + (v.x - bb);
-            lo += e + v.y;
-            hi = s + lo;
-            lo = lo - (hi - s);
+        if (o < n_out) {
+            int ch = r;
+            for (; ch + 3 * R < n_chunks; ch += 4 * R) {
+                const float2 v0 = part[(int64_t)ch * n_out + o];
+                const float2 v1 = part[(int64_t)(ch + R) * n_out + o];
+                const float2 v2 = part[(int64_t)(ch + 2 * R) * n_out + o];
+                const float2 v3 = part[(int64_t)(ch + 3 * R) * n_out + o];
+                ff_add(hi, lo, v0.x, v0.y);
+                ff_add(hi, lo, v1.x, v1.y);
+                ff_add(hi, lo, v2.x, v2.y);
+                ff_add(hi, lo, v3.x, v3.y);
+            }
+            for (; ch < n_chunks; ch += R) {
+                const float2 v = part[(int64_t)ch * n_out + o];
+                ff_add(hi, lo, v.x, v.y);
+            }
         }
-        G[o] = (double)hi + (double)lo;
+#pragma unroll
+        for (int off = R / 2; off > 0; off >>= 1) {
+            const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+            ff_add(hi, lo, ohi, olo);
+        }
+        if (r == 0 && o < n_out) G[o] = (double)hi + (double)lo;
     }
 }
 
@@ -436,13 +467,21 @@ cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, double *G,
+cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
                                  cudaStream_t st)
 {
-    const int64_t n_out = 2LL * kSeg * cols;
-    int64_t blocks = (n_out + 127) / 128;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    combine_split_kernel<<<(unsigned)blocks, 128, 0, st>>>(part, n_chunks, n_out, G);
+    const int64_t n_out = 2LL * L * cols;
+    const int threads = 128;
+    auto blocks_for = [&](int R) {
+        int64_t b = (n_out * R + threads - 1) / threads;
+        return (unsigned)(b > 152 * 16 ? 152 * 16 : b);
+    };
+    if (n_chunks >= 256)
+        combine_split_kernel<32><<<blocks_for(32), threads, 0, st>>>(part, n_chunks, n_out, G);
+    else if (n_chunks >= 32)
+        combine_split_kernel<8><<<blocks_for(8), threads, 0, st>>>(part, n_chunks, n_out, G);
+    else
+        combine_split_kernel<1><<<blocks_for(1), threads, 0, st>>>(part, n_chunks, n_out, G);
     return cudaGetLastError();
 }
 

@@ -1,176 +1,22 @@
-// a4 + a5 in double: the sequential predictor -> f -> corrector -> f chain of
-// Sec. 2 of arXiv:1710.01133 (Eq. abm, the corrector after it) inside one
-// block of L = 32*TPL targets.  One CTA per trajectory, one warp per
-// component.
-//
-// Warp i keeps, in lane a + 32t, the running predictor and corrector sums of
-// component i for target m = cL+1+a+32t:
-//   start   far part from the history kernels (points k < (c-1)L) and the
-//           k = 0 correction D(m) f_0;
-//   lag 1   the L points of block c-1, all known when the block starts;
-//   steps   for s = 0..L-1 the point k = cL+s becomes known; every pending
-//           target adds its term, and the owner of target k+1 then has the
-//           whole sum and runs the step: y^P_i, exchange of y^P across the
-//           component warps, f_i(t, y^P), y_i, exchange of y, f_i(t, y).
-// The accumulators hold y0 + h^alpha * (partial sum) and the weights are
-// pre-multiplied by h^alpha, so the owner's accumulate of the newest point is
-// already y^P (and y0 + h^alpha S^C): six dependent FP64 operations per step
-// for a Lorenz-type component (accumulate, f, corrector, f).
-// GB300 runs a double-precision warp instruction in one 64-cycle slot of its
-// sub-partition's FP64 unit whatever the number of active lanes, so one warp
-// per component spreads the serial chain over the FP64 units of several
-// sub-partitions, and adding f_k to all pending targets of a lane costs one
-// instruction.  The time-only part of f (forcing) is evaluated for every target
-// at block start, off the chain.
-#include "rhs.cuh"
+// a4 + a5: kernels around recur_block / init_one (recurrence.cuh).
+#include "recurrence.cuh"
 
 namespace fabm {
 namespace {
-
-__device__ inline void report_nonfinite(unsigned long long *status, int64_t step, int traj)
-{
-    atomicMin(status, ((unsigned long long)step << 24) | (unsigned long long)traj);
-}
-
-// Finite test on the exponent bits (no floating-point compare).
-__device__ inline bool finite_bits(double x)
-{
-    return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
-}
 
 template <class Rhs, int D>
 __global__ void init_kernel(DevBatch bt)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= bt.B) return;
-    double y[D], p[kMaxParams];
-#pragma unroll
-    for (int i = 0; i < kMaxParams; ++i) p[i] = bt.params[(int64_t)b * kMaxParams + i];
-#pragma unroll
-    for (int i = 0; i < D; ++i) y[i] = bt.y0[(int64_t)b * D + i];
-    const double aux = Rhs::aux(0.0, p);
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const double f = Rhs::template one<D>(i, y, p, aux);
-        bt.Y[(int64_t)b * (bt.N + 1) * D + i] = y[i];
-        bt.F[(int64_t)b * D + i] = f;
-        ok = ok && finite_bits(y[i]) && finite_bits(f);
-    }
-    if (!ok) report_nonfinite(bt.status, 0, b);
+    if (b < bt.B) init_one<Rhs, D>(bt, b);
 }
 
 template <class Rhs, int D, int TPL>
 __global__ void __launch_bounds__(D *kWarp)
     recur_kernel(DevBatch bt, DevWeights w, StepConsts kc, int64_t c, const double *G)
 {
-    constexpr int L = kWarp * TPL;
-    // weights pre-multiplied by h^alpha: the accumulators hold y0 + h^alpha * sum,
-    // so adding the newest point to the owner's accumulator yields y^P directly
-    __shared__ double sB[2 * L + 1], sA[2 * L + 1];
-    __shared__ double sy[2][D];      // y^P and y of the current step, all components
-    __shared__ double sF[L + 1][D];  // f of the lag-1 block and f_{m0}
-    const int b = blockIdx.x;
-    const int i = threadIdx.x / kWarp;  // component of this warp
-    const int lane = threadIdx.x % kWarp;
-    const int64_t Nb = bt.N_each[b];
-    const int64_t m0 = c * L;  // f_{m0} is the newest known point
-    if (m0 >= Nb) return;      // trajectory finished (uniform over the CTA)
-    const double ha = kc.h_alpha;
-    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
-        sB[j] = ha * w.B[j];
-        sA[j] = ha * w.A[j];
-    }
-    // rows m0-L .. m0 of this trajectory's history, all loads in flight at once
-    for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
-        const int64_t row = m0 - L + j / D;
-        sF[j / D][j % D] = row >= 0 ? bt.F[row * bt.ldF + (int64_t)b * D + j % D] : 0.0;
-    }
-    __syncthreads();
-
-    double p[kMaxParams];
-#pragma unroll
-    for (int q = 0; q < kMaxParams; ++q) p[q] = bt.params[(int64_t)b * kMaxParams + q];
-    const double y0 = bt.y0[(int64_t)b * D + i];
-    const int64_t col = (int64_t)b * D + i;
-    const double ha_ig2 = ha * kc.inv_gamma2;
-
-    double accP[TPL], accC[TPL], aux[TPL];
-    const double f0 = bt.F[col];
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) {
-        const int a = lane + kWarp * t;
-        const int64_t m = m0 + 1 + a;
-        aux[t] = Rhs::aux((double)m * kc.h, p);
-        const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
-        const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
-        accP[t] = fma(ha, gP, y0);
-        accC[t] = fma(ha, gC, y0);
-    }
-    if (c >= 1) {  // lag-1 block: k = m0-L+j, d = m-k = L+1+a-j in [2, 2L]
-        for (int j = 0; j < L; ++j) {
-            const double fk = sF[j][i];
-#pragma unroll
-            for (int t = 0; t < TPL; ++t) {
-                const int d = L + 1 + lane + kWarp * t - j;
-                accP[t] = fma(sB[d], fk, accP[t]);
-                accC[t] = fma(sA[d], fk, accC[t]);
-            }
-        }
-    }
-
-    double fk = sF[L][i];
-    const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
-    double *Yb = bt.Y + (int64_t)b * (bt.N + 1) * D;
-    for (int s = 0; s < steps; ++s) {
-        // add the newest point k = m0+s; for the owner of target k+1 this
-        // completes y^P (accP) and y0 + h^a S^C (accC)
-#pragma unroll
-        for (int t = 0; t < TPL; ++t) {
-            const int d = lane + kWarp * t - s + 1;
-            const int dd = d > 0 ? d : 0;  // done targets add B(0) = A(0) = 0
-            accP[t] = fma(sB[dd], fk, accP[t]);
-            accC[t] = fma(sA[dd], fk, accC[t]);
-        }
-        const int owner = s % kWarp, slot = s / kWarp;  // uniform over the CTA
-        double yp = 0.0, aC = 0.0, ax = 0.0;
-#pragma unroll
-        for (int t = 0; t < TPL; ++t)
-            if (t == slot) yp = accP[t], aC = accC[t], ax = aux[t];
-        double fn = 0.0, yc = 0.0;
-        if constexpr (D == 1) {
-            if (lane == owner) {
-                const double fp = Rhs::template one<D>(0, &yp, p, ax);
-                yc = fma(ha_ig2, fp, aC);
-                fn = Rhs::template one<D>(0, &yc, p, ax);
-            }
-        } else {
-            if (lane == owner) sy[0][i] = yp;
-            __syncthreads();
-            if (lane == owner) {
-                double y[D];
-#pragma unroll
-                for (int q = 0; q < D; ++q) y[q] = sy[0][q];
-                const double fp = Rhs::template one<D>(i, y, p, ax);
-                yc = fma(ha_ig2, fp, aC);  // corrector
-                sy[1][i] = yc;
-            }
-            __syncthreads();
-            if (lane == owner) {
-                double y[D];
-#pragma unroll
-                for (int q = 0; q < D; ++q) y[q] = sy[1][q];
-                fn = Rhs::template one<D>(i, y, p, ax);
-            }
-        }
-        if (lane == owner) {
-            const int64_t mm = m0 + 1 + s;
-            Yb[mm * D + i] = yc;
-            bt.F[mm * bt.ldF + col] = fn;
-            if (!(finite_bits(yc) && finite_bits(fn))) report_nonfinite(bt.status, mm, b);
-        }
-        fk = __shfl_sync(0xffffffffu, fn, owner);
-    }
+    __shared__ double smem[recur_smem_doubles<D, TPL>()];
+    recur_block<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem);
 }
 
 }  // namespace

@@ -1,0 +1,621 @@
+// a7: continuous-batching server.  Requests (each an independent Caputo
+// problem of Sec. 2 of arXiv:1710.01133 with its own right-hand side, dim,
+// alpha, h and N) wait in a host queue and are admitted as "slots" while the
+// device memory they need (weights, history, output, partials) fits in the
+// server's HBM budget.  Each fabm_server_step advances every admitted slot by
+// one block of 32 steps with shared launches over tables of slots:
+//   stream G: far history of block c+1 of every slot (one launch over a list
+//             of (slot, chunk) items), then the fixed-order combine
+//   stream R: weights and initial values of newly admitted slots, then the
+//             recurrence of block c of every slot (one CTA per slot, the
+//             right-hand side dispatched at run time)
+// which is the two-stream schedule of a single solve, run for all slots at
+// once.  Finished slots are copied to host memory and their device memory is
+// returned to the stream-ordered pool; the freed budget admits waiting
+// requests at the next step.  A slot's chunking depends on its own block index
+// only, so its result does not depend on the other requests in flight.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "history_blocks.cuh"
+#include "recurrence.cuh"
+#include "weights.cuh"
+
+using namespace fabm;
+
+namespace {
+
+constexpr int kSL = kRecurL;        // block length of served solves (32)
+constexpr int kMaxChunksSlot = 64;  // far-history chunks per slot and block
+constexpr int kMinChunkPts = 256;   // points per chunk at least
+
+struct SlotDev {
+    int rhs, dim, hk;
+    int pad;
+    int64_t N, w_ext;
+    int64_t *Nb;  // device copy of N (read by the recurrence)
+    double *F, *Y, *y0, *params, *WB, *WA, *WD, *G;
+    float *WBf, *WAf;
+    void *part;  // double (FP64) or float2 (split) partials
+    StepConsts kc;
+    double alpha, inv_g1;
+    unsigned long long *status;
+};
+
+struct Item {
+    int slot;
+    int chunk;     // history: chunk index; combine: number of chunks
+    int64_t c;     // block index (history/combine: target block; recurrence: block to run)
+    int64_t kc;    // history: points per chunk
+    int gbuf;      // G buffer (c % 2) the item reads or writes; -1: none
+    int pad;
+};
+
+__device__ inline DevBatch slot_batch(const SlotDev &s)
+{
+    DevBatch bt{};
+    bt.dim = s.dim;
+    bt.B = 1;
+    bt.cols = s.dim;
+    bt.N = s.N;
+    bt.N_each = s.Nb;
+    bt.y0 = s.y0;
+    bt.params = s.params;
+    bt.F = s.F;
+    bt.ldF = s.dim;
+    bt.Y = s.Y;
+    bt.status = s.status;
+    return bt;
+}
+
+// Runs fn.template operator()<Rhs, D>() for the slot's right-hand side.
+template <class Fn>
+__device__ inline void slot_dispatch(int rhs, int dim, Fn &&fn)
+{
+    switch (rhs) {
+    case FABM_RHS_CONST:
+        if (dim == 1) fn.template operator()<RhsConst, 1>();
+        else if (dim == 2) fn.template operator()<RhsConst, 2>();
+        else if (dim == 3) fn.template operator()<RhsConst, 3>();
+        else fn.template operator()<RhsConst, 4>();
+        break;
+    case FABM_RHS_TIME:
+        if (dim == 1) fn.template operator()<RhsTime, 1>();
+        else if (dim == 2) fn.template operator()<RhsTime, 2>();
+        else if (dim == 3) fn.template operator()<RhsTime, 3>();
+        else fn.template operator()<RhsTime, 4>();
+        break;
+    case FABM_RHS_LINEAR:
+        if (dim == 1) fn.template operator()<RhsLinear, 1>();
+        else if (dim == 2) fn.template operator()<RhsLinear, 2>();
+        else if (dim == 3) fn.template operator()<RhsLinear, 3>();
+        else fn.template operator()<RhsLinear, 4>();
+        break;
+    case FABM_RHS_LORENZ: fn.template operator()<RhsLorenz, 3>(); break;
+    case FABM_RHS_DUFFING: fn.template operator()<RhsDuffing, 2>(); break;
+    case FABM_RHS_MANUFACTURED: fn.template operator()<RhsManufactured, 1>(); break;
+    case FABM_RHS_LCR: fn.template operator()<RhsLcr, 2>(); break;
+    default: break;
+    }
+}
+
+// Weights (double, and fp32 copies for split slots) of new slots:
+// blockIdx.y = new slot, grid-stride over the distances.
+__global__ void weights_slots_kernel(const SlotDev *__restrict__ slots, const int *__restrict__ idx)
+{
+    const SlotDev s = slots[idx[blockIdx.y]];
+    const double inv_g2 = s.kc.inv_gamma2;
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d <= s.w_ext;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        weights_at(d, s.alpha, s.inv_g1, inv_g2, s.WB, s.WA, s.WD);
+        if (s.WBf) {
+            s.WBf[d] = (float)s.WB[d];
+            s.WAf[d] = (float)s.WA[d];
+        }
+    }
+}
+
+__global__ void init_slots_kernel(const SlotDev *__restrict__ slots, const int *__restrict__ idx,
+                                  int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const SlotDev s = slots[idx[j]];
+    const DevBatch bt = slot_batch(s);
+    slot_dispatch(s.rhs, s.dim, [&]<class R, int D>() { init_one<R, D>(bt, 0); });
+}
+
+// One CTA (4 warps) per (slot, chunk) item of the far history.
+__global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
+    hist_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+{
+    const Item it = items[blockIdx.x];
+    const SlotDev s = slots[it.slot];
+    const int64_t k_end = (it.c - 1) * kSL;
+    if (s.hk == FABM_HIST_FP32C)
+        hist::f32c::hist_fp32c_block(s.F, s.dim, s.dim, s.WBf, s.WAf, it.c, it.kc, k_end,
+                                     static_cast<float2 *>(s.part), it.chunk, 0);
+    else
+        hist::f64::hist_fp64_block(s.F, s.dim, s.dim, s.WB, s.WA, it.c, it.kc, k_end,
+                                   static_cast<double *>(s.part), it.chunk, 0);
+}
+
+// One CTA per slot: G[gbuf][kind][t][col] = sum over the chunks in ascending
+// order (double, or float-float rounded once to double).
+__global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+{
+    const Item it = items[blockIdx.x];
+    const SlotDev s = slots[it.slot];
+    const int n_out = 2 * kSL * s.dim;
+    double *G = s.G + (int64_t)it.gbuf * n_out;
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        if (s.hk == FABM_HIST_FP32C) {
+            const float2 *p = static_cast<const float2 *>(s.part);
+            float hi = 0.f, lo = 0.f;
+            for (int ch = 0; ch < it.chunk; ++ch) {
+                const float2 v = p[(int64_t)ch * n_out + o];
+                const float t = hi + v.x;
+                const float bb = t - hi;
+                const float e = (hi - (t - bb)) + (v.x - bb);
+                lo += e + v.y;
+                hi = t + lo;
+                lo = lo - (hi - t);
+            }
+            G[o] = (double)hi + (double)lo;
+        } else {
+            const double *p = static_cast<const double *>(s.part);
+            double acc = 0.0;
+            for (int ch = 0; ch < it.chunk; ++ch) acc += p[(int64_t)ch * n_out + o];
+            G[o] = acc;
+        }
+    }
+}
+
+// One CTA of 4 warps per slot: block it.c of the recurrence.
+__global__ void __launch_bounds__(kWarp *FABM_MAX_DIM)
+    recur_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+{
+    __shared__ double smem[recur_smem_doubles<FABM_MAX_DIM, 1>()];
+    const Item it = items[blockIdx.x];
+    const SlotDev s = slots[it.slot];
+    const DevBatch bt = slot_batch(s);
+    const DevWeights w{s.WB, s.WA, s.WD, s.w_ext};
+    const double *G = it.gbuf >= 0 ? s.G + (int64_t)it.gbuf * 2 * kSL * s.dim : nullptr;
+    slot_dispatch(s.rhs, s.dim, [&]<class R, int D>() {
+        recur_block<R, D, 1>(bt, 0, w, s.kc, it.c, G, smem);
+    });
+}
+
+// ------------------------------------------------------------------- host ---
+
+fabm_status srv_fail(fabm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error(buf);
+    return st;
+}
+
+#define SRV_TRY(expr)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return srv_fail(e_ == cudaErrorMemoryAllocation ? FABM_ENOMEM : FABM_ECUDA,      \
+                            "%s failed: %s", #expr, cudaGetErrorString(e_));                 \
+    } while (0)
+
+struct Req {
+    int64_t ticket;
+    int dim, rhs;
+    double alpha, h;
+    int64_t N;
+    double params[kMaxParams];
+    int n_params;
+    double y0[FABM_MAX_DIM];
+};
+
+struct Slot {
+    Req req;
+    int64_t c = 0, nblk = 0;
+    size_t bytes = 0;
+    void *mem = nullptr;
+    SlotDev dev{};
+    bool fresh = true;
+};
+
+struct Result {
+    int state;  // FABM_REQ_*
+    fabm_status status;
+    std::vector<double> y;
+};
+
+size_t slot_bytes(const Req &r, int hk, int64_t *w_ext_out)
+{
+    const int64_t nblk = (r.N + kSL - 1) / kSL;
+    const int64_t w_ext = nblk * kSL + 2 * kSL;
+    *w_ext_out = w_ext;
+    const int64_t n_chunks = kMaxChunksSlot;
+    size_t b = 0;
+    auto add = [&](size_t n) { b += (n + 255) / 256 * 256; };
+    add(sizeof(int64_t));                                   // Nb
+    add(sizeof(unsigned long long));                        // status
+    add(sizeof(double) * FABM_MAX_DIM);                     // y0
+    add(sizeof(double) * kMaxParams);                       // params
+    for (int i = 0; i < 3; ++i) add(sizeof(double) * (w_ext + 1));  // WB WA WD
+    if (hk == FABM_HIST_FP32C)
+        for (int i = 0; i < 2; ++i) add(sizeof(float) * (w_ext + 1));
+    add(sizeof(double) * (r.N + 1) * r.dim);                // F
+    add(sizeof(double) * (r.N + 1) * r.dim);                // Y
+    add(sizeof(double) * 2 * 2 * kSL * r.dim);              // G
+    add((size_t)8 * n_chunks * 2 * kSL * r.dim);            // partials
+    return b;
+}
+
+// Carves a slot's device block into its buffers.
+void slot_layout(Slot &s, int hk, int64_t w_ext)
+{
+    uint8_t *p = static_cast<uint8_t *>(s.mem);
+    auto take = [&](size_t n) {
+        uint8_t *q = p;
+        p += (n + 255) / 256 * 256;
+        return q;
+    };
+    const Req &r = s.req;
+    SlotDev &d = s.dev;
+    d.rhs = r.rhs, d.dim = r.dim, d.hk = hk, d.N = r.N, d.w_ext = w_ext;
+    d.Nb = reinterpret_cast<int64_t *>(take(sizeof(int64_t)));
+    d.status = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
+    d.y0 = reinterpret_cast<double *>(take(sizeof(double) * FABM_MAX_DIM));
+    d.params = reinterpret_cast<double *>(take(sizeof(double) * kMaxParams));
+    d.WB = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
+    d.WA = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
+    d.WD = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
+    d.WBf = d.WAf = nullptr;
+    if (hk == FABM_HIST_FP32C) {
+        d.WBf = reinterpret_cast<float *>(take(sizeof(float) * (w_ext + 1)));
+        d.WAf = reinterpret_cast<float *>(take(sizeof(float) * (w_ext + 1)));
+    }
+    d.F = reinterpret_cast<double *>(take(sizeof(double) * (r.N + 1) * r.dim));
+    d.Y = reinterpret_cast<double *>(take(sizeof(double) * (r.N + 1) * r.dim));
+    d.G = reinterpret_cast<double *>(take(sizeof(double) * 2 * 2 * kSL * r.dim));
+    d.part = take((size_t)8 * kMaxChunksSlot * 2 * kSL * r.dim);
+    d.kc.h = r.h;
+    d.kc.h_alpha = std::pow(r.h, r.alpha);
+    d.kc.inv_gamma2 = 1.0 / std::tgamma(r.alpha + 2.0);
+    d.alpha = r.alpha;
+    d.inv_g1 = 1.0 / std::tgamma(r.alpha + 1.0);
+}
+
+// Chunking of block c's far history for one slot: depends on c only.
+void slot_chunks(int64_t c, int64_t *kc, int *n)
+{
+    const int64_t k_end = (c - 1) * kSL;
+    int64_t pts = std::max<int64_t>(kMinChunkPts, (k_end + kMaxChunksSlot - 1) / kMaxChunksSlot);
+    pts = (pts + 31) / 32 * 32;
+    *kc = pts;
+    *n = (int)((k_end + pts - 1) / pts);
+}
+
+}  // namespace
+
+struct fabm_server {
+    int device = 0;
+    int precision = FABM_FP64;
+    size_t budget = 0, in_use = 0;
+    int max_slots = 0;
+    std::deque<Req> queue;
+    std::vector<Slot> slots;
+    std::unordered_map<int64_t, Result> results;
+    int64_t next_ticket = 1;
+    cudaStream_t sR = nullptr, sG = nullptr;
+    cudaEvent_t evUp = nullptr;
+    SlotDev *d_slots = nullptr;  // device tables
+    Item *d_items = nullptr;
+    int *d_idx = nullptr;
+    SlotDev *h_slots = nullptr;  // pinned staging
+    Item *h_items = nullptr;
+    int *h_idx = nullptr;
+    int64_t item_cap = 0;
+    int64_t steps_done = 0, launches = 0;
+    std::mutex mu;
+
+    ~fabm_server()
+    {
+        for (auto &s : slots)
+            if (s.mem) cudaFreeAsync(s.mem, sR);
+        if (sR) cudaStreamSynchronize(sR);
+        if (d_slots) cudaFree(d_slots);
+        if (d_items) cudaFree(d_items);
+        if (d_idx) cudaFree(d_idx);
+        if (h_slots) cudaFreeHost(h_slots);
+        if (h_items) cudaFreeHost(h_items);
+        if (h_idx) cudaFreeHost(h_idx);
+        if (evUp) cudaEventDestroy(evUp);
+        if (sR) cudaStreamDestroy(sR);
+        if (sG) cudaStreamDestroy(sG);
+    }
+};
+
+namespace {
+
+fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
+{
+    const int hk = S->precision == FABM_SPLIT ? FABM_HIST_FP32C : FABM_HIST_FP64;
+    // 1. admission: waiting requests in arrival order while the budget allows
+    std::vector<int> fresh;
+    while (!S->queue.empty() && (int)S->slots.size() < S->max_slots) {
+        Req r = S->queue.front();
+        int64_t w_ext;
+        const size_t bytes = slot_bytes(r, hk, &w_ext);
+        if (S->in_use + bytes > S->budget) {
+            if (S->slots.empty()) {  // can never fit
+                S->queue.pop_front();
+                S->results[r.ticket] = {FABM_REQ_FAILED, FABM_ENOMEM, {}};
+                continue;
+            }
+            break;
+        }
+        Slot s;
+        s.req = r;
+        s.bytes = bytes;
+        s.nblk = (r.N + kSL - 1) / kSL;
+        cudaError_t e = cudaMallocAsync(&s.mem, bytes, S->sR);
+        if (e != cudaSuccess) {
+            if (S->slots.empty()) {
+                S->queue.pop_front();
+                S->results[r.ticket] = {FABM_REQ_FAILED, FABM_ENOMEM, {}};
+                continue;
+            }
+            break;  // retry when memory frees up
+        }
+        slot_layout(s, hk, w_ext);
+        S->queue.pop_front();
+        S->in_use += bytes;
+        S->results[r.ticket] = {FABM_REQ_RUNNING, FABM_OK, {}};
+        fresh.push_back((int)S->slots.size());
+        S->slots.push_back(s);
+    }
+    const int ns = (int)S->slots.size();
+    *n_waiting = (int)S->queue.size();
+    *n_active = ns;
+    if (ns == 0) return FABM_OK;
+
+    // 2. tables: slots, new-slot indices, items (history, combine, recurrence)
+    std::vector<Item> hist, comb, rec;
+    for (int i = 0; i < ns; ++i) {
+        Slot &s = S->slots[i];
+        S->h_slots[i] = s.dev;
+        const int64_t cn = s.c + 1;  // far history of the next block
+        if (cn >= 2 && cn < s.nblk) {
+            int64_t kc;
+            int n;
+            slot_chunks(cn, &kc, &n);
+            for (int ch = 0; ch < n; ++ch) hist.push_back({i, ch, cn, kc, (int)(cn % 2), 0});
+            comb.push_back({i, n, cn, 0, (int)(cn % 2), 0});
+        }
+        rec.push_back({i, 0, s.c, 0, s.c >= 2 ? (int)(s.c % 2) : -1, 0});
+    }
+    const int64_t n_items = (int64_t)hist.size() + (int64_t)comb.size() + (int64_t)rec.size();
+    if (n_items > S->item_cap) {
+        if (S->d_items) cudaFree(S->d_items);
+        if (S->h_items) cudaFreeHost(S->h_items);
+        S->d_items = nullptr, S->h_items = nullptr;
+        S->item_cap = std::max<int64_t>(n_items, 2 * S->item_cap);
+        SRV_TRY(cudaMalloc(&S->d_items, sizeof(Item) * S->item_cap));
+        SRV_TRY(cudaMallocHost(&S->h_items, sizeof(Item) * S->item_cap));
+    }
+    std::copy(hist.begin(), hist.end(), S->h_items);
+    std::copy(comb.begin(), comb.end(), S->h_items + hist.size());
+    std::copy(rec.begin(), rec.end(), S->h_items + hist.size() + comb.size());
+    for (size_t j = 0; j < fresh.size(); ++j) S->h_idx[j] = fresh[j];
+    Item *dH = S->d_items, *dC = dH + hist.size(), *dRc = dC + comb.size();
+
+    SRV_TRY(cudaMemcpyAsync(S->d_slots, S->h_slots, sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, S->sR));
+    SRV_TRY(cudaMemcpyAsync(S->d_items, S->h_items, sizeof(Item) * n_items, cudaMemcpyHostToDevice, S->sR));
+    // 3. new slots: inputs, weights, initial values (stream R)
+    if (!fresh.empty()) {
+        SRV_TRY(cudaMemcpyAsync(S->d_idx, S->h_idx, sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, S->sR));
+        for (int i : fresh) {
+            Slot &s = S->slots[i];
+            double par[kMaxParams] = {};
+            for (int q = 0; q < s.req.n_params; ++q) par[q] = s.req.params[q];
+            SRV_TRY(cudaMemcpyAsync(s.dev.y0, s.req.y0, sizeof(double) * s.req.dim, cudaMemcpyHostToDevice, S->sR));
+            SRV_TRY(cudaMemcpyAsync(s.dev.params, par, sizeof par, cudaMemcpyHostToDevice, S->sR));
+            SRV_TRY(cudaMemcpyAsync(s.dev.Nb, &s.req.N, sizeof(int64_t), cudaMemcpyHostToDevice, S->sR));
+            SRV_TRY(cudaMemsetAsync(s.dev.status, 0xff, sizeof(unsigned long long), S->sR));
+        }
+        int64_t wmax = 0;
+        for (int i : fresh) wmax = std::max(wmax, S->slots[i].dev.w_ext);
+        const unsigned gx = (unsigned)std::min<int64_t>((wmax + 256) / 256, 64);
+        weights_slots_kernel<<<dim3(gx, (unsigned)fresh.size()), 256, 0, S->sR>>>(S->d_slots, S->d_idx);
+        SRV_TRY(cudaGetLastError());
+        init_slots_kernel<<<(unsigned)((fresh.size() + 127) / 128), 128, 0, S->sR>>>(
+            S->d_slots, S->d_idx, (int)fresh.size());
+        SRV_TRY(cudaGetLastError());
+        S->launches += 2;
+    }
+    SRV_TRY(cudaEventRecord(S->evUp, S->sR));
+    SRV_TRY(cudaStreamWaitEvent(S->sG, S->evUp, 0));
+    // 4. shared launches
+    if (!hist.empty()) {
+        hist_slots_kernel<<<(unsigned)hist.size(), kWarp * hist::kColsPerCta, 0, S->sG>>>(S->d_slots, dH);
+        SRV_TRY(cudaGetLastError());
+        combine_slots_kernel<<<(unsigned)comb.size(), 256, 0, S->sG>>>(S->d_slots, dC);
+        SRV_TRY(cudaGetLastError());
+        S->launches += 2;
+    }
+    recur_slots_kernel<<<(unsigned)rec.size(), kWarp * FABM_MAX_DIM, 0, S->sR>>>(S->d_slots, dRc);
+    SRV_TRY(cudaGetLastError());
+    ++S->launches;
+    SRV_TRY(cudaStreamSynchronize(S->sG));
+    SRV_TRY(cudaStreamSynchronize(S->sR));
+    ++S->steps_done;
+
+    // 5. advance; finished slots to host, memory back to the pool
+    std::vector<Slot> keep;
+    keep.reserve(ns);
+    for (int i = 0; i < ns; ++i) {
+        Slot &s = S->slots[i];
+        s.c += 1;
+        if (s.c < s.nblk) {
+            keep.push_back(s);
+            continue;
+        }
+        Result &res = S->results[s.req.ticket];
+        res.y.resize((size_t)(s.req.N + 1) * s.req.dim);
+        unsigned long long st = 0;
+        SRV_TRY(cudaMemcpy(res.y.data(), s.dev.Y, sizeof(double) * res.y.size(), cudaMemcpyDeviceToHost));
+        SRV_TRY(cudaMemcpy(&st, s.dev.status, sizeof st, cudaMemcpyDeviceToHost));
+        res.state = st == ~0ull ? FABM_REQ_DONE : FABM_REQ_FAILED;
+        res.status = st == ~0ull ? FABM_OK : FABM_ENONFINITE;
+        SRV_TRY(cudaFreeAsync(s.mem, S->sR));
+        S->in_use -= s.bytes;
+    }
+    S->slots.swap(keep);
+    *n_active = (int)S->slots.size();
+    return FABM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots, fabm_server **out)
+{
+    set_last_error("");
+    if (!out) return srv_fail(FABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (precision != FABM_FP64 && precision != FABM_SPLIT)
+        return srv_fail(FABM_EINVAL, "precision %d unknown", precision);
+    if (max_slots < 1 || max_slots > (1 << 20)) return srv_fail(FABM_EINVAL, "max_slots %d", max_slots);
+    if (budget_bytes == 0) return srv_fail(FABM_EINVAL, "budget is 0");
+    fabm_server *S = new (std::nothrow) fabm_server();
+    if (!S) return srv_fail(FABM_ENOMEM, "host allocation failed");
+    S->budget = budget_bytes, S->precision = precision, S->max_slots = max_slots;
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->sR, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->sG, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->evUp, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_slots, sizeof(SlotDev) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_idx, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_slots, sizeof(SlotDev) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_idx, sizeof(int) * max_slots);
+    if (e != cudaSuccess) {
+        delete S;
+        return srv_fail(FABM_ECUDA, "fabm_server_create: %s", cudaGetErrorString(e));
+    }
+    *out = S;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *ticket)
+{
+    set_last_error("");
+    if (!S || !q || !ticket) return srv_fail(FABM_EINVAL, "NULL argument");
+    if (q->dim < 1 || q->dim > FABM_MAX_DIM) return srv_fail(FABM_EINVAL, "dim %d", q->dim);
+    if (!(q->alpha > 0.0 && q->alpha < 1.0)) return srv_fail(FABM_EINVAL, "alpha %g", q->alpha);
+    if (!(q->h > 0.0) || !std::isfinite(q->h)) return srv_fail(FABM_EINVAL, "h %g", q->h);
+    if (q->N < 1 || q->N > (1LL << 31)) return srv_fail(FABM_EINVAL, "N %lld", (long long)q->N);
+    const int np = rhs_n_params(q->rhs_id);
+    if (np < 0 || !rhs_supports_dim(q->rhs_id, q->dim))
+        return srv_fail(FABM_EINVAL, "rhs_id %d with dim %d unsupported", q->rhs_id, q->dim);
+    if (q->n_params < np || q->n_params > kMaxParams || (q->n_params > 0 && !q->params))
+        return srv_fail(FABM_EINVAL, "rhs_id %d needs %d params", q->rhs_id, np);
+    if (!q->y0) return srv_fail(FABM_EINVAL, "y0 is NULL");
+    Req r{};
+    r.dim = q->dim, r.rhs = q->rhs_id, r.alpha = q->alpha, r.h = q->h, r.N = q->N;
+    r.n_params = q->n_params;
+    for (int i = 0; i < q->n_params; ++i) r.params[i] = q->params[i];
+    for (int i = 0; i < q->dim; ++i) {
+        if (!std::isfinite(q->y0[i])) return srv_fail(FABM_EINVAL, "y0 not finite");
+        r.y0[i] = q->y0[i];
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    r.ticket = S->next_ticket++;
+    S->queue.push_back(r);
+    S->results[r.ticket] = {FABM_REQ_WAITING, FABM_OK, {}};
+    *ticket = r.ticket;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_step(fabm_server *S, int *n_active, int *n_waiting)
+{
+    set_last_error("");
+    if (!S) return srv_fail(FABM_EINVAL, "server is NULL");
+    int a = 0, w = 0;
+    std::lock_guard<std::mutex> lk(S->mu);
+    int prev = -1;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != S->device) cudaSetDevice(S->device);
+    fabm_status st = server_step(S, &a, &w);
+    if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
+    if (n_active) *n_active = a;
+    if (n_waiting) *n_waiting = w;
+    return st;
+}
+
+fabm_status fabm_server_poll(fabm_server *S, int64_t ticket, int *state)
+{
+    set_last_error("");
+    if (!S || !state) return srv_fail(FABM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) return srv_fail(FABM_EINVAL, "unknown ticket %lld", (long long)ticket);
+    *state = it->second.state;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_result(fabm_server *S, int64_t ticket, double *out)
+{
+    set_last_error("");
+    if (!S || !out) return srv_fail(FABM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) return srv_fail(FABM_EINVAL, "unknown ticket %lld", (long long)ticket);
+    Result &r = it->second;
+    if (r.state == FABM_REQ_WAITING || r.state == FABM_REQ_RUNNING)
+        return srv_fail(FABM_EBUSY, "request %lld not finished", (long long)ticket);
+    const fabm_status st = r.status;
+    if (!r.y.empty()) std::memcpy(out, r.y.data(), sizeof(double) * r.y.size());
+    S->results.erase(it);
+    if (st != FABM_OK)
+        return srv_fail(st, "request %lld failed (%s)", (long long)ticket,
+                        st == FABM_ENONFINITE ? "non-finite value" : "does not fit the budget");
+    return FABM_OK;
+}
+
+fabm_status fabm_server_stats(const fabm_server *S, int64_t *steps, int64_t *launches,
+                              size_t *bytes_in_use)
+{
+    set_last_error("");
+    if (!S) return srv_fail(FABM_EINVAL, "server is NULL");
+    if (steps) *steps = S->steps_done;
+    if (launches) *launches = S->launches;
+    if (bytes_in_use) *bytes_in_use = S->in_use;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_destroy(fabm_server *S)
+{
+    set_last_error("");
+    if (!S) return FABM_OK;
+    const int dev = S->device;
+    int prev = -1;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    delete S;
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    return FABM_OK;
+}
+
+}  // extern "C"

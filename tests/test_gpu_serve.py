@@ -1,0 +1,130 @@
+"""The continuous-batching server (needs a GPU).
+
+Requests with different right-hand sides, dims, alphas and lengths are
+admitted by an HBM budget, advanced together block by block, and must give the
+same result alone and in the mix (bit for bit: a request's chunking depends
+only on its own block index) and match standalone solves (FP64: 1e-12) or the
+oracle (split: 1e-6) on the solution scale.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from fabm_workloads import LORENZ_PARAMS, served_stream
+
+pytestmark = pytest.mark.gpu
+
+MIX = [
+    ("lorenz", 3, 0.95, 1e-3, 3000, [1.0, 1.02, 0.98], LORENZ_PARAMS),
+    ("linear", 1, 0.8, 1e-3, 1000, [1.0], (1.0,)),
+    ("duffing", 2, 0.9, 1e-3, 2047, [0.2, -0.1], (0.1, 1.2, 0.7)),
+    ("lcr", 2, 0.9, 1e-2, 777, [0.05, 0.0], (1.015, 0.55, -1.02, -0.58, 0.1)),
+    ("linear", 3, 0.7, 2e-3, 33, [1.0, -2.0, 0.5], (0.5,)),
+    ("lorenz", 3, 0.75, 5e-4, 1, [1.0, 1.0, 1.0], LORENZ_PARAMS),
+]
+
+
+def rel_err(got, ref):
+    scale = np.max(np.abs(ref), axis=0, keepdims=True)
+    scale = np.where(scale == 0, 1.0, scale)
+    return float(np.max(np.abs(got - ref) / scale))
+
+
+def run_to_completion(srv, tickets, max_steps=100000):
+    for _ in range(max_steps):
+        if all(srv.poll(t) >= 2 for t in tickets):
+            return
+        srv.step()
+    raise AssertionError("server did not finish")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_server_matches_standalone(gpu_lib, precision):
+    with gpu_lib.Server(8 << 30, precision=precision) as srv:
+        tickets = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX]
+        run_to_completion(srv, tickets)
+        results = [srv.result(t) for t in tickets]
+    for (rhs, dim, a, h, N, y0, p), got in zip(MIX, results):
+        assert got.shape == (N + 1, dim)
+        if precision == "fp64":
+            with gpu_lib.Solver(rhs, dim, a, h, N, p) as s:
+                ref = s.solve(y0)
+            assert rel_err(got, ref) <= 1e-12, rhs
+        else:
+            ref = oracle.solve(rhs, a, h, N, y0, params=p)
+            assert rel_err(got, ref) <= 1e-6, rhs
+
+
+def test_same_alone_and_in_mix_bitwise(gpu_lib):
+    target = MIX[0]
+    with gpu_lib.Server(8 << 30) as srv:
+        t = srv.submit(*target[:5], target[5], target[6])
+        run_to_completion(srv, [t])
+        alone = srv.result(t)
+    with gpu_lib.Server(8 << 30) as srv:
+        others = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX[1:4]]
+        for _ in range(7):  # arrive while the others are in flight
+            srv.step()
+        t = srv.submit(*target[:5], target[5], target[6])
+        late = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX[3:]]
+        run_to_completion(srv, [t] + others + late)
+        mixed = srv.result(t)
+    assert np.array_equal(alone, mixed)
+
+
+def test_budget_admission_and_release(gpu_lib):
+    """A budget that holds two of these requests: the others wait until memory
+    is released, then run; every result stays correct."""
+    req = ("lorenz", 3, 0.9, 1e-3, 4000, [1.0, 1.0, 1.0], LORENZ_PARAMS)
+    with gpu_lib.Server(1 << 30) as probe:  # one request's device footprint
+        probe.submit(*req[:5], req[5], req[6])
+        probe.step()
+        per_req = probe.stats()["bytes_in_use"]
+    assert per_req > 0
+    with gpu_lib.Server(2 * per_req + per_req // 2) as srv:
+        tickets = [srv.submit(*req[:5], np.asarray(req[5]) + 0.01 * i, req[6]) for i in range(4)]
+        active, waiting = srv.step()
+        assert (active, waiting) == (2, 2)
+        assert srv.poll(tickets[2]) == gpu_lib.FABM_REQ_WAITING
+        assert srv.stats()["bytes_in_use"] == 2 * per_req
+        run_to_completion(srv, tickets)
+        res = [srv.result(t) for t in tickets]
+    with gpu_lib.Solver(*req[:5], req[6]) as s:
+        for i, got in enumerate(res):
+            assert rel_err(got, s.solve(np.asarray(req[5]) + 0.01 * i)) <= 1e-12
+
+
+def test_failures_are_isolated(gpu_lib):
+    with gpu_lib.Server(64 << 20) as srv:
+        bad = srv.submit("linear", 1, 0.9, 0.1, 5000, [1.0], (-50.0,))     # overflows
+        huge = srv.submit("linear", 1, 0.9, 1e-3, 2 ** 24, [1.0], (1.0,))  # never fits
+        good = srv.submit("linear", 1, 0.8, 1e-3, 500, [1.0], (1.0,))
+        run_to_completion(srv, [bad, huge, good])
+        assert srv.poll(bad) == gpu_lib.FABM_REQ_FAILED
+        assert srv.poll(huge) == gpu_lib.FABM_REQ_FAILED
+        with pytest.raises(gpu_lib.FabmError) as e1:
+            srv.result(bad)
+        assert e1.value.status == gpu_lib.FABM_ENONFINITE
+        with pytest.raises(gpu_lib.FabmError) as e2:
+            srv.result(huge)
+        assert e2.value.status == gpu_lib.FABM_ENOMEM
+        got = srv.result(good)
+    ref = oracle.solve("linear", 0.8, 1e-3, 500, [1.0], params=[1.0])
+    assert rel_err(got, ref) <= 1e-12
+
+
+def test_served_stream_sample_continuous(gpu_lib):
+    """Requests of the mixed stream submitted while others are in flight; each
+    matches the oracle at the split bar."""
+    reqs = served_stream(n=24, rate=1e9, k_lo=9, k_hi=11)
+    with gpu_lib.Server(8 << 30, precision="split") as srv:
+        tickets = []
+        for i, r in enumerate(reqs):
+            tickets.append(srv.submit(r.rhs, r.dim, r.alpha, r.h, r.N, r.y0, r.params))
+            if i % 3 == 2:
+                srv.step()
+        run_to_completion(srv, tickets)
+        results = [srv.result(t) for t in tickets]
+    for r, got in zip(reqs, results):
+        ref = oracle.solve(r.rhs, r.alpha, r.h, r.N, r.y0, params=r.params)
+        assert rel_err(got, ref) <= 1e-6

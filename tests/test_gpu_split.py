@@ -16,6 +16,7 @@ from fabm_workloads import (duffing_sweep, lcr_sweep, lorenz_long, lorenz_single
 
 pytestmark = pytest.mark.gpu
 TOL_SPLIT = 1e-6
+HISTS = ["tensor", "fp32c"]
 
 
 def rel_err(got, ref):
@@ -25,40 +26,44 @@ def rel_err(got, ref):
     return float(np.max(np.abs(np.asarray(got) - ref) / scale))
 
 
-@pytest.mark.parametrize("N", [1, 63, 64, 65, 128, 129, 193, 1000])
-def test_split_constant_rhs_closed_form(gpu_lib, N):
+@pytest.mark.parametrize("hist", HISTS)
+@pytest.mark.parametrize("N", [1, 31, 32, 33, 63, 64, 65, 128, 129, 193, 1000])
+def test_split_constant_rhs_closed_form(gpu_lib, N, hist):
     alpha, h = 0.7, 0.01
-    with gpu_lib.Solver("const", 1, alpha, h, N, [1.5], precision="split") as s:
+    with gpu_lib.Solver("const", 1, alpha, h, N, [1.5], precision="split", history=hist) as s:
         y = s.solve([0.25])
     t = np.arange(N + 1) * h
     ex = 0.25 + 1.5 * t ** alpha / math.gamma(alpha + 1)
     assert np.max(np.abs(y[:, 0] - ex)) / np.max(np.abs(ex)) < TOL_SPLIT
 
 
-def test_split_mittag_leffler(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_mittag_leffler(gpu_lib, hist):
     w = ml_scalar()
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         got = s.solve(w.y0[0])
     ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
     assert rel_err(got, ref) <= TOL_SPLIT
 
 
-def test_split_lorenz_prefix(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_lorenz_prefix(gpu_lib, hist):
     w = lorenz_single(N=20_000)
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         got = s.solve(w.y0[0])
     ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
     assert rel_err(got, ref) <= TOL_SPLIT
 
 
-def test_split_duffing_batch_several_column_tiles(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_duffing_batch_several_column_tiles(gpu_lib, hist):
     """300 trajectories x 2 = 600 columns: five 128-column tiles, the last one
     ragged; uneven lengths."""
     w = duffing_sweep(B=300, N=3000)
     ne = np.full(w.B, w.N, dtype=np.int64)
     ne[::7] = 1777
     ne[3] = 1
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         got = s.solve_batch(w.y0, traj_params=w.traj_params, N_each=ne)
     idx = np.r_[0:8, 150:154, 292:300]
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
@@ -68,26 +73,43 @@ def test_split_duffing_batch_several_column_tiles(gpu_lib):
         assert rel_err(got[b, : n + 1], ref[j, : n + 1]) <= TOL_SPLIT, b
 
 
-def test_split_matches_fp64_gpu_on_lcr(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_matches_fp64_gpu_on_lcr(gpu_lib, hist):
     w = lcr_sweep(B=16, N=4000)
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         sp = s.solve_batch(w.y0, traj_params=w.traj_params)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
         dp = s.solve_batch(w.y0, traj_params=w.traj_params)
     assert rel_err(sp, dp) <= TOL_SPLIT
 
 
-def test_split_lorenz_long_subset(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_lorenz_long_subset(gpu_lib, hist):
     w = lorenz_long().subset(np.arange(4), N=50_000)
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         got = s.solve_batch(w.y0)
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0, params=w.params)
     assert rel_err(got, ref) <= TOL_SPLIT
 
 
-def test_split_deterministic(gpu_lib):
+@pytest.mark.parametrize("hist", HISTS)
+def test_split_deterministic(gpu_lib, hist):
     w = lorenz_single(N=3000)
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
         a = s.solve(w.y0[0])
         b = s.solve(w.y0[0])
     assert np.array_equal(a, b)
+
+
+def test_auto_history_kernel_choice(gpu_lib):
+    """Split precision picks tensor cores for wide batches (64+ columns) and the
+    compensated fp32 kernel for narrow ones; the block length follows."""
+    w = duffing_sweep(B=40, N=300)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        s.solve_batch(w.y0[:2], traj_params=w.traj_params[:2])
+        assert s.block == 32
+        s.solve_batch(w.y0, traj_params=w.traj_params)
+        assert s.block == 64
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
+        with pytest.raises(gpu_lib.FabmError):
+            gpu_lib.fabm_set_history_kernel(s.handle, "tensor")
