@@ -244,6 +244,72 @@ def run_reference(args, w):
     print(json.dumps(line))
 
 
+def run_served(args):
+    """Served mixed stream: requests of fabm_workloads.served_stream submitted
+    at their arrival times to a fabm server while it steps; throughput over the
+    whole stream and arrival-to-result latency percentiles.  The arrival rate is
+    0.8 x the capacity measured first with every request queued at t = 0."""
+    import torch
+
+    import paper_1710_01133_gb300 as fabm
+    fabm.load()
+    torch.cuda.set_device(0)
+    n = args.n_requests
+    k_hi = args.k_max
+
+    def serve(reqs, rate_label):
+        with fabm.Server(120 << 30, precision=args.precision) as srv:
+            t0 = time.perf_counter()
+            pending = list(reqs)
+            inflight = {}
+            lat = []
+            nxt = 0
+            while nxt < len(pending) or inflight:
+                now = time.perf_counter() - t0
+                while nxt < len(pending) and pending[nxt].arrival <= now:
+                    r = pending[nxt]
+                    tk = srv.submit(r.rhs, r.dim, r.alpha, r.h, r.N, r.y0, r.params)
+                    inflight[tk] = r
+                    nxt += 1
+                if not inflight:
+                    time.sleep(max(0.0, pending[nxt].arrival - now))
+                    continue
+                srv.step()
+                now = time.perf_counter() - t0
+                done = [tk for tk in inflight if srv.poll(tk) >= fabm.FABM_REQ_DONE]
+                for tk in done:
+                    r = inflight.pop(tk)
+                    srv.result(tk)
+                    lat.append(now - r.arrival)
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        steps = sum(r.N for r in reqs)
+        macs = sum(float(r.N) ** 2 * r.dim for r in reqs)
+        return {"rate": rate_label, "wall_s": wall, "steps_traj_per_s": steps / wall,
+                "history_gmac_s": macs / wall / 1e9,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "server_steps": st["steps"],
+                "gpu_launches": st["launches"]}
+
+    burst = wl.served_stream(n=n, rate=1e12, k_hi=k_hi)
+    serve(wl.served_stream(n=min(n, 64), rate=1e12, k_hi=min(k_hi, 12)), "warmup")
+    cap = serve(burst, "all at t=0")
+    rate = 0.8 * n / cap["wall_s"]
+    timed = serve(wl.served_stream(n=n, rate=rate, k_hi=k_hi), f"{rate:.1f}/s")
+    line = {
+        "metric": "steps_traj_per_s", "value": timed["steps_traj_per_s"], "unit": "steps*traj/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": timed["wall_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"served-mix-{n}req-k12..{k_hi}", "precision": args.precision,
+                   "requests": n, "arrival_rate_per_s": rate, "hbm_budget_gb": 120},
+        "history_gmac_s": timed["history_gmac_s"],
+        "latency_ms": {"p50": timed["p50_ms"], "p99": timed["p99_ms"]},
+        "capacity_run": cap, "gpu_launches": timed["gpu_launches"],
+    }
+    print(json.dumps(line))
+
+
 def _config(w, args):
     return {"workload": w.name, "precision": args.precision, "rhs": w.rhs, "dim": w.dim,
             "alpha": w.alpha, "h": w.h, "steps_N": w.N, "trajectories": w.B,
@@ -256,7 +322,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fabm", choices=["fabm", "reference"])
-    ap.add_argument("--workload", default="lorenz-single", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lorenz-single",
+                    choices=sorted(WORKLOADS) + ["served-mix"])
     ap.add_argument("--precision", default=None, choices=["fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-steps", type=int, default=None,
@@ -265,7 +332,14 @@ def main():
                     help="keep only the first n trajectories of the workload")
     ap.add_argument("--timing-period", type=int, default=16,
                     help="time the kernel launches of every k-th time block")
+    ap.add_argument("--n-requests", type=int, default=2000, help="served-mix: requests")
+    ap.add_argument("--k-max", type=int, default=14, help="served-mix: N = 2^k, k <= k_max")
     args = ap.parse_args()
+    if args.workload == "served-mix":
+        if args.precision is None:
+            args.precision = "split"
+        run_served(args)
+        return
     w = WORKLOADS[args.workload]()
     if args.n_steps is not None or args.n_traj is not None:
         idx = np.arange(min(args.n_traj or w.B, w.B))

@@ -26,7 +26,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
             "fabm_solve_noalloc", "fabm_set_history_kernel", "fabm_get_history_kernel",
             "fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
-            "fabm_server_result", "fabm_server_stats", "fabm_server_destroy")
+            "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
     for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
               "fabm_server_result", "fabm_server_stats", "fabm_server_destroy"):
         getattr(lib, f).restype = i
+    lib.fabm_autotune.argtypes = [vp, i64, P(d), P(d), i64, i, P(d), P(i), P(i), P(i)]
+    lib.fabm_autotune.restype = i
     lib.fabm_set_history_kernel.argtypes = [vp, i]
     lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
@@ -246,6 +248,20 @@ class Solver:
     @property
     def last_launch_count(self) -> int:
         return fabm_last_launch_count(self.handle)
+
+    def autotune(self, y0, traj_params=None, n_probe=4096):
+        """Time truncated solves of this batch for each candidate setting, keep
+        the fastest; returns [(ms, history kernel, CTA target), ...]."""
+        y0 = _f64(y0).reshape(-1, self.dim)
+        B = y0.shape[0]
+        tp = None if traj_params is None else _f64(traj_params).reshape(B, -1)
+        ms = np.zeros(8)
+        kern = (ctypes.c_int * 8)()
+        ctas = (ctypes.c_int * 8)()
+        n = ctypes.c_int()
+        _check(load().fabm_autotune(self.handle, B, _dp(y0), _dp(tp), int(n_probe), 8, _dp(ms),
+                                    kern, ctas, ctypes.byref(n)))
+        return [(float(ms[i]), int(kern[i]), int(ctas[i])) for i in range(min(n.value, 8))]
 
     def set_graphs(self, enable: bool = True):
         fabm_set_graphs(self.handle, enable)

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -91,6 +92,8 @@ struct fabm_solver {
     double params[kMaxParams] = {};
     int precision = FABM_FP64;
     int hist_kernel = FABM_HIST_AUTO;  // requested
+    int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
+    int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     int L = kRecurL;                   // block length of the last solve
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
@@ -156,10 +159,10 @@ struct fabm_solver {
 namespace {
 
 // Chunking of the far history of block c over the points k < (c-1)L.
-void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int *n_chunks, int64_t *kc)
+void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int want_ctas, int *n_chunks,
+                 int64_t *kc)
 {
     const int col_tiles = (cols + 3) / 4;
-    const int64_t want_ctas = 152 * 4;  // 4 CTAs of up to 4 column warps per SM
     int64_t n = (want_ctas + col_tiles - 1) / col_tiles;
     const int64_t min_kc = 64;
     n = std::min<int64_t>(n, (k_end + min_kc - 1) / min_kc);
@@ -279,7 +282,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                     return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
                 }));
             } else if (hk == FABM_HIST_FP32C) {
-                plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
+                plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
                     return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, c, n_chunks, kc, s->spart.p,
                                              s->sG);
@@ -288,7 +291,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                     return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
                 }));
             } else {
-                plan_chunks(k_end, (int)cols, max_chunks, &n_chunks, &kc);
+                plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
                     return launch_hist_fp64(bt, w, c, L, n_chunks, kc, s->part.p, s->sG);
                 }));
@@ -366,7 +369,12 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int n_ct = (int)((cols + 127) / 128);
     int split_chunks = 1;
     if (split) {
-        split_chunks = std::max(1, 148 / n_ct);
+        // leave SMs for the recurrence CTAs that run beside the tensor kernel
+        // (one tensor CTA fills an SM's register file): about one SM per 12
+        // trajectories, only where the column tiles do not need every SM
+        int reserve = s->sm_reserve;
+        if (reserve < 0) reserve = n_ct <= 16 ? (int)std::min<int64_t>((B + 11) / 12, 40) : 0;
+        split_chunks = std::max(1, (148 - reserve) / n_ct);
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
         FABM_CUDA_TRY(s->spart.ensure(split_part_elems(split_chunks, (int)cols)));
@@ -401,7 +409,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
 
     const std::vector<uintptr_t> key = {
         (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
-        (uintptr_t)s->timing_period, (uintptr_t)hk, (uintptr_t)Y,
+        (uintptr_t)s->timing_period, (uintptr_t)hk, (uintptr_t)s->chunk_ctas,
+        (uintptr_t)(s->sm_reserve + 1), (uintptr_t)Y,
         (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p};
@@ -542,7 +551,10 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     if (e == cudaSuccess) e = s->wB.ensure(s->w_ext + 1);
     if (e == cudaSuccess) e = s->wA.ensure(s->w_ext + 1);
     if (e == cudaSuccess) e = s->wD.ensure(s->w_ext + 1);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sR, cudaStreamNonBlocking);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    // the recurrence is the serial chain: its CTAs are scheduled first
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->sR, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG, cudaStreamNonBlocking);
     for (auto &ev : s->evR)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -675,6 +687,82 @@ fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, d
 }
 
 int64_t fabm_last_launch_count(const fabm_solver *s) { return s ? s->launches : 0; }
+
+fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
+                          int64_t n_probe, int max_report, double *ms_report, int *kernel_report,
+                          int *ctas_report, int *n_report)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (B < 1 || !y0) return fail(FABM_EINVAL, "autotune needs B >= 1 and y0");
+    if (n_probe < 1) return fail(FABM_EINVAL, "n_probe %lld < 1", (long long)n_probe);
+    const int64_t np = std::min<int64_t>(n_probe, s->N);
+    struct Cand {
+        int kernel, ctas;
+    };
+    std::vector<Cand> cands;
+    const int ctas_opts[] = {152 * 2, 152 * 4, 152 * 8};
+    // at most 8 candidates are reported
+    if (s->precision == FABM_FP64) {
+        for (int c : ctas_opts) cands.push_back({FABM_HIST_FP64, c});
+    } else {
+        // tensor kernel: "ctas" carries the SM reserve (-1 automatic, 0, 16, 32)
+        for (int r : {-1, 0, 16, 32}) cands.push_back({FABM_HIST_TENSOR, r});
+        for (int c : ctas_opts) cands.push_back({FABM_HIST_FP32C, c});
+    }
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    DeviceGuard g(s->device);
+    double *dout = nullptr;
+    {
+        cudaError_t e = cudaMalloc(&dout, sizeof(double) * (size_t)B * (s->N + 1) * s->dim);
+        if (e != cudaSuccess) return fail(FABM_ENOMEM, "autotune output: %s", cudaGetErrorString(e));
+    }
+    std::vector<int64_t> ne((size_t)B, np);
+    const int keep_kernel = s->hist_kernel, keep_ctas = s->chunk_ctas, keep_res = s->sm_reserve;
+    const bool keep_timing = s->timing;
+    s->timing = false;
+    double best = 1e300;
+    Cand pick{keep_kernel, keep_ctas};
+    int nr = 0;
+    fabm_status st = FABM_OK;
+    for (const Cand &cd : cands) {
+        s->hist_kernel = cd.kernel;
+        if (cd.kernel == FABM_HIST_TENSOR)
+            s->sm_reserve = cd.ctas, s->chunk_ctas = keep_ctas;
+        else
+            s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
+        double ms = 1e300;
+        for (int rep = 0; rep < 2 && st == FABM_OK; ++rep) {  // first run records the graph
+            const auto t0 = std::chrono::steady_clock::now();
+            st = run_batch(s, B, y0, traj_params, ne.data(), dout, 1);
+            const auto t1 = std::chrono::steady_clock::now();
+            ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        }
+        if (st != FABM_OK) break;
+        if (nr < max_report) {
+            if (ms_report) ms_report[nr] = ms;
+            if (kernel_report) kernel_report[nr] = cd.kernel;
+            if (ctas_report) ctas_report[nr] = cd.ctas;
+        }
+        ++nr;
+        if (ms < best) best = ms, pick = cd;
+    }
+    cudaFree(dout);
+    s->timing = keep_timing;
+    if (st != FABM_OK) {
+        s->hist_kernel = keep_kernel, s->chunk_ctas = keep_ctas, s->sm_reserve = keep_res;
+        return st;
+    }
+    s->hist_kernel = pick.kernel;
+    if (pick.kernel == FABM_HIST_TENSOR)
+        s->sm_reserve = pick.ctas, s->chunk_ctas = keep_ctas;
+    else
+        s->chunk_ctas = pick.ctas, s->sm_reserve = keep_res;
+    s->L = pick.kernel == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    if (n_report) *n_report = nr;
+    return FABM_OK;
+}
 
 fabm_status fabm_set_graphs(fabm_solver *s, int enable)
 {

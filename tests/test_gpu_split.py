@@ -113,3 +113,16 @@ def test_auto_history_kernel_choice(gpu_lib):
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
         with pytest.raises(gpu_lib.FabmError):
             gpu_lib.fabm_set_history_kernel(s.handle, "tensor")
+
+
+def test_autotune_picks_a_candidate_and_stays_correct(gpu_lib):
+    w = duffing_sweep(B=96, N=2000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        rep = s.autotune(w.y0, traj_params=w.traj_params, n_probe=1024)
+        assert len(rep) == 7 and all(ms > 0 for ms, _, _ in rep)
+        best = min(rep)[1]
+        assert gpu_lib.fabm_get_history_kernel(s.handle) == best
+        got = s.solve_batch(w.y0[:4], traj_params=w.traj_params[:4])
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[:4], params=w.params,
+                             traj_params=w.traj_params[:4])
+    assert rel_err(got, ref) <= TOL_SPLIT
