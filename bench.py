@@ -135,9 +135,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _profile_traffic(kernel_src: str, name: str):
+# Sources each profiled kernel is built from; a committed ncu summary gives its
+# traffic only while the sha256 over these files (in this order) still matches.
+KERNEL_SOURCES = {
+    "history_fp64": ["history_fp64.cu", "history_blocks.cuh", "fabm_internal.cuh"],
+    "history_split": ["history_split.cu", "sm100_ptx.cuh", "fabm_internal.cuh"],
+    "recurrence": ["recurrence.cu", "recurrence.cuh", "rhs.cuh", "fabm_internal.cuh"],
+}
+
+
+def kernel_source_sha(key: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[key]:
+        with open(os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _profile_traffic(key: str, name: str):
     """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (sha256 of the .cu file must match)."""
+    the current sources of the kernel."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
         return None
@@ -146,8 +163,7 @@ def _profile_traffic(kernel_src: str, name: str):
     m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     if not (m_sha and m_tr):
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+    return float(m_tr.group(1)) if kernel_source_sha(key) == m_sha.group(1) else None
 
 
 def _measured_peaks():
@@ -183,12 +199,9 @@ def roofline(kind, ks, precision, clocks, w):
                     "frac": achieved / peak if peak else None,
                     "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
                                  "(probe: 1.19 TFLOP/s at 1.96 GHz)"})
-    src_file = {"history": "history_split.cu" if precision == "split" else "history_fp64.cu",
-                "recurrence": "recurrence.cu"}.get(kind)
-    traffic = None
-    if src_file:
-        traffic = _profile_traffic(os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", src_file),
-                                   f"{kind}_{precision}_{w.name}")
+    key = {"history": f"history_{'split' if precision == 'split' else 'fp64'}",
+           "recurrence": "recurrence"}.get(kind)
+    traffic = _profile_traffic(key, f"{kind}_{precision}_{w.name}") if key else None
     out["traffic"] = traffic
     return out
 
