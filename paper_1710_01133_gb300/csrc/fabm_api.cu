@@ -112,7 +112,7 @@ struct fabm_solver {
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
     DevBuf<unsigned long long> status;
-    cudaStream_t sR = nullptr, sG = nullptr;
+    cudaStream_t sR = nullptr, sG = nullptr;  // recurrence, far history
     cudaEvent_t evR[kEvRing] = {}, evG[2] = {}, evFork = nullptr;
     std::mutex busy;
     int64_t launches = 0;
@@ -308,7 +308,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
         const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
                               ((c >= 1 ? L : 0) + 0.5 * (double)(hi - lo + 1));
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
-            return launch_recur(s->rhs, bt, w, s->k, c, L, Gc, s->sR);
+            return launch_recur(s->rhs, bt, w, s->k, c, L, s->precision == FABM_SPLIT, Gc, s->sR);
         }));
         if (split && c + 2 < nblk) {  // segment c is read by the blocks c+2 ..
             FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0, [&] {

@@ -76,11 +76,12 @@ cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c,
 cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols, double *G,
                                cudaStream_t st);
 
-// a4 + a5: steps of block c (L = 32 or 64 targets) for every trajectory, in
-// double; G holds the far history of block c (2 x L x cols) or is NULL when
-// c < 2.
+// a4 + a5: steps of block c (L = 32 or 64 targets) for every trajectory; G
+// holds the far history of block c (2 x L x cols) or is NULL when c < 2.
+// split = false: all in double; split = true: FP64 bases and corrector update,
+// short-range sums and f in fp32 (recur_block_split).
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
-                         int64_t c, int L, const double *G, cudaStream_t st);
+                         int64_t c, int L, bool split, const double *G, cudaStream_t st);
 
 // Message returned by fabm_last_error() on the calling thread.
 void set_last_error(const char *msg);

@@ -11,12 +11,26 @@ __global__ void init_kernel(DevBatch bt)
     if (b < bt.B) init_one<Rhs, D>(bt, b);
 }
 
-template <class Rhs, int D, int TPL>
+template <class Rhs, int D, int TPL, bool SPLIT>
 __global__ void __launch_bounds__(D *kWarp)
     recur_kernel(DevBatch bt, DevWeights w, StepConsts kc, int64_t c, const double *G)
 {
-    __shared__ double smem[recur_smem_doubles<D, TPL>()];
-    recur_block<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem);
+    if constexpr (SPLIT) {
+        __shared__ __align__(16) float smem_f[recur_split_smem_floats<D, TPL>()];
+        recur_block_split<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem_f);
+    } else {
+        __shared__ double smem[recur_smem_doubles<D, TPL>()];
+        recur_block<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem);
+    }
+}
+
+template <int TPL, bool SPLIT>
+bool launch_recur_t(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
+                    int64_t c, const double *G, cudaStream_t st)
+{
+    return dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
+        recur_kernel<R, D, TPL, SPLIT><<<(unsigned)bt.B, D * kWarp, 0, st>>>(bt, w, k, c, G);
+    });
 }
 
 }  // namespace
@@ -32,19 +46,15 @@ cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st)
 }
 
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
-                         int64_t c, int L, const double *G, cudaStream_t st)
+                         int64_t c, int L, bool split, const double *G, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)bt.B;
     bool ok = false;
-    if (L == kWarp) {
-        ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
-            recur_kernel<R, D, 1><<<blocks, D * kWarp, 0, st>>>(bt, w, k, c, G);
-        });
-    } else if (L == 2 * kWarp) {
-        ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
-            recur_kernel<R, D, 2><<<blocks, D * kWarp, 0, st>>>(bt, w, k, c, G);
-        });
-    }
+    if (L == kWarp)
+        ok = split ? launch_recur_t<1, true>(rhs, bt, w, k, c, G, st)
+                   : launch_recur_t<1, false>(rhs, bt, w, k, c, G, st);
+    else if (L == 2 * kWarp)
+        ok = split ? launch_recur_t<2, true>(rhs, bt, w, k, c, G, st)
+                   : launch_recur_t<2, false>(rhs, bt, w, k, c, G, st);
     return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 

@@ -186,4 +186,160 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     }
 }
 
+// ---- split precision ----
+//
+// The same block of steps for the split path with no FP64 operation on the
+// serial chain of a step.  Per target (lane a, slot t):
+//   base    y0 + h^alpha (far part + D(m) f_0), FP64, at block start;
+//   near    the lag-1 block and the in-block points, h^alpha w(d) f_k summed
+//           in float-float (ff.cuh, ~48 bits) as the points become known;
+//   step    the owner forms, in float-float,
+//             y^P = base_P + near_P,  inc = near_C + h^alpha/Gamma(alpha+2) f(t, y^P),
+//           evaluates f(t, base_C + inc), and keeps inc and f;
+//   end     y = base_C + inc (the FP64 corrector update) and f_k are written
+//           as doubles, one target per lane, for the whole block at once.
+// Float-float carries ~48 bits, so the recurrence adds rounding far below
+// that of the split history; GB300 issues its fp32 at 64 times the FP64 rate
+// and a float-float operation completes in fewer cycles than one FP64
+// operation, so the chain is shorter and wide batches no longer saturate the
+// FP64 units.
+template <int D, int TPL>
+__host__ __device__ constexpr int recur_split_smem_floats()
+{
+    return 4 * (2 * kWarp * TPL + 1) + 4 * D + 2 * (kWarp * TPL + 1) * D;
+}
+
+// smem: recur_split_smem_floats<D, TPL>() floats, 8-byte aligned
+template <class Rhs, int D, int TPL>
+__device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w,
+                                  const StepConsts &kc, int64_t c, const double *G, float *smem)
+{
+    constexpr int L = kWarp * TPL;
+    FF *sB = reinterpret_cast<FF *>(smem);  // [2L+1]  h^alpha B(d)
+    FF *sA = sB + 2 * L + 1;                // [2L+1]  h^alpha A(d)
+    FF(*sy)[D] = reinterpret_cast<FF(*)[D]>(sA + 2 * L + 1);  // [2][D]
+    FF(*sF)[D] = sy + 2;                    // [L+1][D]: f of the lag-1 block and f_{m0}
+    const bool act = threadIdx.x / kWarp < D;
+    const int i = act ? threadIdx.x / kWarp : 0;
+    const int lane = threadIdx.x % kWarp;
+    const int64_t Nb = bt.N_each[b];
+    const int64_t m0 = c * L;
+    if (m0 >= Nb) return;
+    const double ha = kc.h_alpha;
+    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
+        sB[j] = ff_from_double(ha * w.B[j]);
+        sA[j] = ff_from_double(ha * w.A[j]);
+    }
+    for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
+        const int64_t row = m0 - L + j / D;
+        sF[j / D][j % D] =
+            ff_from_double(row >= 0 ? bt.F[row * bt.ldF + (int64_t)b * D + j % D] : 0.0);
+    }
+    __syncthreads();
+
+    double p[kMaxParams];
+    FF pf[kMaxParams];
+#pragma unroll
+    for (int q = 0; q < kMaxParams; ++q) {
+        p[q] = bt.params[(int64_t)b * kMaxParams + q];
+        pf[q] = ff_from_double(p[q]);
+    }
+    const double y0 = bt.y0[(int64_t)b * D + i];
+    const int64_t col = (int64_t)b * D + i;
+    const FF ha_ig2 = ff_from_double(ha * kc.inv_gamma2);
+    const double f0 = bt.F[col];
+
+    double baseC[TPL];
+    FF bP[TPL], bC[TPL], aux[TPL], nP[TPL], nC[TPL], inc[TPL], fo[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int a = lane + kWarp * t;
+        const int64_t m = m0 + 1 + a;
+        aux[t] = ff_from_double(Rhs::aux((double)m * kc.h, p));
+        const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
+        const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+        baseC[t] = fma(ha, gC, y0);
+        bP[t] = ff_from_double(fma(ha, gP, y0));
+        bC[t] = ff_from_double(baseC[t]);
+        nP[t] = nC[t] = inc[t] = fo[t] = FF(0);
+    }
+    if (c >= 1) {  // lag-1 block: k = m0-L+j, d = L+1+a-j in [2, 2L]
+        for (int j = 0; j < L; ++j) {
+            const FF fk = sF[j][i];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const int d = L + 1 + lane + kWarp * t - j;
+                nP[t] = ff_fma(sB[d], fk, nP[t]);
+                nC[t] = ff_fma(sA[d], fk, nC[t]);
+            }
+        }
+    }
+
+    FF fk = sF[L][i];
+    const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
+    for (int s = 0; s < steps; ++s) {
+        // add the newest point k = m0+s to every pending target
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int d = lane + kWarp * t - s + 1;
+            const int dd = d > 0 ? d : 0;  // done targets add B(0) = A(0) = 0
+            nP[t] = ff_fma(sB[dd], fk, nP[t]);
+            nC[t] = ff_fma(sA[dd], fk, nC[t]);
+        }
+        const int owner = s % kWarp, slot = s / kWarp;  // uniform over the CTA
+        FF yp(0), nc(0), bc(0), ax(0);
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (t == slot) yp = bP[t] + nP[t], nc = nC[t], bc = bC[t], ax = aux[t];
+        FF fn(0), in(0);
+        if constexpr (D == 1) {
+            if (lane == owner) {
+                const FF fp = Rhs::template one<D>(0, &yp, pf, ax);
+                in = ha_ig2 * fp + nc;
+                const FF yc = bc + in;
+                fn = Rhs::template one<D>(0, &yc, pf, ax);
+            }
+        } else {
+            if (act && lane == owner) sy[0][i] = yp;
+            __syncthreads();
+            if (lane == owner) {
+                FF y[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) y[q] = sy[0][q];
+                const FF fp = Rhs::template one<D>(i, y, pf, ax);
+                in = ha_ig2 * fp + nc;  // corrector increment
+                if (act) sy[1][i] = bc + in;
+            }
+            __syncthreads();
+            if (lane == owner) {
+                FF y[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) y[q] = sy[1][q];
+                fn = Rhs::template one<D>(i, y, pf, ax);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (t == slot && lane == owner) inc[t] = in, fo[t] = fn;
+        fk = shfl_ff(fn, owner);
+    }
+
+    // FP64 corrector update and f of the block's targets, one per lane
+    if (act) {
+        double *Yb = bt.Y + (int64_t)b * (bt.N + 1) * D;
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int a = lane + kWarp * t;
+            if (a < steps) {
+                const int64_t mm = m0 + 1 + a;
+                const double yc = baseC[t] + ff_to_double(inc[t]);
+                const double fd = ff_to_double(fo[t]);
+                Yb[mm * D + i] = yc;
+                bt.F[mm * bt.ldF + col] = fd;
+                if (!(finite_bits(yc) && finite_bits(fd))) report_nonfinite(bt.status, mm, b);
+            }
+        }
+    }
+}
+
 }  // namespace fabm

@@ -1,9 +1,12 @@
 // a5: right-hand sides f(t, y) of the FDE D^a y = f(t, y) (Sec. 2, Eq. fde),
 // as device functors.  Each has the dimension and parameter layout documented
-// for FABM_RHS_* in fabm.h.  All arithmetic is double.
+// for FABM_RHS_* in fabm.h.  aux() is double; one() runs in the scalar type T
+// of y, p and aux: double on the FP64 path, float-float (FF, ff.cuh) in the
+// split recurrence.
 #pragma once
 
 #include "fabm_internal.cuh"
+#include "ff.cuh"
 
 namespace fabm {
 
@@ -17,20 +20,20 @@ namespace fabm {
 
 struct RhsConst {  // f_i = p0
     __device__ static double aux(double, const double *p) { return p[0]; }
-    template <int D>
-    __device__ static double one(int, const double *, const double *, double aux) { return aux; }
+    template <int D, class T>
+    __device__ static T one(int, const T *, const T *, T aux) { return aux; }
 };
 
 struct RhsTime {  // f_i = t
     __device__ static double aux(double t, const double *) { return t; }
-    template <int D>
-    __device__ static double one(int, const double *, const double *, double aux) { return aux; }
+    template <int D, class T>
+    __device__ static T one(int, const T *, const T *, T aux) { return aux; }
 };
 
 struct RhsLinear {  // f_i = -p0 y_i
     __device__ static double aux(double, const double *) { return 0.0; }
-    template <int D>
-    __device__ static double one(int i, const double *y, const double *p, double)
+    template <int D, class T>
+    __device__ static T one(int i, const T *y, const T *p, T)
     {
         return -p[0] * y[i];
     }
@@ -38,8 +41,8 @@ struct RhsLinear {  // f_i = -p0 y_i
 
 struct RhsLorenz {  // p = (sigma, rho, beta)
     __device__ static double aux(double, const double *) { return 0.0; }
-    template <int D>
-    __device__ static double one(int i, const double *y, const double *p, double)
+    template <int D, class T>
+    __device__ static T one(int i, const T *y, const T *p, T)
     {
         if (i == 0) return p[0] * (y[1] - y[0]);
         if (i == 1) return y[0] * (p[1] - y[2]) - y[1];
@@ -49,19 +52,19 @@ struct RhsLorenz {  // p = (sigma, rho, beta)
 
 struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 + F cos(omega t)
     __device__ static double aux(double t, const double *p) { return p[2] * cos(p[1] * t); }
-    template <int D>
-    __device__ static double one(int i, const double *y, const double *p, double aux)
+    template <int D, class T>
+    __device__ static T one(int i, const T *y, const T *p, T aux)
     {
         if (i == 0) return y[1];
-        const double x = y[0];
-        return aux - (p[0] * y[1] + x * (1.0 + x * x));
+        const T x = y[0];
+        return aux - (p[0] * y[1] + x * (T(1) + x * x));
     }
 };
 
 struct RhsManufactured {  // f = p0 t^p1 + t^2 - y
     __device__ static double aux(double t, const double *p) { return p[0] * pow(t, p[1]) + t * t; }
-    template <int D>
-    __device__ static double one(int, const double *y, const double *, double aux)
+    template <int D, class T>
+    __device__ static T one(int, const T *y, const T *, T aux)
     {
         return aux - y[0];
     }
@@ -69,16 +72,16 @@ struct RhsManufactured {  // f = p0 t^p1 + t^2 - y
 
 struct RhsLcr {  // Sec. 5, Eq. sys.LRC; p = (sigma, omega, a, b, f)
     __device__ static double aux(double t, const double *p) { return p[4] * sin(p[1] * t); }
-    template <int D>
-    __device__ static double one(int i, const double *y, const double *p, double aux)
+    template <int D, class T>
+    __device__ static T one(int i, const T *y, const T *p, T aux)
     {
-        const double x = y[0];
+        const T x = y[0];
         if (i == 1) return aux - (p[0] * y[1] + x);
-        const double a = p[2], b = p[3];
-        double g;
-        if (x <= -1.0)
+        const T a = p[2], b = p[3];
+        T g;
+        if (x <= T(-1))
             g = b * x - a + b;
-        else if (x >= 1.0)
+        else if (x >= T(1))
             g = b * x + a - b;
         else
             g = a * x;

@@ -180,18 +180,25 @@ __global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const It
     }
 }
 
-// One CTA of 4 warps per slot: block it.c of the recurrence.
+// One CTA of 4 warps per slot: block it.c of the recurrence (the split
+// recurrence for split slots).
 __global__ void __launch_bounds__(kWarp *FABM_MAX_DIM)
     recur_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
 {
+    static_assert(recur_split_smem_floats<FABM_MAX_DIM, 1>() <=
+                  2 * recur_smem_doubles<FABM_MAX_DIM, 1>());
     __shared__ double smem[recur_smem_doubles<FABM_MAX_DIM, 1>()];
     const Item it = items[blockIdx.x];
     const SlotDev s = slots[it.slot];
     const DevBatch bt = slot_batch(s);
     const DevWeights w{s.WB, s.WA, s.WD, s.w_ext};
     const double *G = it.gbuf >= 0 ? s.G + (int64_t)it.gbuf * 2 * kSL * s.dim : nullptr;
+    const bool split = s.hk == FABM_HIST_FP32C;
     slot_dispatch(s.rhs, s.dim, [&]<class R, int D>() {
-        recur_block<R, D, 1>(bt, 0, w, s.kc, it.c, G, smem);
+        if (split)
+            recur_block_split<R, D, 1>(bt, 0, w, s.kc, it.c, G, reinterpret_cast<float *>(smem));
+        else
+            recur_block<R, D, 1>(bt, 0, w, s.kc, it.c, G, smem);
     });
 }
 

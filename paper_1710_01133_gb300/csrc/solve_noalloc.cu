@@ -171,7 +171,7 @@ extern "C" fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64
             NA_TRY(launch_hist_reduce(S + kOffPart, n_chunks, kNaL, dim, Gbuf, st));
             Gc = Gbuf;
         }
-        NA_TRY(launch_recur(rhs_id, bt, w, kc, c, kNaL, Gc, st));
+        NA_TRY(launch_recur(rhs_id, bt, w, kc, c, kNaL, false, Gc, st));
     }
     NA_TRY(cudaStreamSynchronize(st));
     unsigned long long status = 0;

@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -19,3 +20,25 @@ def gpu_lib():
     import paper_1710_01133_gb300 as fabm
     fabm.load()
     return fabm
+
+
+_PARITY = []
+
+
+@pytest.fixture
+def parity(request):
+    """check(err, bar, label=''): assert a measured error against its bar and
+    record it; with FABM_PARITY_REPORT set, the session writes every record
+    (test, label, err, bar) to that JSON file."""
+    def check(err, bar, label=""):
+        _PARITY.append({"test": request.node.name, "label": str(label),
+                        "err": float(err), "bar": float(bar)})
+        assert err <= bar, (label, err, bar)
+    return check
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("FABM_PARITY_REPORT")
+    if path and _PARITY:
+        with open(path, "w") as fh:
+            json.dump(_PARITY, fh, indent=1)

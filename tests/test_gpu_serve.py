@@ -39,7 +39,7 @@ def run_to_completion(srv, tickets, max_steps=100000):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
-def test_server_matches_standalone(gpu_lib, precision):
+def test_server_matches_standalone(gpu_lib, parity, precision):
     with gpu_lib.Server(8 << 30, precision=precision) as srv:
         tickets = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX]
         run_to_completion(srv, tickets)
@@ -49,10 +49,10 @@ def test_server_matches_standalone(gpu_lib, precision):
         if precision == "fp64":
             with gpu_lib.Solver(rhs, dim, a, h, N, p) as s:
                 ref = s.solve(y0)
-            assert rel_err(got, ref) <= 1e-12, rhs
+            parity(rel_err(got, ref), 1e-12, rhs)
         else:
             ref = oracle.solve(rhs, a, h, N, y0, params=p)
-            assert rel_err(got, ref) <= 1e-6, rhs
+            parity(rel_err(got, ref), 1e-6, rhs)
 
 
 def test_same_alone_and_in_mix_bitwise(gpu_lib):
@@ -72,7 +72,7 @@ def test_same_alone_and_in_mix_bitwise(gpu_lib):
     assert np.array_equal(alone, mixed)
 
 
-def test_budget_admission_and_release(gpu_lib):
+def test_budget_admission_and_release(gpu_lib, parity):
     """A budget that holds two of these requests: the others wait until memory
     is released, then run; every result stays correct."""
     req = ("lorenz", 3, 0.9, 1e-3, 4000, [1.0, 1.0, 1.0], LORENZ_PARAMS)
@@ -91,10 +91,10 @@ def test_budget_admission_and_release(gpu_lib):
         res = [srv.result(t) for t in tickets]
     with gpu_lib.Solver(*req[:5], req[6]) as s:
         for i, got in enumerate(res):
-            assert rel_err(got, s.solve(np.asarray(req[5]) + 0.01 * i)) <= 1e-12
+            parity(rel_err(got, s.solve(np.asarray(req[5]) + 0.01 * i)), 1e-12, "")
 
 
-def test_failures_are_isolated(gpu_lib):
+def test_failures_are_isolated(gpu_lib, parity):
     with gpu_lib.Server(64 << 20) as srv:
         bad = srv.submit("linear", 1, 0.9, 0.1, 5000, [1.0], (-50.0,))     # overflows
         huge = srv.submit("linear", 1, 0.9, 1e-3, 2 ** 24, [1.0], (1.0,))  # never fits
@@ -110,10 +110,10 @@ def test_failures_are_isolated(gpu_lib):
         assert e2.value.status == gpu_lib.FABM_ENOMEM
         got = srv.result(good)
     ref = oracle.solve("linear", 0.8, 1e-3, 500, [1.0], params=[1.0])
-    assert rel_err(got, ref) <= 1e-12
+    parity(rel_err(got, ref), 1e-12, "")
 
 
-def test_served_stream_sample_continuous(gpu_lib):
+def test_served_stream_sample_continuous(gpu_lib, parity):
     """Requests of the mixed stream submitted while others are in flight; each
     matches the oracle at the split bar."""
     reqs = served_stream(n=24, rate=1e9, k_lo=9, k_hi=11)
@@ -127,4 +127,4 @@ def test_served_stream_sample_continuous(gpu_lib):
         results = [srv.result(t) for t in tickets]
     for r, got in zip(reqs, results):
         ref = oracle.solve(r.rhs, r.alpha, r.h, r.N, r.y0, params=r.params)
-        assert rel_err(got, ref) <= 1e-6
+        parity(rel_err(got, ref), 1e-6, "")
