@@ -362,7 +362,7 @@ def main():
                     help="override the workload's N (small cases for profiling)")
     ap.add_argument("--n-traj", type=int, default=None,
                     help="keep only the first n trajectories of the workload")
-    ap.add_argument("--timing-period", type=int, default=16,
+    ap.add_argument("--timing-period", type=int, default=64,
                     help="time the kernel launches of every k-th time block")
     ap.add_argument("--n-requests", type=int, default=2000, help="served-mix: requests")
     ap.add_argument("--k-max", type=int, default=14, help="served-mix: N = 2^k, k <= k_max")

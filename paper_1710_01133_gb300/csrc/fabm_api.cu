@@ -169,7 +169,7 @@ void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int want_ctas, int
     n = std::min<int64_t>(n, max_chunks);
     n = std::max<int64_t>(n, 1);
     int64_t c = (k_end + n - 1) / n;
-    c = (c + 31) / 32 * 32;
+    c = (c + 7) / 8 * 8;  // near n chunks of equal size (one wave of want_ctas CTAs)
     *kc = c;
     *n_chunks = (int)((k_end + c - 1) / c);
 }

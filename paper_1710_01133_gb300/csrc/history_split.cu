@@ -33,9 +33,13 @@
 //
 // CTA layout (1 CTA per SM, 320 threads): warp 0 streams segments into a
 // 3-stage shared-memory ring with bulk copies; warp 1 issues the MMAs into one
-// of two TMEM accumulator sets (512 columns); warps 2..9 drain the other set,
-// each warp one TMEM lane quadrant (its columns) and the 64 targets of one
-// kind, with Kahan-compensated fp32 sums held in registers.
+// of two TMEM accumulator sets (512 columns), one weight kind at a time with
+// per-kind barriers; warps 2..9 drain the other set, each warp one TMEM lane
+// quadrant (its columns) and the 64 targets of one kind, with
+// Kahan-compensated fp32 sums held in registers.  Measured in isolation: the
+// copy ring alone streams at the HBM peak, the MMAs alone reach ~0.6 of the
+// bf16 peak (N = 64 per MMA), and the drain's arithmetic on the MMA warp's
+// sub-partition costs ~15% (issue slots shared with the MMA thread).
 // Every wait is bounded; on timeout the CTA sets an error flag, waits for its
 // own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -197,9 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageStride);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;
-    uint64_t *acc_empty = acc_full + 2;
-    uint64_t *done = acc_empty + 2;
+    uint64_t *acc_full = empty + kStages;  // [buffer][kind]
+    uint64_t *acc_empty = acc_full + 4;    // [buffer][kind]
+    uint64_t *done = acc_empty + 4;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1), mbar_init(&empty[i], 1);
-        for (int i = 0; i < 2; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], kEpiWarps);
+        for (int i = 0; i < 4; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], kEpiWarps / 2);
         mbar_init(done, 1);
         fence_mbar_init();
     }
@@ -251,36 +255,42 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 const uint32_t ph = (i / kStages) & 1;
                 const int b = i & 1;
                 const uint32_t bph = (i >> 1) & 1;
-                if (!mbar_wait(&full[st], ph, kWaitCycles) ||
-                    !mbar_wait(&acc_empty[b], bph ^ 1, kWaitCycles)) {
+                if (!mbar_wait(&full[st], ph, kWaitCycles)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
                 const uint32_t sF = smem_u32(smem + st * kStageStride);
                 const uint32_t sW = sF + kFBytes;
+                // one kind at a time, each with its own accumulator barriers, so
+                // the drain of kind 0 starts while the MMAs of kind 1 run
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
+                    if (!mbar_wait(&acc_empty[b * 2 + k], bph ^ 1, kWaitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     const uint32_t d0 = tmem + b * 256 + k * 64;  // level 0
                     const uint32_t d12 = d0 + 128;                // levels 1 and 2
+                    // descriptors as base word + offset/16: few instructions per
+                    // MMA, since this thread shares its issue slots with two
+                    // drain warps
+                    const uint32_t a_lo = smem_desc_lo(sF, 2048);
+                    const uint32_t b_lo = smem_desc_lo(sW + k * 3 * (kHk * 128), 128);
+                    constexpr uint32_t a_hi = smem_desc_hi(128), b_hi = smem_desc_hi(128);
 #pragma unroll
                     for (int s = 0; s < kSeg / 16; ++s) {
-                        uint64_t A[3], Bw[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            A[q] = smem_desc(sF + q * (kFBytes / 3) + s * 4096, 2048, 128);
-                            Bw[q] = smem_desc(sW + (k * 3 + q) * (kHk * 128) + s * 256, 128, 128);
-                        }
-                        mma_bf16(d0, A[0], Bw[0], idesc, s > 0);
-                        mma_bf16(d12, A[0], Bw[1], idesc, s > 0);
-                        mma_bf16(d12, A[1], Bw[0], idesc, 1);
-                        mma_bf16(d12, A[0], Bw[2], idesc, 1);
-                        mma_bf16(d12, A[1], Bw[1], idesc, 1);
-                        mma_bf16(d12, A[2], Bw[0], idesc, 1);
+                        constexpr uint32_t fq = (kFBytes / 3) >> 4, wq = (kHk * 128) >> 4;
+                        const uint32_t ao = a_lo + s * (4096 >> 4), bo = b_lo + s * (256 >> 4);
+                        mma_bf16_split6(d0, d12, desc_join(ao, a_hi), desc_join(ao + fq, a_hi),
+                                        desc_join(ao + 2 * fq, a_hi), desc_join(bo, b_hi),
+                                        desc_join(bo + wq, b_hi), desc_join(bo + 2 * wq, b_hi),
+                                        idesc, s == 0);
                     }
+                    mma_commit(&acc_full[b * 2 + k]);
                 }
+                if (!ok) break;
                 mma_commit(&empty[st]);
-                mma_commit(&acc_full[b]);
             }
             mma_commit(done);
             if (!mbar_wait(done, 0, kWaitCycles)) ok = false;
@@ -311,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
                 ew_next = a.Ew[(a.c - sn) * 2 + kind];
             }
-            if (!mbar_wait(&acc_full[b], bph, kWaitCycles)) {
+            if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles)) {
                 ok = false;
                 break;
             }
@@ -348,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if (lane == 0) mbar_arrive(&acc_empty[b * 2 + kind]);
         }
         if (ok && col < a.cols) {
             float2 *out = a.part + ((int64_t)(ch * 2 + kind) * kSeg + t0) * a.cols + col;

@@ -16,12 +16,11 @@
 // pre-multiplied by h^alpha, so the owner's accumulate of the newest point is
 // already y^P (and y0 + h^alpha S^C): six dependent FP64 operations per step
 // for a Lorenz-type component (accumulate, f, corrector, f).
-// GB300 runs a double-precision warp instruction in one 64-cycle slot of its
-// sub-partition's FP64 unit whatever the number of active lanes, so one warp
-// per component spreads the serial chain over the FP64 units of several
-// sub-partitions, and adding f_k to all pending targets of a lane costs one
-// instruction.  The time-only part of f (forcing) is evaluated for every target
-// at block start, off the chain.
+// On GB300 a warp FP64 instruction takes the FP64 pipe for many cycles
+// whatever the number of active lanes, so adding f_k to all pending targets
+// of a warp costs one instruction per sum, and the components run on separate
+// warps so that their chains overlap.  The time-only part of f (forcing) is
+// evaluated for every target at block start, off the chain.
 #pragma once
 
 #include "rhs.cuh"
@@ -202,7 +201,7 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
 // that of the split history; GB300 issues its fp32 at 64 times the FP64 rate
 // and a float-float operation completes in fewer cycles than one FP64
 // operation, so the chain is shorter and wide batches no longer saturate the
-// FP64 units.
+// FP64 pipe.
 template <int D, int TPL>
 __host__ __device__ constexpr int recur_split_smem_floats()
 {

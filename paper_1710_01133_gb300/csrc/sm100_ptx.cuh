@@ -132,6 +132,46 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// The six products of order <= 2 of three-term splits a = a0+a1+a2 and
+// b = b0+b1+b2 for one K step: a0*b0 into d0 (accumulating unless `first`),
+// a0*b1 (idem), a1*b0, a0*b2, a1*b1, a2*b0 into d12.  One statement, so one
+// predicate setup serves the six MMAs.
+__device__ __forceinline__ void mma_bf16_split6(uint32_t d0, uint32_t d12, uint64_t a0,
+                                                uint64_t a1, uint64_t a2, uint64_t b0,
+                                                uint64_t b1, uint64_t b2, uint32_t idesc,
+                                                uint32_t first)
+{
+    asm volatile(
+        "{\n .reg .pred pa, pt;\n"
+        " setp.eq.b32 pa, %9, 0;\n"
+        " setp.eq.b32 pt, %9, %9;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %5, %8, pa;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %6, %8, pa;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %5, %8, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %7, %8, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %6, %8, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %5, %8, pt;\n}\n" ::"r"(d0),
+        "r"(d12), "l"(a0), "l"(a1), "l"(a2), "l"(b0), "l"(b1), "l"(b2), "r"(idesc), "r"(first)
+        : "memory");
+}
+
+// Descriptor of a no-swizzle K-major operand at shared address addr with the
+// given leading/stride byte offsets, as two 32-bit words; the address field
+// is the low 14 bits of `lo`, so a byte offset o (o/16 added to lo) moves it
+// as long as the address stays below 256 KB.
+__device__ __forceinline__ uint32_t smem_desc_lo(uint32_t addr, uint32_t lbo)
+{
+    return ((addr >> 4) & 0x3FFF) | (((lbo >> 4) & 0x3FFF) << 16);
+}
+__host__ __device__ constexpr uint32_t smem_desc_hi(uint32_t sbo)
+{
+    return ((sbo >> 4) & 0x3FFF) | (1u << 14);
+}
+__device__ __forceinline__ uint64_t desc_join(uint32_t lo, uint32_t hi)
+{
+    return ((uint64_t)hi << 32) | lo;
+}
+
 // Arrive on bar once every tcgen05 operation issued so far by this thread is done.
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
