@@ -44,7 +44,15 @@ WORKLOADS = {
     "ml-scalar": lambda: wl.ml_scalar(),
     "duffing-sweep": lambda: wl.duffing_sweep(),
     "lorenz-long": lambda: wl.lorenz_long(),
+    "lcr-sweep": lambda: _lcr_sweep(),
 }
+
+
+def _lcr_sweep():
+    """Sec. 5's forced LCR circuit, 1024 forcing amplitudes in [0, 0.2], split precision."""
+    w = wl.lcr_sweep(B=1024, N=2 ** 14)
+    w.precision = "split"
+    return w
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
 L2_FLUSH_BYTES = 256 << 20

@@ -166,6 +166,25 @@ fabm_status fabm_set_graphs(fabm_solver *s, int enable);
  * distance form d = (n+1) - k used by the kernels.  Any of B, A, D may be NULL. */
 fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D);
 
+/* Stroboscopic samples of solved trajectories, the sampling behind the
+ * bifurcation diagram of Sec. 5 (the attractor of the forced LCR system seen
+ * once per forcing period 2 pi / omega, plotted against the amplitude f).
+ *   Y        device array B x (N+1) x dim, the layout fabm_solve_batch writes
+ *            (out_on_device = 1); row n of trajectory b is t_n = n h;
+ *   N_each   device array of B per-trajectory step counts (rows beyond N_each[b]
+ *            are not read), or NULL for N;
+ *   samples  device array B x n_samples: samples[b][j] = component comp of
+ *            trajectory b at t = t0 + j period, linearly interpolated between the
+ *            two grid points around it; NaN where t lies outside [0, N_each[b] h]
+ *            or N_each[b] is outside 1..N.
+ * Caller-owned device memory; runs on the current device and synchronizes it.
+ * FABM_EINVAL for NULL pointers, B or n_samples < 0, N < 1, dim outside
+ * 1..FABM_MAX_DIM, comp outside 0..dim-1, h or period not positive, t0 not
+ * finite; FABM_ECUDA if the launch fails. */
+fabm_status fabm_stroboscope(const double *Y, int64_t B, int64_t N, int dim,
+                             const int64_t *N_each, double h, double t0, double period,
+                             int64_t n_samples, int comp, double *samples);
+
 /* Number of kernel launches made by the last solve call on this solver. */
 int64_t fabm_last_launch_count(const fabm_solver *s);
 
@@ -240,6 +259,28 @@ fabm_status fabm_server_poll(fabm_server *s, int64_t ticket, int *state);
  * FABM_EBUSY if it has not finished; the request's own error if it failed
  * (FABM_ENONFINITE, or FABM_ENOMEM when it can never fit the budget). */
 fabm_status fabm_server_result(fabm_server *s, int64_t ticket, double *out);
+/* Checkpoint of a waiting or running request at the current block boundary:
+ * its problem, the index of the next block, the history f and solution rows
+ * computed so far, the far-history sums of the next block and its status,
+ * serialized into buf (host memory, cap bytes, in the host's byte order).
+ * *size receives the bytes needed; with buf NULL only the size is reported.
+ * The request keeps running; fabm_server_cancel after a checkpoint evicts it
+ * (its device memory is released).  FABM_EINVAL for an unknown or finished
+ * ticket or cap < *size. */
+fabm_status fabm_server_checkpoint(fabm_server *s, int64_t ticket, void *buf, size_t cap,
+                                   size_t *size);
+/* Queue a request from a checkpoint taken on a server of the same precision
+ * (this one or another); once admitted it continues from the saved block and
+ * gives the same result, bit for bit, as a run that was never interrupted.
+ * FABM_EINVAL for a buffer that is not a consistent checkpoint or a precision
+ * mismatch. */
+fabm_status fabm_server_resume(fabm_server *s, const void *buf, size_t size, int64_t *ticket);
+/* Steps N and dimension of a known request (for sizing the result buffer of a
+ * resumed one).  FABM_EINVAL for an unknown ticket. */
+fabm_status fabm_server_shape(fabm_server *s, int64_t ticket, int64_t *N, int *dim);
+/* Drop a request in any state; a running one releases its device memory at
+ * once.  The ticket becomes unknown.  FABM_EINVAL for an unknown ticket. */
+fabm_status fabm_server_cancel(fabm_server *s, int64_t ticket);
 /* Steps run, kernel launches made, device bytes held by admitted requests. */
 fabm_status fabm_server_stats(const fabm_server *s, int64_t *steps, int64_t *launches,
                               size_t *bytes_in_use);

@@ -176,3 +176,19 @@ def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
         None if ne is None else ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         _dp(out), int(threads), int(compensated)), "solve_batch")
     return out
+
+
+def stroboscope(Y, h, t0, period, n_samples, comp=0):
+    """Samples of trajectories Y (B x (N+1) x dim on t_n = n h) at
+    t_j = t0 + j period, by linear interpolation between the two grid points
+    around t_j (np.interp); NaN outside [0, N h].  This is the sampling of the
+    bifurcation diagram of Sec. 5 (once per forcing period 2 pi / omega)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    B, rows = Y.shape[0], Y.shape[1]
+    t = t0 + np.arange(n_samples) * period
+    grid = np.arange(rows) * h
+    out = np.empty((B, n_samples))
+    for b in range(B):
+        out[b] = np.interp(t, grid, Y[b, :, comp])
+    out[:, (t < 0) | (t > (rows - 1) * h)] = np.nan
+    return out

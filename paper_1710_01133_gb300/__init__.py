@@ -26,7 +26,9 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
             "fabm_solve_noalloc", "fabm_set_history_kernel", "fabm_get_history_kernel",
             "fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
-            "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune")
+            "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
+            "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
+            "fabm_server_cancel", "fabm_server_shape")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -83,8 +85,14 @@ def load(build_if_missing: bool = True):
     lib.fabm_server_result.argtypes = [vp, i64, P(d)]
     lib.fabm_server_stats.argtypes = [vp, P(i64), P(i64), P(ctypes.c_size_t)]
     lib.fabm_server_destroy.argtypes = [vp]
+    lib.fabm_server_checkpoint.argtypes = [vp, i64, vp, ctypes.c_size_t, P(ctypes.c_size_t)]
+    lib.fabm_server_resume.argtypes = [vp, vp, ctypes.c_size_t, P(i64)]
+    lib.fabm_server_cancel.argtypes = [vp, i64]
+    lib.fabm_server_shape.argtypes = [vp, i64, P(i64), P(i)]
     for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
-              "fabm_server_result", "fabm_server_stats", "fabm_server_destroy"):
+              "fabm_server_result", "fabm_server_stats", "fabm_server_destroy",
+              "fabm_server_checkpoint", "fabm_server_resume", "fabm_server_cancel",
+              "fabm_server_shape"):
         getattr(lib, f).restype = i
     lib.fabm_autotune.argtypes = [vp, i64, P(d), P(d), i64, i, P(d), P(i), P(i), P(i)]
     lib.fabm_autotune.restype = i
@@ -92,6 +100,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
+    lib.fabm_stroboscope.argtypes = [vp, i64, i64, i, vp, d, d, d, i64, i, vp]
+    lib.fabm_stroboscope.restype = i
     for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
@@ -127,6 +137,29 @@ def fabm_create(dim, alpha, h, N, rhs_id, params, precision=FABM_FP64):
                               _dp(p) if p.size else None, int(p.size), int(precision),
                               ctypes.byref(handle)))
     return handle
+
+
+def fabm_stroboscope(Y, N, h, t0, period, n_samples, comp=0, N_each=None):
+    """Samples of the device trajectories Y (torch tensor B x (N+1) x dim on the
+    GPU) at t0 + j*period, linearly interpolated; returns a device tensor
+    B x n_samples.  N_each: optional device int64 tensor of B step counts."""
+    import torch
+    if not (Y.is_cuda and Y.dtype == torch.float64 and Y.is_contiguous() and Y.dim() == 3):
+        raise ValueError("Y must be a contiguous float64 CUDA tensor B x (N+1) x dim")
+    B, rows, dim = Y.shape
+    if rows != N + 1:
+        raise ValueError(f"Y has {rows} rows per trajectory, expected N+1 = {N + 1}")
+    out = torch.empty((B, int(n_samples)), dtype=torch.float64, device=Y.device)
+    ne = None
+    if N_each is not None:
+        if not (N_each.is_cuda and N_each.dtype == torch.int64 and N_each.numel() == B):
+            raise ValueError("N_each must be a CUDA int64 tensor of B entries")
+        ne = ctypes.c_void_p(N_each.data_ptr())
+    with torch.cuda.device(Y.device):
+        _check(load().fabm_stroboscope(ctypes.c_void_p(Y.data_ptr()), int(B), int(N), int(dim),
+                                       ne, float(h), float(t0), float(period), int(n_samples),
+                                       int(comp), ctypes.c_void_p(out.data_ptr())))
+    return out
 
 
 def fabm_solve(handle, y0, out):
@@ -317,7 +350,6 @@ class Server:
         _check(load().fabm_server_create(int(budget_bytes), self.precision, int(max_slots),
                                          ctypes.byref(h)))
         self.handle = h
-        self._dims = {}
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -344,7 +376,6 @@ class Server:
                            _dp(p) if p.size else None, int(p.size), _dp(y))
         t = ctypes.c_int64()
         _check(load().fabm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
-        self._dims[t.value] = (int(N), int(dim))
         return t.value
 
     def step(self):
@@ -357,14 +388,36 @@ class Server:
         _check(load().fabm_server_poll(self.handle, int(ticket), ctypes.byref(st)))
         return st.value
 
+    def shape(self, ticket):
+        """(N, dim) of a known request."""
+        n, d = ctypes.c_int64(), ctypes.c_int()
+        _check(load().fabm_server_shape(self.handle, int(ticket), ctypes.byref(n), ctypes.byref(d)))
+        return n.value, d.value
+
     def result(self, ticket) -> np.ndarray:
-        N, dim = self._dims[ticket]
+        N, dim = self.shape(ticket)
         out = np.empty((N + 1, dim))
-        st = load().fabm_server_result(self.handle, int(ticket), _dp(out))
-        if st != FABM_EBUSY:
-            self._dims.pop(ticket, None)
-        _check(st)
+        _check(load().fabm_server_result(self.handle, int(ticket), _dp(out)))
         return out
+
+    def checkpoint(self, ticket) -> bytes:
+        """Serialized state of a waiting or running request (it keeps running)."""
+        size = ctypes.c_size_t()
+        _check(load().fabm_server_checkpoint(self.handle, int(ticket), None, 0, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        _check(load().fabm_server_checkpoint(self.handle, int(ticket), buf, size.value,
+                                             ctypes.byref(size)))
+        return buf.raw[: size.value]
+
+    def resume(self, state: bytes) -> int:
+        """Queue a request from a checkpoint; returns its ticket."""
+        t = ctypes.c_int64()
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(load().fabm_server_resume(self.handle, buf, len(state), ctypes.byref(t)))
+        return t.value
+
+    def cancel(self, ticket):
+        _check(load().fabm_server_cancel(self.handle, int(ticket)))
 
     def stats(self):
         s, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()

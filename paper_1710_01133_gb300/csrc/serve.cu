@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -223,6 +224,28 @@ fabm_status srv_fail(fabm_status st, const char *fmt, ...)
                             "%s failed: %s", #expr, cudaGetErrorString(e_));                 \
     } while (0)
 
+// State of a request taken at a block boundary (fabm_server_checkpoint): the
+// next block to run, the history f and the solution rows known so far, both
+// far-history buffers and the non-finite status word.
+struct Ckpt {
+    int64_t c = 0;
+    unsigned long long status = ~0ull;
+    std::vector<double> F, Y, G;  // rows x dim, rows x dim, 2 x 2 x kSL x dim
+};
+
+// Layout of a serialized checkpoint: this header, then F and Y (rows x dim
+// each) and G (2 x 2 x kSL x dim), doubles in the host's byte order.
+constexpr char kCkptMagic[8] = {'F', 'A', 'B', 'M', 'C', 'K', 'P', '1'};
+struct CkptHead {
+    char magic[8];
+    int32_t precision, dim, rhs, n_params;
+    double alpha, h;
+    int64_t N, c, rows;
+    unsigned long long status;
+    double params[kMaxParams];
+    double y0[FABM_MAX_DIM];
+};
+
 struct Req {
     int64_t ticket;
     int dim, rhs;
@@ -231,6 +254,7 @@ struct Req {
     double params[kMaxParams];
     int n_params;
     double y0[FABM_MAX_DIM];
+    std::shared_ptr<const Ckpt> ckpt;  // set for a resumed request
 };
 
 struct Slot {
@@ -325,6 +349,7 @@ struct fabm_server {
     std::deque<Req> queue;
     std::vector<Slot> slots;
     std::unordered_map<int64_t, Result> results;
+    std::unordered_map<int64_t, std::pair<int64_t, int>> shapes;  // ticket -> (N, dim)
     int64_t next_ticket = 1;
     cudaStream_t sR = nullptr, sG = nullptr;
     cudaEvent_t evUp = nullptr;
@@ -388,12 +413,18 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             break;  // retry when memory frees up
         }
         slot_layout(s, hk, w_ext);
+        if (r.ckpt) s.c = r.ckpt->c;
         S->queue.pop_front();
         S->in_use += bytes;
         S->results[r.ticket] = {FABM_REQ_RUNNING, FABM_OK, {}};
         fresh.push_back((int)S->slots.size());
         S->slots.push_back(s);
     }
+    // new slots needing initial values first, resumed ones after them
+    std::stable_partition(fresh.begin(), fresh.end(),
+                          [&](int i) { return !S->slots[i].req.ckpt; });
+    int n_init = 0;
+    for (int i : fresh) n_init += S->slots[i].req.ckpt ? 0 : 1;
     const int ns = (int)S->slots.size();
     *n_waiting = (int)S->queue.size();
     *n_active = ns;
@@ -441,17 +472,28 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             SRV_TRY(cudaMemcpyAsync(s.dev.y0, s.req.y0, sizeof(double) * s.req.dim, cudaMemcpyHostToDevice, S->sR));
             SRV_TRY(cudaMemcpyAsync(s.dev.params, par, sizeof par, cudaMemcpyHostToDevice, S->sR));
             SRV_TRY(cudaMemcpyAsync(s.dev.Nb, &s.req.N, sizeof(int64_t), cudaMemcpyHostToDevice, S->sR));
-            SRV_TRY(cudaMemsetAsync(s.dev.status, 0xff, sizeof(unsigned long long), S->sR));
+            if (const Ckpt *k = s.req.ckpt.get()) {  // resumed: the saved state
+                const size_t rows = k->F.size() / s.req.dim;
+                SRV_TRY(cudaMemcpyAsync(s.dev.F, k->F.data(), sizeof(double) * rows * s.req.dim, cudaMemcpyHostToDevice, S->sR));
+                SRV_TRY(cudaMemcpyAsync(s.dev.Y, k->Y.data(), sizeof(double) * rows * s.req.dim, cudaMemcpyHostToDevice, S->sR));
+                SRV_TRY(cudaMemcpyAsync(s.dev.G, k->G.data(), sizeof(double) * k->G.size(), cudaMemcpyHostToDevice, S->sR));
+                SRV_TRY(cudaMemcpyAsync(s.dev.status, &k->status, sizeof k->status, cudaMemcpyHostToDevice, S->sR));
+            } else {
+                SRV_TRY(cudaMemsetAsync(s.dev.status, 0xff, sizeof(unsigned long long), S->sR));
+            }
         }
         int64_t wmax = 0;
         for (int i : fresh) wmax = std::max(wmax, S->slots[i].dev.w_ext);
         const unsigned gx = (unsigned)std::min<int64_t>((wmax + 256) / 256, 64);
         weights_slots_kernel<<<dim3(gx, (unsigned)fresh.size()), 256, 0, S->sR>>>(S->d_slots, S->d_idx);
         SRV_TRY(cudaGetLastError());
-        init_slots_kernel<<<(unsigned)((fresh.size() + 127) / 128), 128, 0, S->sR>>>(
-            S->d_slots, S->d_idx, (int)fresh.size());
-        SRV_TRY(cudaGetLastError());
-        S->launches += 2;
+        S->launches += 1;
+        if (n_init > 0) {
+            init_slots_kernel<<<(unsigned)((n_init + 127) / 128), 128, 0, S->sR>>>(
+                S->d_slots, S->d_idx, n_init);
+            SRV_TRY(cudaGetLastError());
+            S->launches += 1;
+        }
     }
     SRV_TRY(cudaEventRecord(S->evUp, S->sR));
     SRV_TRY(cudaStreamWaitEvent(S->sG, S->evUp, 0));
@@ -475,6 +517,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     keep.reserve(ns);
     for (int i = 0; i < ns; ++i) {
         Slot &s = S->slots[i];
+        s.req.ckpt.reset();  // restored on the device by now
         s.c += 1;
         if (s.c < s.nblk) {
             keep.push_back(s);
@@ -553,6 +596,7 @@ fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *t
     r.ticket = S->next_ticket++;
     S->queue.push_back(r);
     S->results[r.ticket] = {FABM_REQ_WAITING, FABM_OK, {}};
+    S->shapes[r.ticket] = {r.N, r.dim};
     *ticket = r.ticket;
     return FABM_OK;
 }
@@ -596,10 +640,142 @@ fabm_status fabm_server_result(fabm_server *S, int64_t ticket, double *out)
     const fabm_status st = r.status;
     if (!r.y.empty()) std::memcpy(out, r.y.data(), sizeof(double) * r.y.size());
     S->results.erase(it);
+    S->shapes.erase(ticket);
     if (st != FABM_OK)
         return srv_fail(st, "request %lld failed (%s)", (long long)ticket,
                         st == FABM_ENONFINITE ? "non-finite value" : "does not fit the budget");
     return FABM_OK;
+}
+
+fabm_status fabm_server_checkpoint(fabm_server *S, int64_t ticket, void *buf, size_t cap,
+                                   size_t *size)
+{
+    set_last_error("");
+    if (!S || !size) return srv_fail(FABM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    const Req *r = nullptr;
+    const Slot *slot = nullptr;
+    for (const Slot &sl : S->slots)
+        if (sl.req.ticket == ticket) slot = &sl, r = &sl.req;
+    if (!r)
+        for (const Req &q : S->queue)
+            if (q.ticket == ticket) r = &q;
+    if (!r) return srv_fail(FABM_EINVAL, "request %lld is not waiting or running", (long long)ticket);
+    const int64_t c = slot ? slot->c : (r->ckpt ? r->ckpt->c : 0);
+    const int64_t rows = c == 0 ? 0 : std::min<int64_t>(r->N, c * kSL) + 1;
+    const size_t n_g = (size_t)4 * kSL * r->dim;
+    const size_t need = sizeof(CkptHead) + sizeof(double) * ((size_t)2 * rows * r->dim + n_g);
+    *size = need;
+    if (!buf) return FABM_OK;
+    if (cap < need) return srv_fail(FABM_EINVAL, "checkpoint needs %zu bytes, buffer has %zu", need, cap);
+    CkptHead hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.precision = S->precision, hd.dim = r->dim, hd.rhs = r->rhs, hd.n_params = r->n_params;
+    hd.alpha = r->alpha, hd.h = r->h, hd.N = r->N, hd.c = c, hd.rows = rows;
+    hd.status = ~0ull;
+    for (int i = 0; i < kMaxParams; ++i) hd.params[i] = r->params[i];
+    for (int i = 0; i < FABM_MAX_DIM; ++i) hd.y0[i] = r->y0[i];
+    uint8_t *p = static_cast<uint8_t *>(buf);
+    double *F = reinterpret_cast<double *>(p + sizeof hd);
+    double *Y = F + rows * r->dim;
+    double *G = Y + rows * r->dim;
+    if (slot) {  // between steps both streams are idle: plain copies
+        const size_t n = sizeof(double) * rows * r->dim;
+        SRV_TRY(cudaMemcpy(F, slot->dev.F, n, cudaMemcpyDeviceToHost));
+        SRV_TRY(cudaMemcpy(Y, slot->dev.Y, n, cudaMemcpyDeviceToHost));
+        SRV_TRY(cudaMemcpy(G, slot->dev.G, sizeof(double) * n_g, cudaMemcpyDeviceToHost));
+        SRV_TRY(cudaMemcpy(&hd.status, slot->dev.status, sizeof hd.status, cudaMemcpyDeviceToHost));
+    } else if (r->ckpt) {
+        std::memcpy(F, r->ckpt->F.data(), sizeof(double) * r->ckpt->F.size());
+        std::memcpy(Y, r->ckpt->Y.data(), sizeof(double) * r->ckpt->Y.size());
+        std::memcpy(G, r->ckpt->G.data(), sizeof(double) * n_g);
+        hd.status = r->ckpt->status;
+    } else {
+        std::memset(G, 0, sizeof(double) * n_g);
+    }
+    std::memcpy(p, &hd, sizeof hd);
+    return FABM_OK;
+}
+
+fabm_status fabm_server_resume(fabm_server *S, const void *buf, size_t size, int64_t *ticket)
+{
+    set_last_error("");
+    if (!S || !buf || !ticket) return srv_fail(FABM_EINVAL, "NULL argument");
+    if (size < sizeof(CkptHead)) return srv_fail(FABM_EINVAL, "checkpoint of %zu bytes is truncated", size);
+    CkptHead hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0) return srv_fail(FABM_EINVAL, "not a checkpoint");
+    if (hd.precision != S->precision)
+        return srv_fail(FABM_EINVAL, "checkpoint of precision %d on a server of precision %d",
+                        hd.precision, S->precision);
+    if (hd.dim < 1 || hd.dim > FABM_MAX_DIM || !rhs_supports_dim(hd.rhs, hd.dim) ||
+        hd.n_params < rhs_n_params(hd.rhs) || hd.n_params > kMaxParams ||
+        !(hd.alpha > 0.0 && hd.alpha < 1.0) || !(hd.h > 0.0) || hd.N < 1 || hd.N > (1LL << 31))
+        return srv_fail(FABM_EINVAL, "checkpoint header is invalid");
+    const int64_t nblk = (hd.N + kSL - 1) / kSL;
+    const int64_t rows = hd.c == 0 ? 0 : std::min<int64_t>(hd.N, hd.c * kSL) + 1;
+    const size_t n_g = (size_t)4 * kSL * hd.dim;
+    if (hd.c < 0 || hd.c >= nblk || hd.rows != rows ||
+        size != sizeof hd + sizeof(double) * ((size_t)2 * rows * hd.dim + n_g))
+        return srv_fail(FABM_EINVAL, "checkpoint sizes are inconsistent");
+    Req r{};
+    r.dim = hd.dim, r.rhs = hd.rhs, r.alpha = hd.alpha, r.h = hd.h, r.N = hd.N;
+    r.n_params = hd.n_params;
+    for (int i = 0; i < kMaxParams; ++i) r.params[i] = hd.params[i];
+    for (int i = 0; i < FABM_MAX_DIM; ++i) r.y0[i] = hd.y0[i];
+    if (hd.c > 0) {
+        auto k = std::make_shared<Ckpt>();
+        const double *F = reinterpret_cast<const double *>(static_cast<const uint8_t *>(buf) + sizeof hd);
+        k->c = hd.c;
+        k->status = hd.status;
+        k->F.assign(F, F + rows * hd.dim);
+        k->Y.assign(F + rows * hd.dim, F + 2 * rows * hd.dim);
+        k->G.assign(F + 2 * rows * hd.dim, F + 2 * rows * hd.dim + n_g);
+        r.ckpt = std::move(k);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    r.ticket = S->next_ticket++;
+    S->queue.push_back(r);
+    S->results[r.ticket] = {FABM_REQ_WAITING, FABM_OK, {}};
+    S->shapes[r.ticket] = {r.N, r.dim};
+    *ticket = r.ticket;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_shape(fabm_server *S, int64_t ticket, int64_t *N, int *dim)
+{
+    set_last_error("");
+    if (!S || !N || !dim) return srv_fail(FABM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->shapes.find(ticket);
+    if (it == S->shapes.end()) return srv_fail(FABM_EINVAL, "unknown ticket %lld", (long long)ticket);
+    *N = it->second.first;
+    *dim = it->second.second;
+    return FABM_OK;
+}
+
+fabm_status fabm_server_cancel(fabm_server *S, int64_t ticket)
+{
+    set_last_error("");
+    if (!S) return srv_fail(FABM_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) return srv_fail(FABM_EINVAL, "unknown ticket %lld", (long long)ticket);
+    S->results.erase(it);
+    S->shapes.erase(ticket);
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+        if (q->ticket == ticket) {
+            S->queue.erase(q);
+            return FABM_OK;
+        }
+    for (size_t i = 0; i < S->slots.size(); ++i)
+        if (S->slots[i].req.ticket == ticket) {
+            SRV_TRY(cudaFreeAsync(S->slots[i].mem, S->sR));
+            S->in_use -= S->slots[i].bytes;
+            S->slots.erase(S->slots.begin() + (std::ptrdiff_t)i);
+            return FABM_OK;
+        }
+    return FABM_OK;  // finished: its result is dropped
 }
 
 fabm_status fabm_server_stats(const fabm_server *S, int64_t *steps, int64_t *launches,

@@ -128,3 +128,79 @@ def test_served_stream_sample_continuous(gpu_lib, parity):
     for r, got in zip(reqs, results):
         ref = oracle.solve(r.rhs, r.alpha, r.h, r.N, r.y0, params=r.params)
         parity(rel_err(got, ref), 1e-6, "")
+
+
+def _uninterrupted(gpu_lib, req, precision):
+    with gpu_lib.Server(8 << 30, precision=precision) as srv:
+        t = srv.submit(*req[:5], req[5], req[6])
+        run_to_completion(srv, [t])
+        return srv.result(t)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("blocks", [0, 1, 2, 40])
+def test_checkpoint_resume_on_another_server_bitwise(gpu_lib, precision, blocks):
+    """A request checkpointed after `blocks` steps and resumed on a fresh
+    server (in a mix) gives the uninterrupted result bit for bit."""
+    req = MIX[0]
+    ref = _uninterrupted(gpu_lib, req, precision)
+    with gpu_lib.Server(8 << 30, precision=precision) as a:
+        t = a.submit(*req[:5], req[5], req[6])
+        other = a.submit(*MIX[2][:5], MIX[2][5], MIX[2][6])
+        for _ in range(blocks):
+            a.step()
+        state = a.checkpoint(t)
+        run_to_completion(a, [t, other])
+        assert np.array_equal(a.result(t), ref)  # checkpointing does not disturb it
+    with gpu_lib.Server(8 << 30, precision=precision) as b:
+        mix = [b.submit(r, d, al, h, N, y0, p) for r, d, al, h, N, y0, p in MIX[1:4]]
+        t2 = b.resume(state)
+        assert b.shape(t2) == (req[4], req[1])
+        run_to_completion(b, [t2] + mix)
+        got = b.result(t2)
+    assert np.array_equal(got, ref)
+
+
+def test_evict_and_resume_releases_memory(gpu_lib):
+    req = MIX[0]
+    ref = _uninterrupted(gpu_lib, req, "fp64")
+    with gpu_lib.Server(8 << 30) as srv:
+        t = srv.submit(*req[:5], req[5], req[6])
+        for _ in range(17):
+            srv.step()
+        assert srv.stats()["bytes_in_use"] > 0
+        state = srv.checkpoint(t)
+        srv.cancel(t)
+        assert srv.stats()["bytes_in_use"] == 0
+        with pytest.raises(gpu_lib.FabmError):
+            srv.poll(t)
+        t2 = srv.resume(state)
+        run_to_completion(srv, [t2])
+        assert np.array_equal(srv.result(t2), ref)
+
+
+def test_checkpoint_errors(gpu_lib):
+    req = MIX[1]
+    with gpu_lib.Server(8 << 30) as srv:
+        t = srv.submit(*req[:5], req[5], req[6])
+        srv.step()
+        state = bytearray(srv.checkpoint(t))
+        with pytest.raises(gpu_lib.FabmError) as e:
+            srv.resume(bytes(state[:-8]))               # truncated
+        assert e.value.status == gpu_lib.FABM_EINVAL
+        bad = bytearray(state)
+        bad[0] ^= 0xFF                                  # not a checkpoint
+        with pytest.raises(gpu_lib.FabmError):
+            srv.resume(bytes(bad))
+        with pytest.raises(gpu_lib.FabmError):
+            srv.checkpoint(12345)                       # unknown ticket
+        with pytest.raises(gpu_lib.FabmError):
+            srv.cancel(12345)
+        run_to_completion(srv, [t])
+        with pytest.raises(gpu_lib.FabmError):
+            srv.checkpoint(t)                           # finished
+        srv.result(t)
+    with gpu_lib.Server(8 << 30, precision="split") as other:
+        with pytest.raises(gpu_lib.FabmError) as e:
+            other.resume(bytes(state))                  # precision mismatch
+        assert e.value.status == gpu_lib.FABM_EINVAL

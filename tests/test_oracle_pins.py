@@ -322,3 +322,19 @@ def test_planted_mistakes_are_caught():
     }
     for name, (w, hf, g) in mistakes.items():
         assert not _pins_hold(w, hf, g, alpha), name
+
+
+def test_stroboscope_exact_on_linear_trajectories():
+    """Linear interpolation reproduces a trajectory linear in t at any sample
+    time; samples outside [0, N h] are NaN (the sampling of Sec. 5's
+    bifurcation diagram)."""
+    h, N = 0.25, 40
+    t = np.arange(N + 1) * h
+    Y = np.stack([np.stack([2.0 - 3.0 * t, 0.5 * t], axis=1),
+                  np.stack([1.0 + t, -t], axis=1)])
+    tj = -0.3 + np.arange(12) * 0.97
+    s = oracle.stroboscope(Y, h, -0.3, 0.97, 12, comp=0)
+    inside = (tj >= 0) & (tj <= N * h)
+    np.testing.assert_allclose(s[0, inside], 2.0 - 3.0 * tj[inside], rtol=1e-14)
+    np.testing.assert_allclose(s[1, inside], 1.0 + tj[inside], rtol=1e-14)
+    assert np.all(np.isnan(s[:, ~inside]))
