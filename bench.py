@@ -55,6 +55,7 @@ def _lcr_sweep():
     return w
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
+FP32_FLOP_PER_CLK_PER_SM = 256  # 128 FFMA per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -200,6 +201,15 @@ def roofline(kind, ks, precision, clocks, w):
                     "frac": achieved / bf16 if bf16 else None,
                     "peak_note": f"dense bf16 burst {src} (MEASURED_PEAKS.json); achieved counts "
                                  "the 6 bf16 products per algorithmic multiply-add"})
+    elif kind == "recurrence" and precision == "split":
+        # float-float on the FP32 pipe: algorithmic near-field FLOP/s against FP32 FMA
+        peak = FP32_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
+        achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                    "frac": achieved / peak if peak else None,
+                    "peak_note": "FP32 FMA pipe: 128 FFMA/clk/SM x 152 SMs x max SM clock "
+                                 "(probe: 74.7 TFLOP/s); a latency-bound serial chain, each "
+                                 "algorithmic multiply-add costs ~15 float-float operations"})
     else:
         peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
         achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0

@@ -69,8 +69,9 @@ enum {
     FABM_RHS_DUFFING = 4,      /* forced oscillator with cubic capacitor, dim 2,
                                   p = (gamma, omega, F):
                                   f = (y, -gamma y - x - x^3 + F cos(omega t))       */
-    FABM_RHS_MANUFACTURED = 5, /* f = p0 t^p1 + t^2 - y, dim 1 (solution t^2 when
-                                  p0 = 2/Gamma(3-alpha), p1 = 2-alpha, y0 = 0)       */
+    FABM_RHS_MANUFACTURED = 5, /* f = p0 t^p1 + t^p2 - y, dim 1 (solution t^p2 when
+                                  p0 = Gamma(p2+1)/Gamma(p2+1-alpha), p1 = p2-alpha,
+                                  y(0) = 0 and, for alpha > 1, y'(0) = 0)           */
     FABM_RHS_LCR = 6           /* forced series LCR circuit, Sec. 5, Eq. sys.LRC,
                                   dim 2, p = (sigma, omega, a, b, f):
                                   f = (y - g(x), -sigma y - x + f sin(omega t)),
@@ -82,7 +83,10 @@ enum {
 
 /* Create a solver for D^alpha y = f(t, y) on t_n = n h, n = 0..N (Sec. 2).
  *   dim        number of components (must match rhs_id, 1..FABM_MAX_DIM)
- *   alpha      fractional order, 0 < alpha < 1
+ *   alpha      fractional order, 0 < alpha < 2.  The Taylor part of the initial
+ *              data (the sum over k < ceil(alpha) of t^k/k! y^(k)(0) in Sec. 2) is
+ *              y0 for alpha <= 1 and y0 + t y'(0) for 1 < alpha < 2, y'(0) given
+ *              to fabm_solve_batch_ic (zero otherwise)
  *   h          step size, h > 0 (T = N h)
  *   N          number of steps, 1 <= N <= 2^31
  *   rhs_id     one of FABM_RHS_*
@@ -108,6 +112,13 @@ fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out);
  * Synchronous.  B = 0 is allowed and does nothing. */
 fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
                              const int64_t *N_each, double *out, int out_on_device);
+
+/* As fabm_solve_batch, with the first derivatives y'(0) of the initial data:
+ *   y1           B x dim doubles (host), for 1 < alpha < 2; NULL means zero.
+ * FABM_EINVAL if y1 is given for alpha <= 1 or holds a non-finite value. */
+fabm_status fabm_solve_batch_ic(fabm_solver *s, int64_t B, const double *y0, const double *y1,
+                                const double *traj_params, const int64_t *N_each, double *out,
+                                int out_on_device);
 
 /* Release the solver and its device memory.  NULL is allowed. */
 fabm_status fabm_destroy(fabm_solver *s);

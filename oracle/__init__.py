@@ -31,7 +31,7 @@ RHS = {
     "linear": (2, None, 1, (1.0,)),
     "lorenz": (3, 3, 3, (10.0, 28.0, 8.0 / 3.0)),
     "duffing": (4, 2, 3, (0.1, 1.2, 1.0)),
-    "manufactured": (5, 1, 2, None),
+    "manufactured": (5, 1, 3, None),
     "lcr": (6, 2, 5, (1.015, 0.55, -1.02, -0.58, 0.0)),
 }
 
@@ -60,10 +60,10 @@ def _load():
         lib.fabm_oracle_weights.argtypes = [d, i64, P(d), P(d), P(d)]
         lib.fabm_oracle_constants.argtypes = [d, d, P(d), P(d)]
         lib.fabm_oracle_rhs.argtypes = [i, i, d, P(d), P(d), i, P(d)]
-        lib.fabm_oracle_solve.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), i]
+        lib.fabm_oracle_solve.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), P(d), i]
         lib.fabm_oracle_solve_w.argtypes = [i, d, i64, i, P(d), i, P(d), P(d), P(d), d, d,
-                                            P(d), P(d), i]
-        lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d),
+                                            P(d), P(d), P(d), i]
+        lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d), P(d),
                                                 P(ctypes.c_int64), P(d), i, i]
         for f in ("fabm_oracle_weights", "fabm_oracle_constants", "fabm_oracle_rhs",
                   "fabm_oracle_solve", "fabm_oracle_solve_w", "fabm_oracle_solve_batch"):
@@ -126,39 +126,48 @@ def rhs_eval(name: str, t: float, y, params=None):
     return out
 
 
+def _y1(y1, shape):
+    return None if y1 is None else _f64(y1).reshape(shape)
+
+
 def solve(name: str, alpha: float, h: float, N: int, y0, params=None,
-          compensated: bool = True):
-    """One trajectory: returns y_0..y_N as an (N+1, dim) array."""
+          compensated: bool = True, y1=None):
+    """One trajectory: returns y_0..y_N as an (N+1, dim) array.  y1 = y'(0)
+    (the second Taylor term, 1 < alpha < 2 only; None: zero)."""
     y0 = _f64(y0).reshape(-1)
     rid, p = _rhs(name, y0.size, params)
+    y1 = _y1(y1, y0.shape)
     out = np.empty((N + 1, y0.size))
     _check(_load().fabm_oracle_solve(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
-                                     _dp(out), int(compensated)), "solve")
+                                     _dp(y1), _dp(out), int(compensated)), "solve")
     return out
 
 
 def solve_with_weights(name: str, h: float, N: int, y0, b, a, c, h_alpha: float,
-                       inv_gamma2: float, params=None, compensated: bool = True):
+                       inv_gamma2: float, params=None, compensated: bool = True, y1=None):
     """One trajectory with caller-supplied weight vectors (length >= N)."""
     y0 = _f64(y0).reshape(-1)
     rid, p = _rhs(name, y0.size, params)
     b, a, c = _f64(b), _f64(a), _f64(c)
     if min(b.size, a.size, c.size) < N:
         raise ValueError("weight vectors shorter than N")
+    y1 = _y1(y1, y0.shape)
     out = np.empty((N + 1, y0.size))
     _check(_load().fabm_oracle_solve_w(y0.size, h, N, rid, _dp(p), p.size, _dp(b), _dp(a),
-                                       _dp(c), h_alpha, inv_gamma2, _dp(y0), _dp(out),
+                                       _dp(c), h_alpha, inv_gamma2, _dp(y0), _dp(y1), _dp(out),
                                        int(compensated)), "solve_w")
     return out
 
 
 def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
                 traj_params=None, N_each=None, threads: int | None = None,
-                compensated: bool = True, out=None):
-    """B trajectories: y0 is (B, dim); returns (B, N+1, dim).  Rows of trajectory t
-    past N_each[t] are left as they were in ``out`` (NaN when out is None)."""
+                compensated: bool = True, out=None, y1=None):
+    """B trajectories: y0 (and y1 = y'(0) for 1 < alpha < 2) are (B, dim);
+    returns (B, N+1, dim).  Rows of trajectory t past N_each[t] are left as
+    they were in ``out`` (NaN when out is None)."""
     y0 = _f64(y0)
     B, dim = y0.shape
+    y1 = _y1(y1, y0.shape)
     rid, p = _rhs(name, dim, params)
     tp = None
     if traj_params is not None:
@@ -172,7 +181,7 @@ def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
         out = np.full((B, N + 1, dim), np.nan)
     threads = threads or os.cpu_count() or 1
     _check(_load().fabm_oracle_solve_batch(
-        dim, alpha, h, N, rid, _dp(p), p.size, B, _dp(y0), _dp(tp),
+        dim, alpha, h, N, rid, _dp(p), p.size, B, _dp(y0), _dp(y1), _dp(tp),
         None if ne is None else ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         _dp(out), int(threads), int(compensated)), "solve_batch")
     return out

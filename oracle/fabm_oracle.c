@@ -7,8 +7,9 @@
  * algorithm for the simulation of fractional-order systems" (arXiv:1710.01133):
  *
  *   grid            t_n = n h, n = 0..N, f_n = f(t_n, y_n)            (Sec. 2)
- *   predictor       y^P_{n+1} = y_0 + h^a sum_{k=0}^{n} b_{n-k} f_k     (Eq. abm)
- *   corrector       y_{n+1}   = y_0 + h^a ( c_n f_0
+ *   Taylor part     T(t) = sum_{k < ceil(a)} t^k/k! y^(k)(0)  = y_0 (+ t y'_0 for 1 < a < 2)
+ *   predictor       y^P_{n+1} = T(t_{n+1}) + h^a sum_{k=0}^{n} b_{n-k} f_k   (Eq. abm)
+ *   corrector       y_{n+1}   = T(t_{n+1}) + h^a ( c_n f_0
  *                               + sum_{k=1}^{n} a_{n-k} f_k
  *                               + f(t_{n+1}, y^P_{n+1}) / Gamma(a+2) )  (Sec. 2)
  *   weights         b_n = ((n+1)^a - n^a) / Gamma(a+1)                  (Eq. abm)
@@ -25,7 +26,8 @@
  *   - 0^p = 0 for p > 0, so b_0 = 1/Gamma(a+1) and c_0 = a/Gamma(a+2).
  *   - one predictor and one corrector evaluation per step (PECE); f_{n+1} is
  *     evaluated at the corrected value, as the grid definition says.
- *   - 0 < a < 1 only, so the Taylor part of both formulas is y_0.
+ *   - 0 < a < 2: the Taylor part is y_0 for a <= 1 and y_0 + t y'_0 for
+ *     1 < a < 2 (the sum over k < ceil(a) of Sec. 2's formulas).
  *
  * Precision.  The weights are evaluated from the direct formulas above in
  * binary128 (_Float128) and rounded once to double: the second difference in
@@ -57,7 +59,7 @@ enum {
     ORC_LINEAR = 2,       /* f_i = -p0 * y_i                                */
     ORC_LORENZ = 3,       /* fractional Lorenz-type system, dim 3           */
     ORC_DUFFING = 4,      /* forced oscillator with cubic capacitor, dim 2  */
-    ORC_MANUFACTURED = 5, /* f = p0 t^p1 + t^2 - y (solution t^2), dim 1    */
+    ORC_MANUFACTURED = 5, /* f = p0 t^p1 + t^p2 - y (solution t^p2), dim 1  */
     ORC_LCR = 6           /* the paper's forced series LCR system (Sec. 5)  */
 };
 
@@ -95,8 +97,8 @@ static void orc_rhs(int rhs, int dim, double t, const double *y, const double *p
         out[0] = y[1];
         out[1] = -p[0] * y[1] - y[0] - y[0] * y[0] * y[0] + p[2] * cos(p[1] * t);
         break;
-    case ORC_MANUFACTURED: /* p = (kappa, q): f = kappa t^q + t^2 - y */
-        out[0] = p[0] * pow(t, p[1]) + t * t - y[0];
+    case ORC_MANUFACTURED: /* p = (kappa, q, r): f = kappa t^q + t^r - y */
+        out[0] = p[0] * pow(t, p[1]) + pow(t, p[2]) - y[0];
         break;
     case ORC_LCR: /* p = (sigma, omega, a, b, f), Eq. sys.LRC */
         out[0] = y[1] - orc_lcr_g(y[0], p[2], p[3]);
@@ -115,7 +117,7 @@ static int orc_rhs_dim_ok(int rhs, int dim, int np)
     case ORC_LINEAR: return dim >= 1 && np >= 1;
     case ORC_LORENZ: return dim == 3 && np >= 3;
     case ORC_DUFFING: return dim == 2 && np >= 3;
-    case ORC_MANUFACTURED: return dim == 1 && np >= 2;
+    case ORC_MANUFACTURED: return dim == 1 && np >= 3;
     case ORC_LCR: return dim == 2 && np >= 5;
     default: return 0;
     }
@@ -142,7 +144,7 @@ static q128 orc_powq(q128 x, q128 p)
  * Uses P[j] = j^alpha and j^{alpha+1} = j * P[j]. */
 int fabm_oracle_weights(double alpha, int64_t n, double *b, double *a, double *c)
 {
-    if (!(alpha > 0.0 && alpha < 1.0) || n < 1) return ORC_EINVAL;
+    if (!(alpha > 0.0 && alpha < 2.0) || n < 1) return ORC_EINVAL;
     q128 *P = (q128 *)malloc((size_t)(n + 2) * sizeof(q128));
     if (!P) return ORC_ENOMEM;
     const q128 al = (q128)alpha;
@@ -162,7 +164,7 @@ int fabm_oracle_weights(double alpha, int64_t n, double *b, double *a, double *c
 /* h^alpha, 1/Gamma(alpha+2) rounded once from binary128. */
 int fabm_oracle_constants(double alpha, double h, double *h_alpha, double *inv_gamma2)
 {
-    if (!(alpha > 0.0 && alpha < 1.0) || !(h > 0.0)) return ORC_EINVAL;
+    if (!(alpha > 0.0 && alpha < 2.0) || !(h > 0.0)) return ORC_EINVAL;
     if (h_alpha) *h_alpha = (double)powf128((q128)h, (q128)alpha);
     if (inv_gamma2) *inv_gamma2 = (double)(1 / tgammaf128((q128)alpha + 2));
     return ORC_OK;
@@ -207,21 +209,23 @@ static double orc_hist_dot(const double *w, int64_t n, const double *f, int64_t 
 
 /* One trajectory with caller-given weights (b, a, c of length >= N) and
  * constants; out holds (N+1) x dim values, row n = y_n. f_work holds
- * (N+1) x dim doubles of scratch. */
+ * (N+1) x dim doubles of scratch.  y1 = y'(0) (dim values) enters the Taylor
+ * part for 1 < a < 2; NULL means the Taylor part is y_0 alone. */
 static int orc_solve_one(int dim, double h, int64_t N, int rhs, const double *p,
                          const double *b, const double *a, const double *c, double h_alpha,
-                         double inv_gamma2, const double *y0, double *out, double *fw,
-                         int compensated)
+                         double inv_gamma2, const double *y0, const double *y1, double *out,
+                         double *fw, int compensated)
 {
-    double yp[8], fp[8], yc[8];
+    double yp[8], fp[8], yc[8], T[8];
     for (int i = 0; i < dim; ++i) out[i] = y0[i];
     orc_rhs(rhs, dim, 0.0, y0, p, fw);
     for (int64_t n = 0; n < N; ++n) {
         const double t1 = (double)(n + 1) * h;
+        for (int i = 0; i < dim; ++i) T[i] = y1 ? y0[i] + t1 * y1[i] : y0[i];
         /* predictor, Eq. abm */
         for (int i = 0; i < dim; ++i) {
             double sp = orc_hist_dot(b, n, fw + i, dim, 0, n, compensated);
-            yp[i] = y0[i] + h_alpha * sp;
+            yp[i] = T[i] + h_alpha * sp;
         }
         orc_rhs(rhs, dim, t1, yp, p, fp);
         /* corrector */
@@ -234,7 +238,7 @@ static int orc_solve_one(int dim, double h, int64_t N, int rhs, const double *p,
             } else {
                 sc = c[n] * fw[i] + sc;
             }
-            yc[i] = y0[i] + h_alpha * (sc + fp[i] * inv_gamma2);
+            yc[i] = T[i] + h_alpha * (sc + fp[i] * inv_gamma2);
         }
         for (int i = 0; i < dim; ++i) out[(n + 1) * dim + i] = yc[i];
         orc_rhs(rhs, dim, t1, yc, p, fw + (n + 1) * dim);
@@ -245,23 +249,26 @@ static int orc_solve_one(int dim, double h, int64_t N, int rhs, const double *p,
 /* Solve with explicit weight vectors (b, a, c each of length >= N). */
 int fabm_oracle_solve_w(int dim, double h, int64_t N, int rhs, const double *params, int n_params,
                         const double *b, const double *a, const double *c, double h_alpha,
-                        double inv_gamma2, const double *y0, double *out, int compensated)
+                        double inv_gamma2, const double *y0, const double *y1, double *out,
+                        int compensated)
 {
     if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !orc_rhs_dim_ok(rhs, dim, n_params))
         return ORC_EINVAL;
     double *fw = (double *)malloc((size_t)(N + 1) * dim * sizeof(double));
     if (!fw) return ORC_ENOMEM;
-    int st = orc_solve_one(dim, h, N, rhs, params, b, a, c, h_alpha, inv_gamma2, y0, out, fw,
+    int st = orc_solve_one(dim, h, N, rhs, params, b, a, c, h_alpha, inv_gamma2, y0, y1, out, fw,
                            compensated);
     free(fw);
     return st;
 }
 
+/* y1 = y'(0) for 1 < alpha < 2 (NULL: zero); must be NULL for alpha <= 1. */
 int fabm_oracle_solve(int dim, double alpha, double h, int64_t N, int rhs, const double *params,
-                      int n_params, const double *y0, double *out, int compensated)
+                      int n_params, const double *y0, const double *y1, double *out,
+                      int compensated)
 {
-    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !(alpha > 0.0 && alpha < 1.0) ||
-        !orc_rhs_dim_ok(rhs, dim, n_params))
+    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !(alpha > 0.0 && alpha < 2.0) ||
+        (y1 && alpha <= 1.0) || !orc_rhs_dim_ok(rhs, dim, n_params))
         return ORC_EINVAL;
     double *w = (double *)malloc((size_t)3 * N * sizeof(double));
     if (!w) return ORC_ENOMEM;
@@ -270,7 +277,7 @@ int fabm_oracle_solve(int dim, double alpha, double h, int64_t N, int rhs, const
     if (st == ORC_OK) st = fabm_oracle_constants(alpha, h, &ha, &ig2);
     if (st == ORC_OK)
         st = fabm_oracle_solve_w(dim, h, N, rhs, params, n_params, w, w + N, w + 2 * N, ha, ig2,
-                                 y0, out, compensated);
+                                 y0, y1, out, compensated);
     free(w);
     return st;
 }
@@ -281,7 +288,7 @@ typedef struct {
     int dim, rhs, n_params, compensated, tid, nthreads;
     double h, h_alpha, inv_gamma2;
     int64_t N, B;
-    const double *params, *traj_params, *y0, *w;
+    const double *params, *traj_params, *y0, *y1, *w;
     const int64_t *N_each;
     double *out;
     int status;
@@ -299,14 +306,16 @@ static void *orc_batch_worker(void *arg)
         const int64_t Nt = j->N_each ? j->N_each[t] : j->N;
         const double *p = j->traj_params ? j->traj_params + t * j->n_params : j->params;
         orc_solve_one(j->dim, j->h, Nt, j->rhs, p, j->w, j->w + j->N, j->w + 2 * j->N, j->h_alpha,
-                      j->inv_gamma2, j->y0 + t * j->dim, j->out + t * (j->N + 1) * j->dim, fw,
-                      j->compensated);
+                      j->inv_gamma2, j->y0 + t * j->dim, j->y1 ? j->y1 + t * j->dim : NULL,
+                      j->out + t * (j->N + 1) * j->dim, fw, j->compensated);
     }
     free(fw);
     return NULL;
 }
 
-/* B independent trajectories sharing (dim, alpha, h, rhs); trajectory t runs
+/* B independent trajectories sharing (dim, alpha, h, rhs) with initial values
+ * y0 and, for 1 < alpha < 2, first derivatives y1 (B x dim each; y1 NULL:
+ * zero); trajectory t runs
  * N_each[t] <= N steps (all N when N_each is NULL) with its own parameter row
  * traj_params[t*n_params ..] (params for all when NULL).  out is B x (N+1) x
  * dim; rows past N_each[t] are left untouched.  Trajectories are spread over
@@ -314,11 +323,11 @@ static void *orc_batch_worker(void *arg)
  * solve would compute it. */
 int fabm_oracle_solve_batch(int dim, double alpha, double h, int64_t N, int rhs,
                             const double *params, int n_params, int64_t B, const double *y0,
-                            const double *traj_params, const int64_t *N_each, double *out,
-                            int n_threads, int compensated)
+                            const double *y1, const double *traj_params, const int64_t *N_each,
+                            double *out, int n_threads, int compensated)
 {
-    if (dim < 1 || dim > 8 || N < 1 || B < 0 || !(h > 0.0) || !(alpha > 0.0 && alpha < 1.0) ||
-        !orc_rhs_dim_ok(rhs, dim, n_params))
+    if (dim < 1 || dim > 8 || N < 1 || B < 0 || !(h > 0.0) || !(alpha > 0.0 && alpha < 2.0) ||
+        (y1 && alpha <= 1.0) || !orc_rhs_dim_ok(rhs, dim, n_params))
         return ORC_EINVAL;
     if (N_each)
         for (int64_t t = 0; t < B; ++t)
@@ -348,6 +357,7 @@ int fabm_oracle_solve_batch(int dim, double alpha, double h, int64_t N, int rhs,
         j->dim = dim, j->rhs = rhs, j->n_params = n_params, j->compensated = compensated;
         j->tid = i, j->nthreads = n_threads, j->h = h, j->h_alpha = ha, j->inv_gamma2 = ig2;
         j->N = N, j->B = B, j->params = params, j->traj_params = traj_params, j->y0 = y0;
+        j->y1 = y1;
         j->w = w, j->N_each = N_each, j->out = out, j->status = ORC_OK;
     }
     for (int i = 1; i < n_threads; ++i)

@@ -28,7 +28,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
             "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
-            "fabm_server_cancel", "fabm_server_shape")
+            "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True):
     lib.fabm_create.argtypes = [i, d, d, i64, i, P(d), i, i, P(vp)]
     lib.fabm_solve.argtypes = [vp, P(d), P(d)]
     lib.fabm_solve_batch.argtypes = [vp, i64, P(d), P(d), P(i64), vp, i]
+    lib.fabm_solve_batch_ic.argtypes = [vp, i64, P(d), P(d), P(d), P(i64), vp, i]
     lib.fabm_destroy.argtypes = [vp]
     lib.fabm_last_error.argtypes = []
     lib.fabm_last_error.restype = ctypes.c_char_p
@@ -102,7 +103,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     lib.fabm_stroboscope.argtypes = [vp, i64, i64, i, vp, d, d, d, i64, i, vp]
     lib.fabm_stroboscope.restype = i
-    for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy", "fabm_set_block",
+    for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_solve_batch_ic",
+              "fabm_destroy", "fabm_set_block",
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
               "fabm_get_history_kernel"):
@@ -172,6 +174,14 @@ def fabm_solve_batch(handle, B, y0, traj_params, N_each, out_ptr, out_on_device)
         ne = N_each.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     _check(load().fabm_solve_batch(handle, int(B), _dp(y0), _dp(traj_params), ne,
                                    ctypes.c_void_p(out_ptr), int(out_on_device)))
+
+
+def fabm_solve_batch_ic(handle, B, y0, y1, traj_params, N_each, out_ptr, out_on_device):
+    ne = None
+    if N_each is not None:
+        ne = N_each.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(load().fabm_solve_batch_ic(handle, int(B), _dp(y0), _dp(y1), _dp(traj_params), ne,
+                                      ctypes.c_void_p(out_ptr), int(out_on_device)))
 
 
 def fabm_destroy(handle):
@@ -307,20 +317,24 @@ class Solver:
         return {k: dict(zip(("launches", "ms", "flops"), fabm_kernel_stats(self.handle, k)))
                 for k in KERNEL_KINDS}
 
-    def solve(self, y0) -> np.ndarray:
+    def solve(self, y0, y1=None) -> np.ndarray:
+        """One trajectory; y1 = y'(0) for 1 < alpha < 2."""
         y0 = _f64(y0).reshape(-1)
         if y0.size != self.dim:
             raise ValueError("y0 must have dim entries")
+        if y1 is not None:
+            return self.solve_batch(y0.reshape(1, -1), y1=_f64(y1).reshape(1, -1))[0]
         out = np.empty((self.N + 1, self.dim))
         fabm_solve(self.handle, y0, out)
         return out
 
-    def solve_batch(self, y0, traj_params=None, N_each=None, out=None):
-        """y0: (B, dim).  out: None (a new host array), a host float64 array of
-        shape (B, N+1, dim), or a CUDA tensor of that shape (written in place on
-        the device).  Returns out."""
+    def solve_batch(self, y0, traj_params=None, N_each=None, out=None, y1=None):
+        """y0 (and y1 = y'(0), for 1 < alpha < 2): (B, dim).  out: None (a new
+        host array), a host float64 array of shape (B, N+1, dim), or a CUDA
+        tensor of that shape (written in place on the device).  Returns out."""
         y0 = _f64(y0).reshape(-1, self.dim)
         B = y0.shape[0]
+        y1 = None if y1 is None else _f64(y1).reshape(B, self.dim)
         tp = None if traj_params is None else _f64(traj_params).reshape(B, -1)
         ne = None if N_each is None else np.ascontiguousarray(np.asarray(N_each, np.int64))
         if out is None:
@@ -337,7 +351,10 @@ class Solver:
                 raise ValueError("out must be float64")
             ptr = out.data_ptr()
             on_dev = 1 if out.is_cuda else 0
-        fabm_solve_batch(self.handle, B, y0, tp, ne, ptr, on_dev)
+        if y1 is None:
+            fabm_solve_batch(self.handle, B, y0, tp, ne, ptr, on_dev)
+        else:
+            fabm_solve_batch_ic(self.handle, B, y0, y1, tp, ne, ptr, on_dev)
         return out
 
 

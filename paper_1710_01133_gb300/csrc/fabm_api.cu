@@ -321,8 +321,9 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
     return FABM_OK;
 }
 
-fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
-                      const int64_t *N_each, double *out, int out_on_device)
+fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double *y1,
+                      const double *traj_params, const int64_t *N_each, double *out,
+                      int out_on_device)
 {
     const int dim = s->dim;
     const int64_t cols = B * dim;
@@ -349,7 +350,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         for (int i = 0; i < s->n_params; ++i)
             par[b * kMaxParams + i] = traj_params ? traj_params[b * s->n_params + i] : s->params[i];
     for (int64_t i = 0; i < B * dim; ++i)
-        if (!std::isfinite(y0[i])) return fail(FABM_EINVAL, "y0[%lld] is not finite", (long long)i);
+        if (!std::isfinite(y0[i]) || (y1 && !std::isfinite(y1[i])))
+            return fail(FABM_EINVAL, "y0[%lld] or y1[%lld] is not finite", (long long)i, (long long)i);
 
     const bool split = hk == FABM_HIST_TENSOR;
     // workspace
@@ -362,7 +364,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     FABM_CUDA_TRY(s->G.ensure((size_t)2 * 2 * L * cols));
     if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)max_chunks * part_per_chunk));
     if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)max_chunks * part_per_chunk));
-    FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim));
+    FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim * 2));  // y0, then y1
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
     FABM_CUDA_TRY(s->status.ensure(1));
@@ -387,6 +389,13 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         Y = s->Ystage.p;
     }
     FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p, y0, sizeof(double) * B * dim, cudaMemcpyHostToDevice, s->sR));
+    // y'(0) (1 < alpha < 2): zeros when not given, so that one cached graph
+    // serves solves with and without it
+    if (y1)
+        FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p + B * dim, y1, sizeof(double) * B * dim,
+                                      cudaMemcpyHostToDevice, s->sR));
+    else
+        FABM_CUDA_TRY(cudaMemsetAsync(s->y0.p + B * dim, 0, sizeof(double) * B * dim, s->sR));
     FABM_CUDA_TRY(cudaMemcpyAsync(s->par.p, par.data(), sizeof(double) * par.size(),
                                   cudaMemcpyHostToDevice, s->sR));
     FABM_CUDA_TRY(cudaMemcpyAsync(s->nEach.p, ne.data(), sizeof(int64_t) * B,
@@ -400,6 +409,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     bt.N = N;
     bt.N_each = s->nEach.p;
     bt.y0 = s->y0.p;
+    bt.y1 = s->alpha > 1.0 ? s->y0.p + B * dim : nullptr;
     bt.params = s->par.p;
     bt.F = s->F.p;
     bt.ldF = cols;
@@ -515,7 +525,7 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     if (!out) return fail(FABM_EINVAL, "out is NULL");
     *out = nullptr;
     if (dim < 1 || dim > FABM_MAX_DIM) return fail(FABM_EINVAL, "dim %d outside 1..%d", dim, FABM_MAX_DIM);
-    if (!(alpha > 0.0 && alpha < 1.0)) return fail(FABM_EINVAL, "alpha %g outside (0, 1)", alpha);
+    if (!(alpha > 0.0 && alpha < 2.0)) return fail(FABM_EINVAL, "alpha %g outside (0, 2)", alpha);
     if (!(h > 0.0) || !std::isfinite(h)) return fail(FABM_EINVAL, "h %g must be positive", h);
     if (N < 1 || N > (1LL << 31)) return fail(FABM_EINVAL, "N %lld outside 1..2^31", (long long)N);
     if (precision != FABM_FP64 && precision != FABM_SPLIT)
@@ -598,8 +608,17 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
 fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
                              const int64_t *N_each, double *out, int out_on_device)
 {
+    return fabm_solve_batch_ic(s, B, y0, nullptr, traj_params, N_each, out, out_on_device);
+}
+
+fabm_status fabm_solve_batch_ic(fabm_solver *s, int64_t B, const double *y0, const double *y1,
+                                const double *traj_params, const int64_t *N_each, double *out,
+                                int out_on_device)
+{
     g_last_error.clear();
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (y1 && s->alpha <= 1.0)
+        return fail(FABM_EINVAL, "y1 given for alpha %g <= 1 (its Taylor part is y0 alone)", s->alpha);
     if (B < 0 || B > (1LL << 24)) return fail(FABM_EINVAL, "B %lld outside 0..2^24", (long long)B);
     if (B == 0) return FABM_OK;
     if (!y0 || !out) return fail(FABM_EINVAL, "y0 and out must not be NULL");
@@ -610,7 +629,7 @@ fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const 
             if (!std::isfinite(traj_params[i]))
                 return fail(FABM_EINVAL, "traj_params[%lld] is not finite", (long long)i);
     DeviceGuard g(s->device);
-    return run_batch(s, B, y0, traj_params, N_each, out, out_on_device);
+    return run_batch(s, B, y0, y1, traj_params, N_each, out, out_on_device);
 }
 
 fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out)
@@ -735,7 +754,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         double ms = 1e300;
         for (int rep = 0; rep < 2 && st == FABM_OK; ++rep) {  // first run records the graph
             const auto t0 = std::chrono::steady_clock::now();
-            st = run_batch(s, B, y0, traj_params, ne.data(), dout, 1);
+            st = run_batch(s, B, y0, nullptr, traj_params, ne.data(), dout, 1);
             const auto t1 = std::chrono::steady_clock::now();
             ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         }

@@ -46,6 +46,7 @@ struct DevBatch {
     int64_t N;             // steps of the longest trajectory
     const int64_t *N_each; // per-trajectory steps (device)
     const double *y0;      // B x dim
+    const double *y1;      // B x dim, y'(0) for 1 < alpha < 2, or NULL (Taylor part y0)
     const double *params;  // B x kMaxParams
     double *F;             // history f_k, (N+1) x ldF, row k = time k
     int64_t ldF;           // row stride of F (>= cols)

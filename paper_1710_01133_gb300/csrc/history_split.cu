@@ -9,8 +9,8 @@
 // |f|), then x = s0 + s1 + s2 with s0 an integer, s1 a multiple of 2^-8 and s2
 // of 2^-16, each with at most 8 significant bits, i.e. each an exact bf16.
 // The weight rows of a segment get the same treatment with one exponent per
-// weight kind (the weights decrease with the distance, so the first one is
-// the largest).  Dropping the products of order >= 3 and the rounding of the
+// weight kind (the weights are monotone in the distance, so the largest is at
+// one end of the tile).  Dropping the products of order >= 3 and the rounding of the
 // last slice leave a representation error of at most 2^-25 of the segment's
 // largest |f| (and weight).
 //
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(256) slice_f_kernel(const double *__restrict__
 
 // ------------------------------------------------- Hankel weight tiles ---
 
-// For every lag g in [2, g_max]: D0 = 64 g - 62, exponent E_w = ilogb(W(D0)) + 1
-// per kind, and the Hankel core matrices of the three slices of W(D0 + t),
+// For every lag g in [2, g_max]: D0 = 64 g - 62, exponent E_w = ilogb of the
+// tile's largest weight + 1 per kind, and the Hankel core matrices of the three slices of W(D0 + t),
 // t = 8h + r0 + c0.  WH[g][kind][slice][h][r0][c0]; Ew[g][kind].
 // One thread per (g, kind, h, r0) row.
 __global__ void hankel_weights_kernel(const double *__restrict__ WB, const double *__restrict__ WA,
@@ -150,7 +150,10 @@ __global__ void hankel_weights_kernel(const double *__restrict__ WB, const doubl
         if (g < 2) continue;
         const double *W = kind ? WA : WB;
         const int64_t D0 = 64 * g - 62;
-        const int E = ilogb(W[D0]) + 1;
+        // the tile spans the distances D0 .. D0+126; the weights are monotone in
+        // the distance (decreasing for alpha < 1, increasing for alpha > 1), so
+        // the largest sits at one end
+        const int E = ilogb(fmax(W[D0], W[D0 + 126])) + 1;
         if (h == 0 && r0 == 0) Ew[g * 2 + kind] = E;
         const double sc = ldexp(1.0, 8 - E);
         uint32_t w[3][4];

@@ -109,15 +109,18 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
 
     double accP[TPL], accC[TPL], aux[TPL];
     const double f0 = bt.F[col];
+    const double y1 = bt.y1 ? bt.y1[col] : 0.0;
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
         const int a = lane + kWarp * t;
         const int64_t m = m0 + 1 + a;
         aux[t] = Rhs::aux((double)m * kc.h, p);
+        // Taylor part of the initial data at t_m: y0, or y0 + t_m y'(0) for 1 < alpha < 2
+        const double Tm = bt.y1 ? fma((double)m * kc.h, y1, y0) : y0;
         const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
         const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
-        accP[t] = fma(ha, gP, y0);
-        accC[t] = fma(ha, gC, y0);
+        accP[t] = fma(ha, gP, Tm);
+        accC[t] = fma(ha, gC, Tm);
     }
     if (c >= 1) {  // lag-1 block: k = m0-L+j, d = m-k = L+1+a-j in [2, 2L]
         for (int j = 0; j < L; ++j) {
@@ -250,15 +253,17 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
 
     double baseC[TPL];
     FF bP[TPL], bC[TPL], aux[TPL], nP[TPL], nC[TPL], inc[TPL], fo[TPL];
+    const double y1 = bt.y1 ? bt.y1[col] : 0.0;
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
         const int a = lane + kWarp * t;
         const int64_t m = m0 + 1 + a;
         aux[t] = ff_from_double(Rhs::aux((double)m * kc.h, p));
+        const double Tm = bt.y1 ? fma((double)m * kc.h, y1, y0) : y0;  // Taylor part at t_m
         const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
         const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
-        baseC[t] = fma(ha, gC, y0);
-        bP[t] = ff_from_double(fma(ha, gP, y0));
+        baseC[t] = fma(ha, gC, Tm);
+        bP[t] = ff_from_double(fma(ha, gP, Tm));
         bC[t] = ff_from_double(baseC[t]);
         nP[t] = nC[t] = inc[t] = fo[t] = FF(0);
     }

@@ -61,8 +61,8 @@ struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 +
     }
 };
 
-struct RhsManufactured {  // f = p0 t^p1 + t^2 - y
-    __device__ static double aux(double t, const double *p) { return p[0] * pow(t, p[1]) + t * t; }
+struct RhsManufactured {  // f = p0 t^p1 + t^p2 - y
+    __device__ static double aux(double t, const double *p) { return p[0] * pow(t, p[1]) + pow(t, p[2]); }
     template <int D, class T>
     __device__ static T one(int, const T *y, const T *, T aux)
     {
@@ -154,7 +154,7 @@ inline int rhs_n_params(int rhs)
     case FABM_RHS_LINEAR: return 1;
     case FABM_RHS_LORENZ: return 3;
     case FABM_RHS_DUFFING: return 3;
-    case FABM_RHS_MANUFACTURED: return 2;
+    case FABM_RHS_MANUFACTURED: return 3;
     case FABM_RHS_LCR: return 5;
     default: return -1;
     }

@@ -38,7 +38,7 @@ def test_library_links_cuda_runtime_dynamically():
 
 
 @pytest.mark.parametrize("kw,msg", [
-    (dict(alpha=1.2), "alpha"),
+    (dict(alpha=2.0), "alpha"),
     (dict(alpha=0.0), "alpha"),
     (dict(h=-1.0), "h"),
     (dict(N=0), "N"),

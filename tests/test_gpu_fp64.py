@@ -135,9 +135,9 @@ def test_manufactured_solution(gpu_lib, parity):
     alpha = 0.8
     kappa = 2.0 / math.gamma(3.0 - alpha)
     N = 640
-    with gpu_lib.Solver("manufactured", 1, alpha, 1.0 / N, N, [kappa, 2.0 - alpha]) as s:
+    with gpu_lib.Solver("manufactured", 1, alpha, 1.0 / N, N, [kappa, 2.0 - alpha, 2.0]) as s:
         got = s.solve([0.0])
-    ref = oracle.solve("manufactured", alpha, 1.0 / N, N, [0.0], params=[kappa, 2.0 - alpha])
+    ref = oracle.solve("manufactured", alpha, 1.0 / N, N, [0.0], params=[kappa, 2.0 - alpha, 2.0])
     parity(rel_err(got, ref), TOL_FP64, "")
     t = np.arange(N + 1) / N
     assert np.max(np.abs(got[:, 0] - t * t)) < 1e-4

@@ -24,7 +24,7 @@ def _grid(h, N):
 
 # ------------------------------------------------------------- weights ---
 
-@pytest.mark.parametrize("alpha", [0.3, 0.7, 0.95, 0.99])
+@pytest.mark.parametrize("alpha", [0.3, 0.7, 0.95, 0.99, 1.3, 1.7])
 def test_weight_telescoping_identities(alpha):
     """sum_{j<=n} b_j = (n+1)^a/G(a+1) and c_n + sum_{j<n} a_j + 1/G(a+2) =
     (n+1)^a/G(a+1): the product-rectangle and product-trapezoid rules integrate
@@ -148,7 +148,7 @@ def test_convergence_order_manufactured(alpha):
     solution the fractional Adams method converges with order 1 + a (Diethelm,
     Ford, Freed, Numer. Algorithms 36 (2004)); the paper's scheme must show it."""
     kappa = 2.0 / math.gamma(3.0 - alpha)
-    params = [kappa, 2.0 - alpha]
+    params = [kappa, 2.0 - alpha, 2.0]
     errs = []
     Ns = [40, 80, 160, 320, 640, 1280]
     for N in Ns:
@@ -217,12 +217,14 @@ def test_batch_equals_singles_and_prefixes():
         assert np.all(np.isnan(out[t, ne[t] + 1:]))
 
 
-def test_tiny_N_against_50_digit_evaluation():
+@pytest.mark.parametrize("alpha,y1", [(0.63, None), (1.45, (0.5, -1.0, 2.0))])
+def test_tiny_N_against_50_digit_evaluation(alpha, y1):
     """Brute force at N <= 8: the scheme evaluated step by step in 50-digit
-    arithmetic; the FP64 oracle must agree to ~1e-15."""
+    arithmetic; the FP64 oracle must agree to ~1e-15.  For 1 < a < 2 the
+    Taylor part is y0 + t y'(0)."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 50
-    alpha, h, N = 0.63, 0.002, 8
+    h, N = 0.002, 8
     A, H = mp.mpf(alpha), mp.mpf(h)
     p = [mp.mpf(v) for v in (10.0, 28.0, 8.0 / 3.0)]
 
@@ -237,20 +239,100 @@ def test_tiny_N_against_50_digit_evaluation():
     aw = lambda j: (pw(j + 2, A + 1) - 2 * pw(j + 1, A + 1) + pw(j, A + 1)) / g2
     cw = lambda j: (pw(j, A + 1) - (j - A) * pw(j + 1, A)) / g2
     y0 = [mp.mpf(v) for v in (0.1, -0.2, 0.3)]
+    d1 = [mp.mpf(v) for v in (y1 or (0, 0, 0))]
     ys, fs = [y0], [f(0, y0)]
     for n in range(N):
-        t1 = (n + 1) * H
-        yp = [y0[i] + H ** A * sum(bw(n - k) * fs[k][i] for k in range(n + 1)) for i in range(3)]
+        t1 = (n + 1) * mp.mpf(h)
+        T = [y0[i] + t1 * d1[i] for i in range(3)]
+        yp = [T[i] + H ** A * sum(bw(n - k) * fs[k][i] for k in range(n + 1)) for i in range(3)]
         fp = f(t1, yp)
-        yc = [y0[i] + H ** A * (cw(n) * fs[0][i] + sum(aw(n - k) * fs[k][i]
-                                                        for k in range(1, n + 1))
-                                + fp[i] / g2) for i in range(3)]
+        yc = [T[i] + H ** A * (cw(n) * fs[0][i] + sum(aw(n - k) * fs[k][i]
+                                                       for k in range(1, n + 1))
+                               + fp[i] / g2) for i in range(3)]
         ys.append(yc)
         fs.append(f(t1, yc))
     ref = np.array([[float(v) for v in row] for row in ys])
-    got = oracle.solve("lorenz", alpha, h, N, [0.1, -0.2, 0.3])
+    got = oracle.solve("lorenz", alpha, h, N, [0.1, -0.2, 0.3], y1=y1)
     scale = np.max(np.abs(ref), axis=0)
     assert np.max(np.abs(got - ref) / scale) < 2e-15
+
+
+# ------------------------------------------------- orders 1 < a < 2 -------
+# Sec. 2 writes the Taylor part as sum_{k < ceil(a)} t^k/k! y^(k)(0); for
+# 1 < a < 2 that is y0 + t y'(0), and the weights are the same formulas.
+
+def test_weight_special_values_above_one():
+    """b_0, c_0, a_0 as for a < 1; the weights now grow with j (like j^{a-1})."""
+    for alpha in (1.2, 1.5, 1.9):
+        b, a, c = oracle.weights(alpha, 3000)
+        g1, g2 = math.gamma(alpha + 1), math.gamma(alpha + 2)
+        assert b[0] == pytest.approx(1 / g1, rel=2e-16)
+        assert c[0] == pytest.approx(alpha / g2, rel=2e-16)
+        assert a[0] == pytest.approx((2 ** (alpha + 1) - 2) / g2, rel=1e-15)
+        assert np.all(np.diff(b) > 0) and np.all(np.diff(a[1:]) > 0)
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.9])
+def test_constant_rhs_is_exact_above_one(alpha):
+    """f = c: y = y0 + y'(0) t + c t^a/G(a+1) at every grid point; without the
+    y'(0) t term the pin fails."""
+    h, N = 0.011, 600
+    t = _grid(h, N)
+    y = oracle.solve("const", alpha, h, N, [0.25, -1.0], params=[1.5], y1=[-0.7, 2.0])
+    ex = 1.5 * t ** alpha / math.gamma(alpha + 1)
+    np.testing.assert_allclose(y[:, 0], 0.25 - 0.7 * t + ex, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(y[:, 1], -1.0 + 2.0 * t + ex, rtol=1e-14, atol=1e-14)
+    y_no = oracle.solve("const", alpha, h, N, [0.25, -1.0], params=[1.5])
+    assert np.max(np.abs(y_no[:, 0] - (0.25 - 0.7 * t + ex))) > 1.0
+
+
+def test_linear_in_time_rhs_is_exact_above_one():
+    alpha, h, N = 1.5, 0.02, 400
+    t = _grid(h, N)
+    y = oracle.solve("time", alpha, h, N, [0.3], y1=[0.9])
+    ex = 0.3 + 0.9 * t + t ** (alpha + 1) / math.gamma(alpha + 2)
+    np.testing.assert_allclose(y[:, 0], ex, rtol=1e-14, atol=1e-14)
+
+
+def _mittag_leffler2(mp, alpha, beta, z):
+    s, k = mp.mpf(0), 0
+    while True:
+        term = z ** k / mp.gamma(alpha * k + beta)
+        s += term
+        k += 1
+        if k > 10 and abs(term) < mp.mpf(10) ** -40:
+            return s
+
+
+def test_mittag_leffler_above_one():
+    """D^a y = -y for a = 1.5: y(0) = 1, y'(0) = 0 gives E_a(-t^a); y(0) = 0,
+    y'(0) = 1 gives t E_{a,2}(-t^a) (damped oscillations).  h = 1e-3, T = 5:
+    both within 1e-5."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    alpha, h, N = 1.5, 1e-3, 5000
+    y = oracle.solve("linear", alpha, h, N, [1.0, 0.0], params=[1.0], y1=[0.0, 1.0])
+    A = mp.mpf(alpha)
+    for T in (0.5, 1, 2, 3.5, 5):
+        n = int(round(T / h))
+        z = -mp.mpf(n * h) ** A
+        assert abs(y[n, 0] - float(_mittag_leffler2(mp, A, 1, z))) < 1e-5
+        assert abs(y[n, 1] - float(mp.mpf(n * h) * _mittag_leffler2(mp, A, 2, z))) < 1e-5
+
+
+@pytest.mark.parametrize("alpha", [1.25, 1.5, 1.8])
+def test_convergence_order_above_one(alpha):
+    """y = t^3 solves D^a y = 6 t^{3-a}/G(4-a) + t^3 - y, y(0) = y'(0) = 0; its
+    D^a y is C^1 for a < 2, and for a >= 1 the method then converges with order
+    2 (Diethelm, Ford, Freed, Numer. Algorithms 36 (2004))."""
+    kappa = 6.0 / math.gamma(4.0 - alpha)
+    errs = []
+    for N in (40, 80, 160, 320, 640):
+        h = 1.0 / N
+        y = oracle.solve("manufactured", alpha, h, N, [0.0], params=[kappa, 3.0 - alpha, 3.0])
+        errs.append(np.max(np.abs(y[:, 0] - _grid(h, N) ** 3)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(orders[-1] - 2.0) < 0.15, orders
 
 
 # ----------------------------------------- planted mistakes must be caught --
@@ -273,7 +355,7 @@ def _pins_hold(wfun, ha_fun, ig, alpha):
         h = 1.0 / N
         b, a, c = wfun(N + 1)
         y = oracle.solve_with_weights("manufactured", h, N, [0.0], b, a, c, ha_fun(h), ig,
-                                      params=[kappa, 2.0 - alpha])
+                                      params=[kappa, 2.0 - alpha, 2.0])
         errs.append(np.max(np.abs(y[:, 0] - _grid(h, N) ** 2)))
     if not np.all(np.isfinite(errs)) or errs[1] == 0:
         return False
