@@ -98,6 +98,18 @@ enum {
 fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
                         const double *params, int n_params, int precision, fabm_solver **out);
 
+/* As fabm_create with one fractional order per component, D^alpha_i y_i =
+ * f_i(t, y) (the systems of Sec. 5 carry an order per equation, alpha1 and
+ * alpha2 for the LCR circuit).  alpha: dim orders, each 0 < alpha_i < 2; each
+ * component uses its own weights, h^alpha_i and Gamma(alpha_i+2), and y'(0)
+ * (fabm_solve_batch_ic) only where alpha_i > 1.  With orders that differ,
+ * split precision sums the history with the compensated-fp32 kernel (a tensor
+ * tile shares one weight operand across its columns); fabm_copy_weights
+ * returns component 0's weights.  Errors as fabm_create. */
+fabm_status fabm_create_multi(int dim, const double *alpha, double h, int64_t N, int rhs_id,
+                              const double *params, int n_params, int precision,
+                              fabm_solver **out);
+
 /* Solve one trajectory.  y0: dim doubles.  out: (N+1) x dim doubles, row n = y_n,
  * row 0 = y0, caller-allocated host memory.  Synchronous. */
 fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out);

@@ -65,8 +65,11 @@ def _load():
                                             P(d), P(d), P(d), i]
         lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d), P(d),
                                                 P(ctypes.c_int64), P(d), i, i]
+        lib.fabm_oracle_solve_batch_multi.argtypes = [i, P(d), d, i64, i, P(d), i, i64, P(d),
+                                                      P(d), P(d), P(ctypes.c_int64), P(d), i]
         for f in ("fabm_oracle_weights", "fabm_oracle_constants", "fabm_oracle_rhs",
-                  "fabm_oracle_solve", "fabm_oracle_solve_w", "fabm_oracle_solve_batch"):
+                  "fabm_oracle_solve", "fabm_oracle_solve_w", "fabm_oracle_solve_batch",
+                  "fabm_oracle_solve_batch_multi"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -130,10 +133,15 @@ def _y1(y1, shape):
     return None if y1 is None else _f64(y1).reshape(shape)
 
 
-def solve(name: str, alpha: float, h: float, N: int, y0, params=None,
+def solve(name: str, alpha, h: float, N: int, y0, params=None,
           compensated: bool = True, y1=None):
     """One trajectory: returns y_0..y_N as an (N+1, dim) array.  y1 = y'(0)
-    (the second Taylor term, 1 < alpha < 2 only; None: zero)."""
+    (the second Taylor term, 1 < alpha < 2 only; None: zero).  alpha may be a
+    sequence of one order per component."""
+    if np.ndim(alpha) > 0:
+        return solve_batch(name, alpha, h, N, _f64(y0).reshape(1, -1), params=params,
+                           compensated=compensated,
+                           y1=None if y1 is None else _f64(y1).reshape(1, -1))[0]
     y0 = _f64(y0).reshape(-1)
     rid, p = _rhs(name, y0.size, params)
     y1 = _y1(y1, y0.shape)
@@ -164,7 +172,8 @@ def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
                 compensated: bool = True, out=None, y1=None):
     """B trajectories: y0 (and y1 = y'(0) for 1 < alpha < 2) are (B, dim);
     returns (B, N+1, dim).  Rows of trajectory t past N_each[t] are left as
-    they were in ``out`` (NaN when out is None)."""
+    they were in ``out`` (NaN when out is None).  alpha may be a sequence of
+    dim orders, one per component (y1 then serves the components above 1)."""
     y0 = _f64(y0)
     B, dim = y0.shape
     y1 = _y1(y1, y0.shape)
@@ -179,6 +188,15 @@ def solve_batch(name: str, alpha: float, h: float, N: int, y0, params=None,
         ne = np.ascontiguousarray(np.asarray(N_each, dtype=np.int64))
     if out is None:
         out = np.full((B, N + 1, dim), np.nan)
+    if np.ndim(alpha) > 0:  # one order per component
+        al = _f64(alpha).reshape(-1)
+        if al.size != dim:
+            raise ValueError("alpha must have dim entries")
+        _check(_load().fabm_oracle_solve_batch_multi(
+            dim, _dp(al), h, N, rid, _dp(p), p.size, B, _dp(y0), _dp(y1), _dp(tp),
+            None if ne is None else ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            _dp(out), int(compensated)), "solve_batch_multi")
+        return out
     threads = threads or os.cpu_count() or 1
     _check(_load().fabm_oracle_solve_batch(
         dim, alpha, h, N, rid, _dp(p), p.size, B, _dp(y0), _dp(y1), _dp(tp),

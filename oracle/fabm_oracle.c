@@ -211,34 +211,58 @@ static double orc_hist_dot(const double *w, int64_t n, const double *f, int64_t 
  * constants; out holds (N+1) x dim values, row n = y_n. f_work holds
  * (N+1) x dim doubles of scratch.  y1 = y'(0) (dim values) enters the Taylor
  * part for 1 < a < 2; NULL means the Taylor part is y_0 alone. */
+static int orc_solve_one_multi(int dim, double h, int64_t N, int rhs, const double *p,
+                               const double *b, const double *a, const double *c,
+                               int64_t wstride, const double *h_alpha, const double *inv_gamma2,
+                               const int *taylor2, const double *y0, const double *y1,
+                               double *out, double *fw, int compensated);
+
 static int orc_solve_one(int dim, double h, int64_t N, int rhs, const double *p,
                          const double *b, const double *a, const double *c, double h_alpha,
                          double inv_gamma2, const double *y0, const double *y1, double *out,
                          double *fw, int compensated)
+{
+    double ha[8], ig[8];
+    int t2[8];
+    for (int i = 0; i < dim; ++i) ha[i] = h_alpha, ig[i] = inv_gamma2, t2[i] = y1 != NULL;
+    return orc_solve_one_multi(dim, h, N, rhs, p, b, a, c, 0, ha, ig, t2, y0, y1, out, fw,
+                               compensated);
+}
+
+/* The same with an order alpha_i per component (Sec. 5's systems carry one
+ * order per equation): component i uses the weights b + i*wstride (a, c
+ * likewise), h^alpha_i and 1/Gamma(alpha_i+2), and its Taylor part
+ * y0_i + t y1_i when taylor2[i] (1 < alpha_i < 2), else y0_i. */
+static int orc_solve_one_multi(int dim, double h, int64_t N, int rhs, const double *p,
+                               const double *b, const double *a, const double *c,
+                               int64_t wstride, const double *h_alpha, const double *inv_gamma2,
+                               const int *taylor2, const double *y0, const double *y1,
+                               double *out, double *fw, int compensated)
 {
     double yp[8], fp[8], yc[8], T[8];
     for (int i = 0; i < dim; ++i) out[i] = y0[i];
     orc_rhs(rhs, dim, 0.0, y0, p, fw);
     for (int64_t n = 0; n < N; ++n) {
         const double t1 = (double)(n + 1) * h;
-        for (int i = 0; i < dim; ++i) T[i] = y1 ? y0[i] + t1 * y1[i] : y0[i];
+        for (int i = 0; i < dim; ++i) T[i] = (y1 && taylor2[i]) ? y0[i] + t1 * y1[i] : y0[i];
         /* predictor, Eq. abm */
         for (int i = 0; i < dim; ++i) {
-            double sp = orc_hist_dot(b, n, fw + i, dim, 0, n, compensated);
-            yp[i] = T[i] + h_alpha * sp;
+            double sp = orc_hist_dot(b + i * wstride, n, fw + i, dim, 0, n, compensated);
+            yp[i] = T[i] + h_alpha[i] * sp;
         }
         orc_rhs(rhs, dim, t1, yp, p, fp);
         /* corrector */
         for (int i = 0; i < dim; ++i) {
-            double sc = orc_hist_dot(a, n, fw + i, dim, 1, n, compensated);
+            const double *ai = a + i * wstride, *ci = c + i * wstride;
+            double sc = orc_hist_dot(ai, n, fw + i, dim, 1, n, compensated);
             if (compensated) {
-                double s, e, pr = c[n] * fw[i], pe = fma(c[n], fw[i], -pr);
+                double s, e, pr = ci[n] * fw[i], pe = fma(ci[n], fw[i], -pr);
                 two_sum(pr, sc, &s, &e);
                 sc = s + (e + pe);
             } else {
-                sc = c[n] * fw[i] + sc;
+                sc = ci[n] * fw[i] + sc;
             }
-            yc[i] = T[i] + h_alpha * (sc + fp[i] * inv_gamma2);
+            yc[i] = T[i] + h_alpha[i] * (sc + fp[i] * inv_gamma2[i]);
         }
         for (int i = 0; i < dim; ++i) out[(n + 1) * dim + i] = yc[i];
         orc_rhs(rhs, dim, t1, yc, p, fw + (n + 1) * dim);
@@ -376,5 +400,54 @@ int fabm_oracle_solve_batch(int dim, double alpha, double h, int64_t N, int rhs,
     free(w);
     free(jobs);
     free(th);
+    return st;
+}
+
+/* --------------------------------------------------- per-component orders --- */
+
+/* B trajectories of a system with one order alpha[i] per component, 0 < alpha[i]
+ * < 2; y1 (B x dim or NULL) is used by the components with alpha[i] > 1.
+ * Otherwise as fabm_oracle_solve_batch (single-threaded). */
+int fabm_oracle_solve_batch_multi(int dim, const double *alpha, double h, int64_t N, int rhs,
+                                  const double *params, int n_params, int64_t B,
+                                  const double *y0, const double *y1,
+                                  const double *traj_params, const int64_t *N_each, double *out,
+                                  int compensated)
+{
+    if (dim < 1 || dim > 8 || N < 1 || B < 0 || !(h > 0.0) || !orc_rhs_dim_ok(rhs, dim, n_params))
+        return ORC_EINVAL;
+    double ha[8], ig[8];
+    int t2[8];
+    for (int i = 0; i < dim; ++i) {
+        if (!(alpha[i] > 0.0 && alpha[i] < 2.0)) return ORC_EINVAL;
+        t2[i] = alpha[i] > 1.0;
+    }
+    if (N_each)
+        for (int64_t t = 0; t < B; ++t)
+            if (N_each[t] < 1 || N_each[t] > N) return ORC_EINVAL;
+    double *w = (double *)malloc((size_t)3 * N * dim * sizeof(double));
+    double *fw = (double *)malloc((size_t)(N + 1) * dim * sizeof(double));
+    if (!w || !fw) {
+        free(w);
+        free(fw);
+        return ORC_ENOMEM;
+    }
+    int st = ORC_OK;
+    /* layout: b for every component, then a, then c (stride N) */
+    for (int i = 0; i < dim && st == ORC_OK; ++i) {
+        st = fabm_oracle_weights(alpha[i], N, w + (int64_t)i * N, w + (int64_t)(dim + i) * N,
+                                 w + (int64_t)(2 * dim + i) * N);
+        if (st == ORC_OK) st = fabm_oracle_constants(alpha[i], h, &ha[i], &ig[i]);
+    }
+    for (int64_t t = 0; t < B && st == ORC_OK; ++t) {
+        const int64_t Nt = N_each ? N_each[t] : N;
+        const double *p = traj_params ? traj_params + t * n_params : params;
+        st = orc_solve_one_multi(dim, h, Nt, rhs, p, w, w + (int64_t)dim * N,
+                                 w + (int64_t)2 * dim * N, N, ha, ig, t2, y0 + t * dim,
+                                 y1 ? y1 + t * dim : NULL, out + t * (N + 1) * dim, fw,
+                                 compensated);
+    }
+    free(w);
+    free(fw);
     return st;
 }

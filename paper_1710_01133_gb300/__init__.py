@@ -28,7 +28,8 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
             "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
-            "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic")
+            "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
+            "fabm_create_multi")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -66,6 +67,7 @@ def load(build_if_missing: bool = True):
     d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     P = ctypes.POINTER
     lib.fabm_create.argtypes = [i, d, d, i64, i, P(d), i, i, P(vp)]
+    lib.fabm_create_multi.argtypes = [i, P(d), d, i64, i, P(d), i, i, P(vp)]
     lib.fabm_solve.argtypes = [vp, P(d), P(d)]
     lib.fabm_solve_batch.argtypes = [vp, i64, P(d), P(d), P(i64), vp, i]
     lib.fabm_solve_batch_ic.argtypes = [vp, i64, P(d), P(d), P(d), P(i64), vp, i]
@@ -103,7 +105,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     lib.fabm_stroboscope.argtypes = [vp, i64, i64, i, vp, d, d, d, i64, i, vp]
     lib.fabm_stroboscope.restype = i
-    for f in ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_solve_batch_ic",
+    for f in ("fabm_create", "fabm_create_multi", "fabm_solve", "fabm_solve_batch",
+              "fabm_solve_batch_ic",
               "fabm_destroy", "fabm_set_block",
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
@@ -133,8 +136,15 @@ def fabm_last_error() -> str:
 
 
 def fabm_create(dim, alpha, h, N, rhs_id, params, precision=FABM_FP64):
+    """alpha: one order, or a sequence of dim orders (fabm_create_multi)."""
     p = _f64(params if params is not None else []).reshape(-1)
     handle = ctypes.c_void_p()
+    if np.ndim(alpha) > 0:
+        al = _f64(alpha).reshape(-1)
+        _check(load().fabm_create_multi(int(dim), _dp(al), float(h), int(N), int(rhs_id),
+                                        _dp(p) if p.size else None, int(p.size), int(precision),
+                                        ctypes.byref(handle)))
+        return handle
     _check(load().fabm_create(int(dim), float(alpha), float(h), int(N), int(rhs_id),
                               _dp(p) if p.size else None, int(p.size), int(precision),
                               ctypes.byref(handle)))
@@ -251,7 +261,8 @@ class Solver:
     def __init__(self, rhs, dim, alpha, h, N, params=None, precision="fp64", block=None,
                  history=None):
         self.rhs = RHS[rhs] if isinstance(rhs, str) else int(rhs)
-        self.dim, self.alpha, self.h, self.N = int(dim), float(alpha), float(h), int(N)
+        self.dim, self.h, self.N = int(dim), float(h), int(N)
+        self.alpha = tuple(float(a) for a in alpha) if np.ndim(alpha) > 0 else float(alpha)
         self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         self.params = _f64(params if params is not None else []).reshape(-1)
         self.handle = fabm_create(dim, alpha, h, N, self.rhs, self.params, self.precision)

@@ -85,7 +85,9 @@ void fabm::set_last_error(const char *msg) { g_last_error = msg; }
 struct fabm_solver {
     int device = 0;
     int dim = 0;
-    double alpha = 0, h = 0;
+    double alpha = 0, h = 0;            // alpha: the largest order of the components
+    double alpha_c[FABM_MAX_DIM] = {};  // order of each component
+    bool multi = false;                 // components have different orders
     int64_t N = 0;
     int rhs = 0;
     int n_params = 0;
@@ -243,6 +245,9 @@ cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &
 int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 {
     if (s->precision == FABM_FP64) return FABM_HIST_FP64;
+    // one order per component: every column tile would need its own weight
+    // operand, so the tensor kernel (one weight operand per tile) is not used
+    if (s->multi) return FABM_HIST_FP32C;
     if (s->hist_kernel == FABM_HIST_TENSOR || s->hist_kernel == FABM_HIST_FP32C)
         return s->hist_kernel;
     return cols >= 64 ? FABM_HIST_TENSOR : FABM_HIST_FP32C;
@@ -284,8 +289,8 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             } else if (hk == FABM_HIST_FP32C) {
                 plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
-                    return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, c, n_chunks, kc, s->spart.p,
-                                             s->sG);
+                    return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, w.stride, c, n_chunks, kc,
+                                             s->spart.p, s->sG);
                 }));
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
                     return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
@@ -391,6 +396,13 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p, y0, sizeof(double) * B * dim, cudaMemcpyHostToDevice, s->sR));
     // y'(0) (1 < alpha < 2): zeros when not given, so that one cached graph
     // serves solves with and without it
+    std::vector<double> y1m;
+    if (y1 && s->multi) {  // components of order <= 1 have no y'(0) term
+        y1m.assign(y1, y1 + B * dim);
+        for (int64_t i = 0; i < B * dim; ++i)
+            if (s->alpha_c[i % dim] <= 1.0) y1m[i] = 0.0;
+        y1 = y1m.data();
+    }
     if (y1)
         FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p + B * dim, y1, sizeof(double) * B * dim,
                                       cudaMemcpyHostToDevice, s->sR));
@@ -415,7 +427,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     bt.ldF = cols;
     bt.Y = Y;
     bt.status = s->status.p;
-    DevWeights w{s->wB.p, s->wA.p, s->wD.p, s->w_ext};
+    DevWeights w{s->wB.p, s->wA.p, s->wD.p, s->w_ext, s->multi ? s->w_ext + 1 : 0};
 
     const std::vector<uintptr_t> key = {
         (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
@@ -518,14 +530,24 @@ extern "C" {
 
 const char *fabm_last_error(void) { return g_last_error.c_str(); }
 
-fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
-                        const double *params, int n_params, int precision, fabm_solver **out)
+namespace {
+
+fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, int rhs_id,
+                          const double *params, int n_params, int precision, fabm_solver **out)
 {
     g_last_error.clear();
     if (!out) return fail(FABM_EINVAL, "out is NULL");
     *out = nullptr;
     if (dim < 1 || dim > FABM_MAX_DIM) return fail(FABM_EINVAL, "dim %d outside 1..%d", dim, FABM_MAX_DIM);
-    if (!(alpha > 0.0 && alpha < 2.0)) return fail(FABM_EINVAL, "alpha %g outside (0, 2)", alpha);
+    if (!alpha_c) return fail(FABM_EINVAL, "alpha is NULL");
+    double alpha = 0.0;
+    bool multi = false;
+    for (int i = 0; i < dim; ++i) {
+        if (!(alpha_c[i] > 0.0 && alpha_c[i] < 2.0))
+            return fail(FABM_EINVAL, "alpha %g outside (0, 2)", alpha_c[i]);
+        alpha = std::max(alpha, alpha_c[i]);
+        multi = multi || alpha_c[i] != alpha_c[0];
+    }
     if (!(h > 0.0) || !std::isfinite(h)) return fail(FABM_EINVAL, "h %g must be positive", h);
     if (N < 1 || N > (1LL << 31)) return fail(FABM_EINVAL, "N %lld outside 1..2^31", (long long)N);
     if (precision != FABM_FP64 && precision != FABM_SPLIT)
@@ -543,12 +565,16 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
         return fail(FABM_ECUDA, "no CUDA device");
     }
     s->dim = dim, s->alpha = alpha, s->h = h, s->N = N, s->rhs = rhs_id;
-    s->n_params = n_params, s->precision = precision;
+    s->n_params = n_params, s->precision = precision, s->multi = multi;
     for (int i = 0; i < n_params; ++i) s->params[i] = params[i];
     s->k.h = h;
-    s->k.h_alpha = std::pow(h, alpha);
-    s->k.inv_gamma2 = 1.0 / std::tgamma(alpha + 2.0);
-    const double inv_g1 = 1.0 / std::tgamma(alpha + 1.0);
+    for (int q = 0; q < FABM_MAX_DIM; ++q) {
+        const double a = alpha_c[q < dim ? q : 0];
+        if (q < dim) s->alpha_c[q] = a;
+        s->k.h_alpha[q] = std::pow(h, a);
+        s->k.inv_gamma2[q] = 1.0 / std::tgamma(a + 2.0);
+    }
+    const int n_sets = multi ? dim : 1;  // weight sets
 
     auto cleanup = [&](fabm_status e) {
         delete s;
@@ -558,9 +584,10 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     // beyond N plus the lag-1 window
     s->w_ext = (N + kMaxBlockL - 1) / kMaxBlockL * kMaxBlockL + 2 * kMaxBlockL;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = s->wB.ensure(s->w_ext + 1);
-    if (e == cudaSuccess) e = s->wA.ensure(s->w_ext + 1);
-    if (e == cudaSuccess) e = s->wD.ensure(s->w_ext + 1);
+    const size_t wlen = (size_t)n_sets * (s->w_ext + 1);
+    if (e == cudaSuccess) e = s->wB.ensure(wlen);
+    if (e == cudaSuccess) e = s->wA.ensure(wlen);
+    if (e == cudaSuccess) e = s->wD.ensure(wlen);
     int prio_lo = 0, prio_hi = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     // the recurrence is the serial chain: its CTAs are scheduled first
@@ -574,20 +601,25 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
     if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
         s->recs.clear();
-        e = timed_launch(s, FABM_KERNEL_WEIGHTS, s->sR, 0.0, [&] {
-            return launch_weights(alpha, s->w_ext, inv_g1, s->k.inv_gamma2, s->wB.p, s->wA.p,
-                                  s->wD.p, s->sR);
-        });
+        for (int q = 0; q < n_sets && e == cudaSuccess; ++q) {
+            const size_t o = (size_t)q * (s->w_ext + 1);
+            const double a = alpha_c[q];
+            e = timed_launch(s, FABM_KERNEL_WEIGHTS, s->sR, 0.0, [&] {
+                return launch_weights(a, s->w_ext, 1.0 / std::tgamma(a + 1.0),
+                                      s->k.inv_gamma2[q], s->wB.p + o, s->wA.p + o, s->wD.p + o,
+                                      s->sR);
+            });
+        }
         s->timing = false;
     }
     if (e == cudaSuccess && precision == FABM_SPLIT) {
         s->L = kSplitSeg;
-        e = s->wBf.ensure(s->w_ext + 1);
-        if (e == cudaSuccess) e = s->wAf.ensure(s->w_ext + 1);
-        if (e == cudaSuccess) e = launch_to_float(s->wB.p, s->w_ext + 1, s->wBf.p, s->sR);
-        if (e == cudaSuccess) e = launch_to_float(s->wA.p, s->w_ext + 1, s->wAf.p, s->sR);
+        e = s->wBf.ensure(wlen);
+        if (e == cudaSuccess) e = s->wAf.ensure(wlen);
+        if (e == cudaSuccess) e = launch_to_float(s->wB.p, (int64_t)wlen, s->wBf.p, s->sR);
+        if (e == cudaSuccess) e = launch_to_float(s->wA.p, (int64_t)wlen, s->wAf.p, s->sR);
         if (e == cudaSuccess) e = prepare_hist_split();
-        s->g_max = (N + kSplitSeg - 1) / kSplitSeg - 1;
+        s->g_max = multi ? 0 : (N + kSplitSeg - 1) / kSplitSeg - 1;  // no tensor tiles when multi
         if (e == cudaSuccess && s->g_max >= 2) {
             e = s->wH.ensure((size_t)(s->g_max + 1) * 2 * 3 * 15 * 64);
             if (e == cudaSuccess) e = s->wHe.ensure((size_t)(s->g_max + 1) * 2);
@@ -603,6 +635,22 @@ fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
                             "fabm_create: %s", cudaGetErrorString(e)));
     *out = s;
     return FABM_OK;
+}
+
+}  // namespace
+
+fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
+                        const double *params, int n_params, int precision, fabm_solver **out)
+{
+    double a[FABM_MAX_DIM] = {alpha, alpha, alpha, alpha};
+    return create_solver(dim, a, h, N, rhs_id, params, n_params, precision, out);
+}
+
+fabm_status fabm_create_multi(int dim, const double *alpha, double h, int64_t N, int rhs_id,
+                              const double *params, int n_params, int precision,
+                              fabm_solver **out)
+{
+    return create_solver(dim, alpha, h, N, rhs_id, params, n_params, precision, out);
 }
 
 fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,

@@ -30,12 +30,15 @@ constexpr int kRecurL = 32;        // targets per block of the FP64 path
 constexpr int kSplitSeg = 64;      // targets per block (= points per segment) of the split path
 constexpr int kMaxParams = FABM_MAX_PARAMS;
 
-// Weight vectors on the device, index 0..N.  B[0] = A[0] = D[0] = 0.
+// Weight vectors on the device, index 0..N.  B[0] = A[0] = D[0] = 0.  With
+// one order per component (stride > 0) component i's vectors start at
+// B + i*stride (A, D likewise); stride 0: one set for all components.
 struct DevWeights {
     const double *B;
     const double *A;
     const double *D;   // D[m] = C(m-1) - A(m)
     int64_t N;
+    int64_t stride = 0;
 };
 
 // One batch of B trajectories of one solver, as the kernels see it.
@@ -54,10 +57,12 @@ struct DevBatch {
     unsigned long long *status;  // [0] = first non-finite (step << 24 | traj), ~0 if none
 };
 
+// Step constants; h^alpha and 1/Gamma(alpha+2) per component (all equal for
+// a single order).
 struct StepConsts {
     double h;
-    double h_alpha;     // h^alpha
-    double inv_gamma2;  // 1/Gamma(alpha+2)
+    double h_alpha[FABM_MAX_DIM];     // h^alpha_i
+    double inv_gamma2[FABM_MAX_DIM];  // 1/Gamma(alpha_i+2)
 };
 
 // a1: weights B(d), A(d), D(m) for d, m = 0..N.
@@ -122,7 +127,9 @@ cudaError_t launch_to_float(const double *x, int64_t n, float *y, cudaStream_t s
 
 // Far history of block c (32 targets) over k < (c-1)*32 in compensated fp32;
 // partials as float2 (sum, -compensation), n_chunks x 2 x 32 x cols.
-cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf, int64_t c,
-                              int n_chunks, int64_t kc, float2 *part, cudaStream_t st);
+// wstride > 0: one order per component (weights of component i at WBf + i*wstride).
+cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf,
+                              int64_t wstride, int64_t c, int n_chunks, int64_t kc, float2 *part,
+                              cudaStream_t st);
 
 }  // namespace fabm

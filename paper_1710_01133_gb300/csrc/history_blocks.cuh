@@ -16,14 +16,18 @@ constexpr int kTile = 256;      // points staged in shared memory at a time
 // One CTA of 32 * kHistCols threads: chunk `chunk` (points k in
 // [chunk*kc, min((chunk+1)*kc, k_end))) of the far history of block c for the
 // columns col0 .. col0+3.
+// MULTI: one order per component, column col's weights at WB + (col % dim)
+// * wstride (WA likewise), one staged window per warp.
+template <bool MULTI = false>
 __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF, int cols,
                                        const double *__restrict__ WB,
                                        const double *__restrict__ WA, int64_t c, int64_t kc,
                                        int64_t k_end, double *__restrict__ part, int64_t chunk,
-                                       int col0)
+                                       int col0, int64_t wstride = 0, int dim = 1)
 {
+    constexpr int NW = MULTI ? kColsPerCta : 1;  // weight windows
     __shared__ double sF[kTile * kColsPerCta];
-    __shared__ double sB[kTile + kL], sA[kTile + kL];
+    __shared__ double sB[NW][kTile + kL], sA[NW][kTile + kL];
     const int64_t k0 = chunk * kc;
     const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
     const int ncol = min(kColsPerCta, cols - col0);
@@ -37,9 +41,12 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
         // weights for d = m - k, m in [cL+1, cL+L], k in [t0, t1):
         // window index i <-> d = cL+2-t1 + i, i < nk+L-1
         const int64_t d_min = c * kL + 2 - t1;
-        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
-            sB[i] = WB[d_min + i];
-            sA[i] = WA[d_min + i];
+        const int nwin = nk + kL - 1;
+        for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
+            const int v = i / nwin, ii = i % nwin;
+            const int64_t o = MULTI ? (int64_t)((col0 + v) % dim) * wstride : 0;
+            sB[v][ii] = WB[o + d_min + ii];
+            sA[v][ii] = WA[o + d_min + ii];
         }
         for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;
@@ -49,12 +56,13 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
         if (w < ncol) {
             // d - d_min = (cL+1+a - (t0+j)) - (cL+2-t1) = a + nk-1-j
             const double *fb = sF + w;
+            const double *wb = sB[MULTI ? w : 0], *wa = sA[MULTI ? w : 0];
             const int base = a + nk - 1;
 #pragma unroll 4
             for (int j = 0; j < nk; ++j) {
                 const double f = fb[j * kColsPerCta];
-                sp = fma(sB[base - j], f, sp);
-                sc = fma(sA[base - j], f, sc);
+                sp = fma(wb[base - j], f, sp);
+                sc = fma(wa[base - j], f, sc);
             }
         }
         __syncthreads();
@@ -82,14 +90,17 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
 
 // One CTA of 32 * kHistCols threads: chunk `chunk` of the far history of
 // block c for the columns col0 .. col0+3, in compensated fp32.
+// MULTI as for hist_fp64_block.
+template <bool MULTI = false>
 __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ldF, int cols,
                                         const float *__restrict__ WB,
                                         const float *__restrict__ WA, int64_t c, int64_t kc,
                                         int64_t k_end, float2 *__restrict__ part, int64_t chunk,
-                                        int col0)
+                                        int col0, int64_t wstride = 0, int dim = 1)
 {
+    constexpr int NW = MULTI ? kColsPerCta : 1;  // weight windows
     __shared__ float sF[kTile * kColsPerCta];
-    __shared__ float sB[kTile + kL], sA[kTile + kL];
+    __shared__ float sB[NW][kTile + kL], sA[NW][kTile + kL];
     const int64_t k0 = chunk * kc;
     const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
     const int ncol = min(kColsPerCta, cols - col0);
@@ -102,9 +113,12 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
         const int nk = (int)(t1 - t0);
         // window index i <-> d = cL+2-t1 + i (see the double kernel)
         const int64_t d_min = c * kL + 2 - t1;
-        for (int i = threadIdx.x; i < nk + kL - 1; i += blockDim.x) {
-            sB[i] = WB[d_min + i];
-            sA[i] = WA[d_min + i];
+        const int nwin = nk + kL - 1;
+        for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
+            const int v = i / nwin, ii = i % nwin;
+            const int64_t o = MULTI ? (int64_t)((col0 + v) % dim) * wstride : 0;
+            sB[v][ii] = WB[o + d_min + ii];
+            sA[v][ii] = WA[o + d_min + ii];
         }
         for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;
@@ -113,6 +127,7 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
         __syncthreads();
         if (w < ncol) {
             const float *fb = sF + w;
+            const float *wb = sB[MULTI ? w : 0], *wa = sA[MULTI ? w : 0];
             const int base = a + nk - 1;
             int j = 0;
             for (; j + kGroup <= nk; j += kGroup) {
@@ -120,8 +135,8 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
                     const float f = fb[(j + u) * kColsPerCta];
-                    gp = fmaf(sB[base - j - u], f, gp);
-                    gc = fmaf(sA[base - j - u], f, gc);
+                    gp = fmaf(wb[base - j - u], f, gp);
+                    gc = fmaf(wa[base - j - u], f, gc);
                 }
                 kahan_add(sp, cp, gp);
                 kahan_add(sc, cc, gc);
@@ -129,8 +144,8 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
             float gp = 0.f, gc = 0.f;
             for (; j < nk; ++j) {
                 const float f = fb[j * kColsPerCta];
-                gp = fmaf(sB[base - j], f, gp);
-                gc = fmaf(sA[base - j], f, gc);
+                gp = fmaf(wb[base - j], f, gp);
+                gc = fmaf(wa[base - j], f, gc);
             }
             kahan_add(sp, cp, gp);
             kahan_add(sc, cc, gc);

@@ -18,13 +18,15 @@ namespace fabm {
 namespace {
 
 // grid = (n_chunks, ceil(cols / kColsPerCta)); block = 32 * kColsPerCta.
+template <bool MULTI>
 __global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
     hist_fp32c_kernel(const double *__restrict__ F, int64_t ldF, int cols,
                       const float *__restrict__ WB, const float *__restrict__ WA, int64_t c,
-                      int64_t kc, int64_t k_end, float2 *__restrict__ part)
+                      int64_t kc, int64_t k_end, float2 *__restrict__ part, int64_t wstride,
+                      int dim)
 {
-    hist::f32c::hist_fp32c_block(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
-                                 blockIdx.y * hist::kColsPerCta);
+    hist::f32c::hist_fp32c_block<MULTI>(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
+                                        blockIdx.y * hist::kColsPerCta, wstride, dim);
 }
 
 __global__ void to_float_kernel(const double *__restrict__ x, int64_t n, float *__restrict__ y)
@@ -44,14 +46,19 @@ cudaError_t launch_to_float(const double *x, int64_t n, float *y, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf, int64_t c,
-                              int n_chunks, int64_t kc, float2 *part, cudaStream_t st)
+cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf,
+                              int64_t wstride, int64_t c, int n_chunks, int64_t kc, float2 *part,
+                              cudaStream_t st)
 {
     const int64_t k_end = (c - 1) * hist::kL;
     if (c < 2 || k_end <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
-    hist_fp32c_kernel<<<grid, kWarp * hist::kColsPerCta, 0, st>>>(bt.F, bt.ldF, bt.cols, WBf, WAf, c, kc,
-                                                           k_end, part);
+    if (wstride)
+        hist_fp32c_kernel<true><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
+            bt.F, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, wstride, bt.dim);
+    else
+        hist_fp32c_kernel<false><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
+            bt.F, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, 0, 1);
     return cudaGetLastError();
 }
 

@@ -20,13 +20,16 @@ namespace fabm {
 namespace {
 
 // grid = (n_chunks, ceil(cols / kColsPerCta)); block = 32 * kColsPerCta.
+// MULTI: one order per component (weights of component i at WB + i*wstride).
+template <bool MULTI>
 __global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
     hist_fp64_kernel(const double *__restrict__ F, int64_t ldF, int cols,
                      const double *__restrict__ WB, const double *__restrict__ WA, int64_t c,
-                     int64_t kc, int64_t k_end, double *__restrict__ part)
+                     int64_t kc, int64_t k_end, double *__restrict__ part, int64_t wstride,
+                     int dim)
 {
-    hist::f64::hist_fp64_block(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
-                               blockIdx.y * hist::kColsPerCta);
+    hist::f64::hist_fp64_block<MULTI>(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
+                                      blockIdx.y * hist::kColsPerCta, wstride, dim);
 }
 
 // a3: G[pc][a][col] = sum_{chunk} part[chunk][pc][a][col], chunk ascending
@@ -74,8 +77,12 @@ cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c,
     if (L != hist::kL) return cudaErrorInvalidValue;
     if (c < 2 || k_end <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
-    hist_fp64_kernel<<<grid, kWarp * hist::kColsPerCta, 0, st>>>(bt.F, bt.ldF, bt.cols, w.B, w.A, c,
-                                                          kc, k_end, part);
+    if (w.stride)
+        hist_fp64_kernel<true><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
+            bt.F, bt.ldF, bt.cols, w.B, w.A, c, kc, k_end, part, w.stride, bt.dim);
+    else
+        hist_fp64_kernel<false><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
+            bt.F, bt.ldF, bt.cols, w.B, w.A, c, kc, k_end, part, 0, 1);
     return cudaGetLastError();
 }
 

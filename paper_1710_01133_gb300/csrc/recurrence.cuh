@@ -64,7 +64,7 @@ __device__ inline void init_one(const DevBatch &bt, int b)
 template <int D, int TPL>
 __host__ __device__ constexpr int recur_smem_doubles()
 {
-    return 2 * (2 * kWarp * TPL + 1) + 2 * D + (kWarp * TPL + 1) * D;
+    return 2 * (2 * kWarp * TPL + 1) * D + 2 * D + (kWarp * TPL + 1) * D;
 }
 
 // One block of steps for trajectory b of the batch, run by a CTA of at least D
@@ -76,9 +76,10 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     constexpr int L = kWarp * TPL;
     // weights pre-multiplied by h^alpha: the accumulators hold y0 + h^alpha * sum,
     // so adding the newest point to the owner's accumulator yields y^P directly
-    double *sB = smem;                   // [2L+1]
-    double *sA = sB + 2 * L + 1;         // [2L+1]
-    double(*sy)[D] = reinterpret_cast<double(*)[D]>(sA + 2 * L + 1);  // [2][D]
+    constexpr int W = 2 * L + 1;
+    double *sB = smem;                   // [D][2L+1], per component (its own order)
+    double *sA = sB + D * W;             // [D][2L+1]
+    double(*sy)[D] = reinterpret_cast<double(*)[D]>(sA + D * W);  // [2][D]
     double(*sF)[D] = sy + 2;             // [L+1][D]: f of the lag-1 block and f_{m0}
     // component of this warp; warps beyond D (a CTA sized for a larger
     // dimension) mirror component 0 and write nothing
@@ -88,10 +89,10 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     const int64_t Nb = bt.N_each[b];
     const int64_t m0 = c * L;  // f_{m0} is the newest known point
     if (m0 >= Nb) return;      // trajectory finished (uniform over the CTA)
-    const double ha = kc.h_alpha;
-    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
-        sB[j] = ha * w.B[j];
-        sA[j] = ha * w.A[j];
+    for (int j = threadIdx.x; j < D * W; j += blockDim.x) {
+        const int q = j / W, jj = j % W;
+        sB[j] = kc.h_alpha[q] * w.B[q * w.stride + jj];
+        sA[j] = kc.h_alpha[q] * w.A[q * w.stride + jj];
     }
     // rows m0-L .. m0 of this trajectory's history, all loads in flight at once
     for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
@@ -105,7 +106,10 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     for (int q = 0; q < kMaxParams; ++q) p[q] = bt.params[(int64_t)b * kMaxParams + q];
     const double y0 = bt.y0[(int64_t)b * D + i];
     const int64_t col = (int64_t)b * D + i;
-    const double ha_ig2 = ha * kc.inv_gamma2;
+    const double ha = kc.h_alpha[i];
+    const double ha_ig2 = ha * kc.inv_gamma2[i];
+    const double *wD = w.D + i * w.stride;
+    sB += i * W, sA += i * W;  // this warp's component
 
     double accP[TPL], accC[TPL], aux[TPL];
     const double f0 = bt.F[col];
@@ -118,7 +122,7 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
         // Taylor part of the initial data at t_m: y0, or y0 + t_m y'(0) for 1 < alpha < 2
         const double Tm = bt.y1 ? fma((double)m * kc.h, y1, y0) : y0;
         const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
-        const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+        const double gC = fma(wD[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
         accP[t] = fma(ha, gP, Tm);
         accC[t] = fma(ha, gC, Tm);
     }
@@ -208,7 +212,7 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
 template <int D, int TPL>
 __host__ __device__ constexpr int recur_split_smem_floats()
 {
-    return 4 * (2 * kWarp * TPL + 1) + 4 * D + 2 * (kWarp * TPL + 1) * D;
+    return 4 * (2 * kWarp * TPL + 1) * D + 4 * D + 2 * (kWarp * TPL + 1) * D;
 }
 
 // smem: recur_split_smem_floats<D, TPL>() floats, 8-byte aligned
@@ -217,9 +221,10 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
                                   const StepConsts &kc, int64_t c, const double *G, float *smem)
 {
     constexpr int L = kWarp * TPL;
-    FF *sB = reinterpret_cast<FF *>(smem);  // [2L+1]  h^alpha B(d)
-    FF *sA = sB + 2 * L + 1;                // [2L+1]  h^alpha A(d)
-    FF(*sy)[D] = reinterpret_cast<FF(*)[D]>(sA + 2 * L + 1);  // [2][D]
+    constexpr int W = 2 * L + 1;
+    FF *sB = reinterpret_cast<FF *>(smem);  // [D][2L+1]  h^alpha_i B_i(d)
+    FF *sA = sB + D * W;                    // [D][2L+1]  h^alpha_i A_i(d)
+    FF(*sy)[D] = reinterpret_cast<FF(*)[D]>(sA + D * W);  // [2][D]
     FF(*sF)[D] = sy + 2;                    // [L+1][D]: f of the lag-1 block and f_{m0}
     const bool act = threadIdx.x / kWarp < D;
     const int i = act ? threadIdx.x / kWarp : 0;
@@ -227,10 +232,10 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
     const int64_t Nb = bt.N_each[b];
     const int64_t m0 = c * L;
     if (m0 >= Nb) return;
-    const double ha = kc.h_alpha;
-    for (int j = threadIdx.x; j <= 2 * L; j += blockDim.x) {
-        sB[j] = ff_from_double(ha * w.B[j]);
-        sA[j] = ff_from_double(ha * w.A[j]);
+    for (int j = threadIdx.x; j < D * W; j += blockDim.x) {
+        const int q = j / W, jj = j % W;
+        sB[j] = ff_from_double(kc.h_alpha[q] * w.B[q * w.stride + jj]);
+        sA[j] = ff_from_double(kc.h_alpha[q] * w.A[q * w.stride + jj]);
     }
     for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
         const int64_t row = m0 - L + j / D;
@@ -248,8 +253,11 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
     }
     const double y0 = bt.y0[(int64_t)b * D + i];
     const int64_t col = (int64_t)b * D + i;
-    const FF ha_ig2 = ff_from_double(ha * kc.inv_gamma2);
+    const double ha = kc.h_alpha[i];
+    const FF ha_ig2 = ff_from_double(ha * kc.inv_gamma2[i]);
     const double f0 = bt.F[col];
+    const double *wD = w.D + i * w.stride;
+    sB += i * W, sA += i * W;  // this warp's component
 
     double baseC[TPL];
     FF bP[TPL], bC[TPL], aux[TPL], nP[TPL], nC[TPL], inc[TPL], fo[TPL];
@@ -261,7 +269,7 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
         aux[t] = ff_from_double(Rhs::aux((double)m * kc.h, p));
         const double Tm = bt.y1 ? fma((double)m * kc.h, y1, y0) : y0;  // Taylor part at t_m
         const double gP = G ? G[(int64_t)a * bt.cols + col] : 0.0;
-        const double gC = fma(w.D[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
+        const double gC = fma(wD[m], f0, G ? G[(int64_t)(L + a) * bt.cols + col] : 0.0);
         baseC[t] = fma(ha, gC, Tm);
         bP[t] = ff_from_double(fma(ha, gP, Tm));
         bC[t] = ff_from_double(baseC[t]);

@@ -114,7 +114,7 @@ __device__ inline void slot_dispatch(int rhs, int dim, Fn &&fn)
 __global__ void weights_slots_kernel(const SlotDev *__restrict__ slots, const int *__restrict__ idx)
 {
     const SlotDev s = slots[idx[blockIdx.y]];
-    const double inv_g2 = s.kc.inv_gamma2;
+    const double inv_g2 = s.kc.inv_gamma2[0];
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d <= s.w_ext;
          d += (int64_t)gridDim.x * blockDim.x) {
         weights_at(d, s.alpha, s.inv_g1, inv_g2, s.WB, s.WA, s.WD);
@@ -323,8 +323,10 @@ void slot_layout(Slot &s, int hk, int64_t w_ext)
     d.G = reinterpret_cast<double *>(take(sizeof(double) * 2 * 2 * kSL * r.dim));
     d.part = take((size_t)8 * kMaxChunksSlot * 2 * kSL * r.dim);
     d.kc.h = r.h;
-    d.kc.h_alpha = std::pow(r.h, r.alpha);
-    d.kc.inv_gamma2 = 1.0 / std::tgamma(r.alpha + 2.0);
+    for (int q = 0; q < FABM_MAX_DIM; ++q) {
+        d.kc.h_alpha[q] = std::pow(r.h, r.alpha);
+        d.kc.inv_gamma2[q] = 1.0 / std::tgamma(r.alpha + 2.0);
+    }
     d.alpha = r.alpha;
     d.inv_g1 = 1.0 / std::tgamma(r.alpha + 1.0);
 }

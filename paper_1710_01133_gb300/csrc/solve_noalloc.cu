@@ -125,7 +125,12 @@ extern "C" fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64
     cudaStream_t st = cudaStreamPerThread;
 
     // host-side constants and inputs
-    StepConsts kc{h, std::pow(h, alpha), 1.0 / std::tgamma(alpha + 2.0)};
+    StepConsts kc{};
+    kc.h = h;
+    for (int q = 0; q < FABM_MAX_DIM; ++q) {
+        kc.h_alpha[q] = std::pow(h, alpha);
+        kc.inv_gamma2[q] = 1.0 / std::tgamma(alpha + 2.0);
+    }
     const double inv_g1 = 1.0 / std::tgamma(alpha + 1.0);
     double par[kMaxParams] = {};
     for (int i = 0; i < n_params; ++i) par[i] = params[i];
@@ -140,7 +145,7 @@ extern "C" fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64
     // block's end plus the lag-1 window
     const int64_t nblk = (N + kNaL - 1) / kNaL;
     const int64_t w_ext = nblk * kNaL + 2 * kNaL;
-    NA_TRY(launch_weights(alpha, w_ext, inv_g1, kc.inv_gamma2, S + kOffB, S + kOffA, S + kOffD, st));
+    NA_TRY(launch_weights(alpha, w_ext, inv_g1, kc.inv_gamma2[0], S + kOffB, S + kOffA, S + kOffD, st));
 
     DevBatch bt{};
     bt.dim = dim;

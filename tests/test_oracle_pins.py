@@ -420,3 +420,48 @@ def test_stroboscope_exact_on_linear_trajectories():
     np.testing.assert_allclose(s[0, inside], 2.0 - 3.0 * tj[inside], rtol=1e-14)
     np.testing.assert_allclose(s[1, inside], 1.0 + tj[inside], rtol=1e-14)
     assert np.all(np.isnan(s[:, ~inside]))
+
+
+# ------------------------------------------- one order per component -------
+# Sec. 5's systems carry one order per equation (alpha1, alpha2); each
+# component then uses the weights and constants of its own order.
+
+def test_multi_order_independent_components_split_exactly():
+    """Uncoupled components (linear RHS) solved as one system with orders
+    (0.5, 0.9, 1.4) equal, bit for bit, the three scalar solves."""
+    al = [0.5, 0.9, 1.4]
+    y0, y1 = [1.0, -0.5, 2.0], [0.0, 0.0, 0.3]
+    h, N = 0.01, 500
+    y = oracle.solve("linear", al, h, N, y0, params=[0.7], y1=y1)
+    for i, a in enumerate(al):
+        yi = oracle.solve("linear", a, h, N, [y0[i]], params=[0.7],
+                          y1=[y1[i]] if a > 1 else None)
+        assert np.array_equal(y[:, i], yi[:, 0]), i
+
+
+def test_multi_order_equal_orders_is_the_single_order_scheme():
+    al = 0.83
+    a = oracle.solve("lorenz", al, 1e-3, 700, [1.0, 1.0, 1.0])
+    b = oracle.solve("lorenz", [al, al, al], 1e-3, 700, [1.0, 1.0, 1.0])
+    assert np.array_equal(a, b)
+
+
+def test_multi_order_constant_rhs_is_exact():
+    al = [0.3, 0.75, 1.6]
+    h, N = 0.02, 300
+    t = _grid(h, N)
+    y = oracle.solve("const", al, h, N, [0.1, 0.2, 0.3], params=[1.5], y1=[9.0, 9.0, -0.4])
+    for i, a in enumerate(al):
+        ex = [0.1, 0.2, 0.3][i] + (-0.4 * t if a > 1 else 0.0) + 1.5 * t ** a / math.gamma(a + 1)
+        np.testing.assert_allclose(y[:, i], ex, rtol=1e-14, atol=1e-14)
+
+
+def test_multi_order_lcr_equilibria():
+    """E+- of Sec. 5 stay fixed at f = 0 for different orders alpha1, alpha2."""
+    g = _lcr_golden()
+    s, a, b = g["sigma"], g["a"], g["b"]
+    x = s * (a - b) / (1 + s * b)
+    yv = (b - a) / (1 + s * b)
+    for E in ([x, yv], [-x, -yv]):
+        traj = oracle.solve("lcr", [0.9, 0.7], 0.01, 300, E, params=[s, g["omega"], a, b, 0.0])
+        assert np.max(np.abs(traj - np.array(E))) < 1e-12
