@@ -383,6 +383,9 @@ def main():
     ap.add_argument("--timing-period", type=int, default=64,
                     help="time the kernel launches of every k-th time block")
     ap.add_argument("--n-requests", type=int, default=2000, help="served-mix: requests")
+    ap.add_argument("--autotune", type=int, default=0, metavar="N_PROBE",
+                    help="before the warm-up, let the library's autotuner pick the history "
+                         "kernel settings on solves truncated to N_PROBE steps (0: off)")
     ap.add_argument("--k-max", type=int, default=14, help="served-mix: N = 2^k, k <= k_max")
     args = ap.parse_args()
     if args.workload == "served-mix":
@@ -414,6 +417,9 @@ def main():
     fabm.load()
     solver = fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision=args.precision)
     wstats = solver.kernel_stats()["weights"]
+    tuned = None
+    if args.autotune > 0:
+        tuned = solver.autotune(w.y0, traj_params=w.traj_params, n_probe=args.autotune)
 
     out_dev = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -497,6 +503,9 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches,
             "clocks": clocks,
+            "autotune": None if tuned is None else {
+                "n_probe": args.autotune,
+                "candidates_ms_kernel_setting": [[round(m, 3), k, c] for m, k, c in tuned]},
             "output_finite": finite,
         }
         if not args.no_cpu_baseline and ws == 1:
