@@ -326,7 +326,7 @@ def run_served(args):
                     continue
                 srv.step()
                 now = time.perf_counter() - t0
-                done = [tk for tk in inflight if srv.poll(tk) >= fabm.FABM_REQ_DONE]
+                done = srv.finished()
                 for tk in done:
                     r = inflight.pop(tk)
                     srv.result(tk)

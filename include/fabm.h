@@ -304,6 +304,10 @@ fabm_status fabm_server_shape(fabm_server *s, int64_t ticket, int64_t *N, int *d
 /* Drop a request in any state; a running one releases its device memory at
  * once.  The ticket becomes unknown.  FABM_EINVAL for an unknown ticket. */
 fabm_status fabm_server_cancel(fabm_server *s, int64_t ticket);
+/* Tickets of requests that finished (done or failed) since the last call, in
+ * the order they finished: up to max of them into tickets, their number in *n;
+ * the rest are kept for the next call.  Saves polling every request. */
+fabm_status fabm_server_finished(fabm_server *s, int64_t *tickets, int max, int *n);
 /* Steps run, kernel launches made, device bytes held by admitted requests. */
 fabm_status fabm_server_stats(const fabm_server *s, int64_t *steps, int64_t *launches,
                               size_t *bytes_in_use);

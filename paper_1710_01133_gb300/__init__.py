@@ -29,7 +29,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
-            "fabm_create_multi")
+            "fabm_create_multi", "fabm_server_finished")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -92,10 +92,11 @@ def load(build_if_missing: bool = True):
     lib.fabm_server_resume.argtypes = [vp, vp, ctypes.c_size_t, P(i64)]
     lib.fabm_server_cancel.argtypes = [vp, i64]
     lib.fabm_server_shape.argtypes = [vp, i64, P(i64), P(i)]
+    lib.fabm_server_finished.argtypes = [vp, P(i64), i, P(i)]
     for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
               "fabm_server_result", "fabm_server_stats", "fabm_server_destroy",
               "fabm_server_checkpoint", "fabm_server_resume", "fabm_server_cancel",
-              "fabm_server_shape"):
+              "fabm_server_shape", "fabm_server_finished"):
         getattr(lib, f).restype = i
     lib.fabm_autotune.argtypes = [vp, i64, P(d), P(d), i64, i, P(d), P(i), P(i), P(i)]
     lib.fabm_autotune.restype = i
@@ -446,6 +447,17 @@ class Server:
 
     def cancel(self, ticket):
         _check(load().fabm_server_cancel(self.handle, int(ticket)))
+
+    def finished(self, max_n=65536):
+        """Tickets that finished since the last call."""
+        buf = (ctypes.c_int64 * max_n)()
+        n = ctypes.c_int()
+        out = []
+        while True:
+            _check(load().fabm_server_finished(self.handle, buf, max_n, ctypes.byref(n)))
+            out.extend(buf[: n.value])
+            if n.value < max_n:
+                return out
 
     def stats(self):
         s, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()

@@ -36,8 +36,8 @@ using namespace fabm;
 namespace {
 
 constexpr int kSL = kRecurL;        // block length of served solves (32)
-constexpr int kMaxChunksSlot = 64;  // far-history chunks per slot and block
-constexpr int kMinChunkPts = 256;   // points per chunk at least
+constexpr int kMaxChunksSlot = 16;  // far-history chunks per slot and block
+constexpr int kMinChunkPts = 1024;  // points per chunk at least
 
 struct SlotDev {
     int rhs, dim, hk;
@@ -58,7 +58,7 @@ struct Item {
     int64_t c;     // block index (history/combine: target block; recurrence: block to run)
     int64_t kc;    // history: points per chunk
     int gbuf;      // G buffer (c % 2) the item reads or writes; -1: none
-    int pad;
+    int pad;       // history: column of the request
 };
 
 __device__ inline DevBatch slot_batch(const SlotDev &s)
@@ -135,19 +135,110 @@ __global__ void init_slots_kernel(const SlotDev *__restrict__ slots, const int *
     slot_dispatch(s.rhs, s.dim, [&]<class R, int D>() { init_one<R, D>(bt, 0); });
 }
 
-// One CTA (4 warps) per (slot, chunk) item of the far history.
-__global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
-    hist_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+// Far history, one warp per (slot, chunk, column) item: requests have one to
+// three columns, so a CTA of four warps takes four items (of one request or
+// several) and no warp idles.  Each warp stages its own tiles of f and of the
+// weights and runs the same per-column arithmetic as the batch kernels
+// (hist_fp64_block / hist_fp32c_block), so a request's partial sums do not
+// depend on which items share its CTA.
+constexpr int kWarpsPerHistCta = 4;
+
+__device__ void hist_warp_f64(const SlotDev &s, const Item &it, double *sF, double *sB, double *sA)
 {
-    const Item it = items[blockIdx.x];
-    const SlotDev s = slots[it.slot];
+    using hist::kL;
+    constexpr int kT = hist::f64::kTile;
+    const int a = threadIdx.x % kWarp, q = it.pad, dim = s.dim;
     const int64_t k_end = (it.c - 1) * kSL;
-    if (s.hk == FABM_HIST_FP32C)
-        hist::f32c::hist_fp32c_block(s.F, s.dim, s.dim, s.WBf, s.WAf, it.c, it.kc, k_end,
-                                     static_cast<float2 *>(s.part), it.chunk, 0);
-    else
-        hist::f64::hist_fp64_block(s.F, s.dim, s.dim, s.WB, s.WA, it.c, it.kc, k_end,
-                                   static_cast<double *>(s.part), it.chunk, 0);
+    const int64_t k0 = (int64_t)it.chunk * it.kc;
+    const int64_t k1 = k0 + it.kc < k_end ? k0 + it.kc : k_end;
+    double sp = 0.0, sc = 0.0;
+    for (int64_t t0 = k0; t0 < k1; t0 += kT) {
+        const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
+        const int nk = (int)(t1 - t0);
+        const int64_t d_min = it.c * kL + 2 - t1;
+        for (int i = a; i < nk + kL - 1; i += kWarp) sB[i] = s.WB[d_min + i], sA[i] = s.WA[d_min + i];
+        for (int i = a; i < nk; i += kWarp) sF[i] = s.F[(t0 + i) * dim + q];
+        __syncwarp();
+        const int base = a + nk - 1;
+#pragma unroll 4
+        for (int j = 0; j < nk; ++j) {
+            const double f = sF[j];
+            sp = fma(sB[base - j], f, sp);
+            sc = fma(sA[base - j], f, sc);
+        }
+        __syncwarp();
+    }
+    double *out = static_cast<double *>(s.part) + ((int64_t)(it.chunk * 2) * kL + a) * dim + q;
+    out[0] = sp;
+    out[(int64_t)kL * dim] = sc;
+}
+
+__device__ void hist_warp_f32c(const SlotDev &s, const Item &it, float *sF, float *sB, float *sA)
+{
+    using hist::kL;
+    constexpr int kT = hist::f32c::kTile, kG = hist::f32c::kGroup;
+    const int a = threadIdx.x % kWarp, q = it.pad, dim = s.dim;
+    const int64_t k_end = (it.c - 1) * kSL;
+    const int64_t k0 = (int64_t)it.chunk * it.kc;
+    const int64_t k1 = k0 + it.kc < k_end ? k0 + it.kc : k_end;
+    float sp = 0.f, cp = 0.f, sc = 0.f, cc = 0.f;
+    for (int64_t t0 = k0; t0 < k1; t0 += kT) {
+        const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
+        const int nk = (int)(t1 - t0);
+        const int64_t d_min = it.c * kL + 2 - t1;
+        for (int i = a; i < nk + kL - 1; i += kWarp) sB[i] = s.WBf[d_min + i], sA[i] = s.WAf[d_min + i];
+        for (int i = a; i < nk; i += kWarp) sF[i] = (float)s.F[(t0 + i) * dim + q];
+        __syncwarp();
+        const int base = a + nk - 1;
+        int j = 0;
+        for (; j + kG <= nk; j += kG) {
+            float gp = 0.f, gc = 0.f;
+#pragma unroll
+            for (int u = 0; u < kG; ++u) {
+                const float f = sF[j + u];
+                gp = fmaf(sB[base - j - u], f, gp);
+                gc = fmaf(sA[base - j - u], f, gc);
+            }
+            hist::f32c::kahan_add(sp, cp, gp);
+            hist::f32c::kahan_add(sc, cc, gc);
+        }
+        float gp = 0.f, gc = 0.f;
+        for (; j < nk; ++j) {
+            const float f = sF[j];
+            gp = fmaf(sB[base - j], f, gp);
+            gc = fmaf(sA[base - j], f, gc);
+        }
+        hist::f32c::kahan_add(sp, cp, gp);
+        hist::f32c::kahan_add(sc, cc, gc);
+        __syncwarp();
+    }
+    float2 *out = static_cast<float2 *>(s.part) + ((int64_t)(it.chunk * 2) * kL + a) * dim + q;
+    out[0] = make_float2(sp, -cp);
+    out[(int64_t)kL * dim] = make_float2(sc, -cc);
+}
+
+// n items; CTA x takes items 4x .. 4x+3, one per warp.
+__global__ void __launch_bounds__(kWarp *kWarpsPerHistCta)
+    hist_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items, int n)
+{
+    constexpr int kBytesF64 = (hist::f64::kTile + 2 * (hist::f64::kTile + hist::kL)) * 8;
+    constexpr int kBytesF32 = (hist::f32c::kTile + 2 * (hist::f32c::kTile + hist::kL)) * 4;
+    constexpr int kWarpBytes = kBytesF64 > kBytesF32 ? kBytesF64 : kBytesF32;
+    __shared__ __align__(16) unsigned char smem[kWarpsPerHistCta][kWarpBytes];
+    const int w = threadIdx.x / kWarp;
+    const int64_t g = (int64_t)blockIdx.x * kWarpsPerHistCta + w;
+    if (g >= n) return;  // uniform over the warp; warps never synchronize with each other
+    const Item it = items[g];
+    const SlotDev s = slots[it.slot];
+    if (s.hk == FABM_HIST_FP32C) {
+        float *sF = reinterpret_cast<float *>(smem[w]);
+        float *sB = sF + hist::f32c::kTile;
+        hist_warp_f32c(s, it, sF, sB, sB + hist::f32c::kTile + hist::kL);
+    } else {
+        double *sF = reinterpret_cast<double *>(smem[w]);
+        double *sB = sF + hist::f64::kTile;
+        hist_warp_f64(s, it, sF, sB, sB + hist::f64::kTile + hist::kL);
+    }
 }
 
 // One CTA per slot: G[gbuf][kind][t][col] = sum over the chunks in ascending
@@ -352,6 +443,7 @@ struct fabm_server {
     std::vector<Slot> slots;
     std::unordered_map<int64_t, Result> results;
     std::unordered_map<int64_t, std::pair<int64_t, int>> shapes;  // ticket -> (N, dim)
+    std::vector<int64_t> finished;  // finished since the last fabm_server_finished
     int64_t next_ticket = 1;
     cudaStream_t sR = nullptr, sG = nullptr;
     cudaEvent_t evUp = nullptr;
@@ -397,6 +489,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             if (S->slots.empty()) {  // can never fit
                 S->queue.pop_front();
                 S->results[r.ticket] = {FABM_REQ_FAILED, FABM_ENOMEM, {}};
+                S->finished.push_back(r.ticket);
                 continue;
             }
             break;
@@ -410,6 +503,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             if (S->slots.empty()) {
                 S->queue.pop_front();
                 S->results[r.ticket] = {FABM_REQ_FAILED, FABM_ENOMEM, {}};
+                S->finished.push_back(r.ticket);
                 continue;
             }
             break;  // retry when memory frees up
@@ -442,7 +536,8 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             int64_t kc;
             int n;
             slot_chunks(cn, &kc, &n);
-            for (int ch = 0; ch < n; ++ch) hist.push_back({i, ch, cn, kc, (int)(cn % 2), 0});
+            for (int ch = 0; ch < n; ++ch)
+                for (int q = 0; q < s.req.dim; ++q) hist.push_back({i, ch, cn, kc, (int)(cn % 2), q});
             comb.push_back({i, n, cn, 0, (int)(cn % 2), 0});
         }
         rec.push_back({i, 0, s.c, 0, s.c >= 2 ? (int)(s.c % 2) : -1, 0});
@@ -501,7 +596,9 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     SRV_TRY(cudaStreamWaitEvent(S->sG, S->evUp, 0));
     // 4. shared launches
     if (!hist.empty()) {
-        hist_slots_kernel<<<(unsigned)hist.size(), kWarp * hist::kColsPerCta, 0, S->sG>>>(S->d_slots, dH);
+        const unsigned hblocks = (unsigned)((hist.size() + kWarpsPerHistCta - 1) / kWarpsPerHistCta);
+        hist_slots_kernel<<<hblocks, kWarp * kWarpsPerHistCta, 0, S->sG>>>(S->d_slots, dH,
+                                                                           (int)hist.size());
         SRV_TRY(cudaGetLastError());
         combine_slots_kernel<<<(unsigned)comb.size(), 256, 0, S->sG>>>(S->d_slots, dC);
         SRV_TRY(cudaGetLastError());
@@ -532,6 +629,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
         SRV_TRY(cudaMemcpy(&st, s.dev.status, sizeof st, cudaMemcpyDeviceToHost));
         res.state = st == ~0ull ? FABM_REQ_DONE : FABM_REQ_FAILED;
         res.status = st == ~0ull ? FABM_OK : FABM_ENONFINITE;
+        S->finished.push_back(s.req.ticket);
         SRV_TRY(cudaFreeAsync(s.mem, S->sR));
         S->in_use -= s.bytes;
     }
@@ -765,6 +863,7 @@ fabm_status fabm_server_cancel(fabm_server *S, int64_t ticket)
     if (it == S->results.end()) return srv_fail(FABM_EINVAL, "unknown ticket %lld", (long long)ticket);
     S->results.erase(it);
     S->shapes.erase(ticket);
+    S->finished.erase(std::remove(S->finished.begin(), S->finished.end(), ticket), S->finished.end());
     for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
         if (q->ticket == ticket) {
             S->queue.erase(q);
@@ -778,6 +877,18 @@ fabm_status fabm_server_cancel(fabm_server *S, int64_t ticket)
             return FABM_OK;
         }
     return FABM_OK;  // finished: its result is dropped
+}
+
+fabm_status fabm_server_finished(fabm_server *S, int64_t *tickets, int max, int *n)
+{
+    set_last_error("");
+    if (!S || !n || max < 0 || (max > 0 && !tickets)) return srv_fail(FABM_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    const int k = (int)std::min<size_t>((size_t)max, S->finished.size());
+    for (int i = 0; i < k; ++i) tickets[i] = S->finished[i];
+    S->finished.erase(S->finished.begin(), S->finished.begin() + k);
+    *n = k;
+    return FABM_OK;
 }
 
 fabm_status fabm_server_stats(const fabm_server *S, int64_t *steps, int64_t *launches,

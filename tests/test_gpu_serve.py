@@ -204,3 +204,17 @@ def test_checkpoint_errors(gpu_lib):
         with pytest.raises(gpu_lib.FabmError) as e:
             other.resume(bytes(state))                  # precision mismatch
         assert e.value.status == gpu_lib.FABM_EINVAL
+
+
+def test_finished_lists_each_request_once(gpu_lib):
+    with gpu_lib.Server(8 << 30) as srv:
+        tickets = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX]
+        seen = []
+        for _ in range(1000):
+            srv.step()
+            seen += srv.finished()
+            if len(seen) == len(tickets):
+                break
+        assert sorted(seen) == sorted(tickets)
+        assert all(srv.poll(t) == gpu_lib.FABM_REQ_DONE for t in tickets)
+        assert srv.finished() == []
