@@ -31,15 +31,19 @@
 // slice instead of 8 KB.  These tiles depend only on the lag c - seg and are
 // built once per solver.
 //
-// CTA layout (1 CTA per SM, 320 threads): warp 0 streams segments into a
+// CTA layout (1 CTA per SM, 384 threads): warp 0 streams segments into a
 // 3-stage shared-memory ring with bulk copies; warp 1 issues the MMAs into one
 // of two TMEM accumulator sets (512 columns), one weight kind at a time with
 // per-kind barriers; warps 2..9 drain the other set, each warp one TMEM lane
 // quadrant (its columns) and the 64 targets of one kind, with
-// Kahan-compensated fp32 sums held in registers.  Measured in isolation: the
-// copy ring alone streams at the HBM peak, the MMAs alone reach ~0.6 of the
-// bf16 peak (N = 64 per MMA), and the drain's arithmetic on the MMA warp's
-// sub-partition costs ~15% (issue slots shared with the MMA thread).
+// Kahan-compensated fp32 sums held in registers.  A warp can only read the
+// TMEM lanes of its own sub-partition, so quadrant 1 is drained on the MMA
+// warp's sub-partition; there warps 5 and 9 only scale their values into
+// shared memory and warps 10 and 11 (other sub-partitions) keep the sums, so
+// that the MMA thread keeps its issue slots.  Measured in isolation: the copy
+// ring alone streams at the HBM peak, the MMAs alone reach ~0.6 of the bf16
+// peak (N = 64 per MMA), the full kernel 0.47-0.53 (0.43-0.49 with the whole
+// drain on the MMA warp's sub-partition).
 // Every wait is bounded; on timeout the CTA sets an error flag, waits for its
 // own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -59,10 +63,14 @@ constexpr int kHk = 15;              // Hankel core matrices per (kind, slice)
 constexpr int kFBytes = 3 * kMC * kSeg * 2;          // 49152: 3 slices of 128 x 64 bf16
 constexpr int kWBytes = 2 * 3 * kHk * 128;           // 11520
 constexpr int kStageStride = 61440;                  // F + W, padded to 1 KB
-constexpr int kThreads = 320;     // warp 0: copies, warp 1: MMAs, warps 2..9: drain
+// warp 0: copies, warp 1: MMAs, warps 2..9: drain (warps 5 and 9, on the MMA
+// warp's sub-partition, only move their values to shared memory), warps 10 and
+// 11: the Kahan sums of warps 5 and 9
+constexpr int kThreads = 384;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiT = 64;         // targets per drain thread
-constexpr size_t kSmemBytes = (size_t)kStages * kStageStride + 1024;
+constexpr int kStashBytes = 2 * 2 * kEpiT * 32 * 4;  // [buffer][kind][target][column]
+constexpr size_t kSmemBytes = (size_t)kStages * kStageStride + 1024 + kStashBytes;
 constexpr long long kWaitCycles = 4000000000LL;      // ~2 s at 2 GHz
 
 __device__ __forceinline__ int exp_clamp(int e) { return e < -126 ? -126 : (e > 127 ? 127 : e); }
@@ -207,7 +215,10 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
     uint64_t *acc_full = empty + kStages;  // [buffer][kind]
     uint64_t *acc_empty = acc_full + 4;    // [buffer][kind]
     uint64_t *done = acc_empty + 4;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *stash_full = done + 1;         // [buffer][kind]
+    uint64_t *stash_empty = stash_full + 4;  // [buffer][kind]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(stash_empty + 4);
+    float *stash = reinterpret_cast<float *>(smem + kStages * kStageStride + 1024);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ct = blockIdx.x, ch = blockIdx.y;
@@ -219,6 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
         for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1), mbar_init(&empty[i], 1);
         for (int i = 0; i < 4; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], kEpiWarps / 2);
         mbar_init(done, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&stash_full[i], 1), mbar_init(&stash_empty[i], 1);
         fence_mbar_init();
     }
     if (warp == 1) tmem_alloc(tslot, 512);
@@ -298,21 +310,11 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
             mma_commit(done);
             if (!mbar_wait(done, 0, kWaitCycles)) ok = false;
         }
-    } else {
-        // drain: warp w reads TMEM lanes 32*(w%4).. (its columns) and the 64
-        // targets of one kind.  Kahan sums in fp32; the compensation terms are
-        // kept as packed bf16 pairs (fp32's exponent range, 2^-9 relative error
-        // on a term that is itself below half an ulp of the sum).
-        const int q = warp % 4, kind = (warp - 2) / 4, t0 = 0;
-        const int cloc = q * 32 + lane;
-        const int64_t col = (int64_t)ct * kMC + cloc;
-        float sum[kEpiT];
-        uint32_t cmp2[kEpiT / 2];
-#pragma unroll
-        for (int t = 0; t < kEpiT; ++t) sum[t] = 0.f;
-#pragma unroll
-        for (int t = 0; t < kEpiT / 2; ++t) cmp2[t] = 0u;
-        // exponents of the first segment; later ones are fetched a segment ahead
+    } else if (warp < 10 && warp % 4 == 1) {
+        // light drain of TMEM quadrant 1 (the MMA warp's sub-partition): scale
+        // the values and hand them to warp 10 or 11 through shared memory
+        const int kind = (warp - 2) / 4;
+        const int cloc = 32 + lane;
         int ef_next = a.Ef[((int64_t)s_lo * a.n_ct + ct) * kMC + cloc];
         int ew_next = a.Ew[(a.c - s_lo) * 2 + kind];
         for (int i = 0; i < nseg; ++i) {
@@ -324,14 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
                 ew_next = a.Ew[(a.c - sn) * 2 + kind];
             }
-            if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles)) {
+            if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles) ||
+                !mbar_wait(&stash_empty[b * 2 + kind], bph ^ 1, kWaitCycles)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + kind * 64 + t0;
-            // software pipeline over 8 pieces of 8 targets: the load of piece
-            // p+1 is in flight while piece p is added
+            const uint32_t base = tmem + (32u << 16) + b * 256 + kind * 64;
+            float *st = stash + (b * 2 + kind) * kEpiT * 32 + lane;
             uint32_t ra[16], rb[16];
             tmem_ld8x2_issue(base, base + 128, ra);
             tmem_wait16(ra);
@@ -341,30 +343,105 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 uint32_t(&nxt)[16] = (p % 2 == 0) ? rb : ra;
                 if (p + 1 < kEpiT / 8) tmem_ld8x2_issue(base + (p + 1) * 8, base + 128 + (p + 1) * 8, nxt);
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    const int t = p * 8 + j;
-                    const uint32_t cw = cmp2[t / 2];
-                    float cnew[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const float c = __uint_as_float(u ? (cw & 0xffff0000u) : (cw << 16));
-                        const float v = __uint_as_float(cur[j + u]) + __uint_as_float(cur[8 + j + u]);
-                        const float y = v * scale - c;
-                        const float s2 = sum[t + u] + y;
-                        cnew[u] = (s2 - sum[t + u]) - y;
-                        sum[t + u] = s2;
-                    }
-                    __nv_bfloat162 pk = __floats2bfloat162_rn(cnew[0], cnew[1]);
-                    cmp2[t / 2] = *reinterpret_cast<uint32_t *>(&pk);
-                }
+                for (int j = 0; j < 8; ++j)
+                    st[(p * 8 + j) * 32] = (__uint_as_float(cur[j]) + __uint_as_float(cur[8 + j])) * scale;
                 if (p + 1 < kEpiT / 8) tmem_wait16(nxt);
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b * 2 + kind]);
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[b * 2 + kind]);
+                mbar_arrive(&stash_full[b * 2 + kind]);
+            }
+        }
+    } else {
+        // drain: warps 2..9 read TMEM lanes 32*(w%4).. (their columns) and the
+        // 64 targets of one kind; warps 10 and 11 take quadrant 1's values from
+        // shared memory.  Kahan sums in fp32; the compensation terms are kept as
+        // packed bf16 pairs (fp32's exponent range, 2^-9 relative error on a term
+        // that is itself below half an ulp of the sum).
+        const bool helper = warp >= 10;
+        const int q = helper ? 1 : warp % 4, kind = helper ? warp - 10 : (warp - 2) / 4;
+        const int cloc = q * 32 + lane;
+        const int64_t col = (int64_t)ct * kMC + cloc;
+        float sum[kEpiT];
+        uint32_t cmp2[kEpiT / 2];
+#pragma unroll
+        for (int t = 0; t < kEpiT; ++t) sum[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kEpiT / 2; ++t) cmp2[t] = 0u;
+        // Kahan step for targets t, t+1 with the scaled values v0, v1
+        auto add2 = [&](int t, float v0, float v1) {
+            const uint32_t cw = cmp2[t / 2];
+            float cnew[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float c = __uint_as_float(u ? (cw & 0xffff0000u) : (cw << 16));
+                const float y = (u ? v1 : v0) - c;
+                const float s2 = sum[t + u] + y;
+                cnew[u] = (s2 - sum[t + u]) - y;
+                sum[t + u] = s2;
+            }
+            __nv_bfloat162 pk = __floats2bfloat162_rn(cnew[0], cnew[1]);
+            cmp2[t / 2] = *reinterpret_cast<uint32_t *>(&pk);
+        };
+        if (helper) {
+            for (int i = 0; i < nseg; ++i) {
+                const int b = i & 1;
+                const uint32_t bph = (i >> 1) & 1;
+                if (!mbar_wait(&stash_full[b * 2 + kind], bph, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                const float *st = stash + (b * 2 + kind) * kEpiT * 32 + lane;
+#pragma unroll
+                for (int t = 0; t < kEpiT; t += 2) add2(t, st[t * 32], st[(t + 1) * 32]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&stash_empty[b * 2 + kind]);
+            }
+        } else {
+            // exponents of the first segment; later ones are fetched a segment ahead
+            int ef_next = a.Ef[((int64_t)s_lo * a.n_ct + ct) * kMC + cloc];
+            int ew_next = a.Ew[(a.c - s_lo) * 2 + kind];
+            for (int i = 0; i < nseg; ++i) {
+                const int b = i & 1;
+                const uint32_t bph = (i >> 1) & 1;
+                const float scale = pow2f(ef_next + ew_next - 16);
+                if (i + 1 < nseg) {
+                    const int64_t sn = s_lo + i + 1;
+                    ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
+                    ew_next = a.Ew[(a.c - sn) * 2 + kind];
+                }
+                if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 256 + kind * 64;
+                // software pipeline over 8 pieces of 8 targets: the load of piece
+                // p+1 is in flight while piece p is added
+                uint32_t ra[16], rb[16];
+                tmem_ld8x2_issue(base, base + 128, ra);
+                tmem_wait16(ra);
+#pragma unroll
+                for (int p = 0; p < kEpiT / 8; ++p) {
+                    uint32_t(&cur)[16] = (p % 2 == 0) ? ra : rb;
+                    uint32_t(&nxt)[16] = (p % 2 == 0) ? rb : ra;
+                    if (p + 1 < kEpiT / 8) tmem_ld8x2_issue(base + (p + 1) * 8, base + 128 + (p + 1) * 8, nxt);
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2)
+                        add2(p * 8 + j,
+                             (__uint_as_float(cur[j]) + __uint_as_float(cur[8 + j])) * scale,
+                             (__uint_as_float(cur[j + 1]) + __uint_as_float(cur[8 + j + 1])) * scale);
+                    if (p + 1 < kEpiT / 8) tmem_wait16(nxt);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b * 2 + kind]);
+            }
         }
         if (ok && col < a.cols) {
-            float2 *out = a.part + ((int64_t)(ch * 2 + kind) * kSeg + t0) * a.cols + col;
+            float2 *out = a.part + ((int64_t)(ch * 2 + kind) * kSeg) * a.cols + col;
 #pragma unroll
             for (int t = 0; t < kEpiT; ++t) {
                 const uint32_t cw = cmp2[t / 2];
