@@ -71,16 +71,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // ------------------------------------------------------------- tcgen05 ---
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
@@ -101,35 +91,12 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, no swizzle: start address, leading byte
-// offset (between core matrices along K) and stride byte offset (between
-// 8-row core-matrix groups along M or N); bits 46-47 hold the sm_100 version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
 // Instruction descriptor for kind::f16 with bf16 A and B (both K-major) and an
 // fp32 accumulator, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
 }
 
 // The six products of order <= 2 of three-term splits a = a0+a1+a2 and
@@ -155,10 +122,12 @@ __device__ __forceinline__ void mma_bf16_split6(uint32_t d0, uint32_t d12, uint6
         : "memory");
 }
 
-// Descriptor of a no-swizzle K-major operand at shared address addr with the
-// given leading/stride byte offsets, as two 32-bit words; the address field
-// is the low 14 bits of `lo`, so a byte offset o (o/16 added to lo) moves it
-// as long as the address stays below 256 KB.
+// Shared-memory matrix descriptor of a no-swizzle K-major operand, as two
+// 32-bit words: bits 0-13 start address / 16, bits 16-29 leading-dimension
+// byte offset / 16, bits 32-45 stride-dimension byte offset / 16, bit 46 the
+// descriptor version, swizzle bits 0.  The address field is the low 14 bits
+// of `lo`, so adding o/16 to lo moves the operand by o bytes as long as the
+// address stays below 256 KB.
 __device__ __forceinline__ uint32_t smem_desc_lo(uint32_t addr, uint32_t lbo)
 {
     return ((addr >> 4) & 0x3FFF) | (((lbo >> 4) & 0x3FFF) << 16);
@@ -179,28 +148,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
         : "memory");
-}
-
-// Two loads of 32 lanes x 8 consecutive 32-bit columns each, followed by the
-// wait for their completion, in one statement so that no use of the results can
-// be scheduled before the wait.  This thread gets lane (taddr.lane + laneid),
-// columns taddr.col .. +7 of each address.
-__device__ __forceinline__ void tmem_ld8x2(uint32_t ta0, uint32_t ta1, float (&v0)[8],
-                                           float (&v1)[8])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(ta0), "r"(ta1)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v0[i] = __uint_as_float(r[i]);
-        v1[i] = __uint_as_float(r[8 + i]);
-    }
 }
 
 // Issue two loads of 32 lanes x 8 consecutive 32-bit columns into r[0..7] and
