@@ -238,6 +238,10 @@ fabm_status fabm_set_timing(fabm_solver *s, int period);
  *             terms).  Any output pointer may be NULL. */
 fabm_status fabm_kernel_stats(const fabm_solver *s, int kind, int64_t *launches, double *total_ms,
                               double *flops);
+/* Milliseconds during which the timed launches of one kind ran (the union of
+ * their intervals, so launches that overlap on different streams count once);
+ * equal to fabm_kernel_stats' total_ms when they never overlap. */
+fabm_status fabm_kernel_busy(const fabm_solver *s, int kind, double *busy_ms);
 
 /* ------------------------------------------------------------ serving ---
  * A continuous-batching server for independent solves that differ in right-

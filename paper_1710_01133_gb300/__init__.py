@@ -29,7 +29,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
-            "fabm_create_multi", "fabm_server_finished")
+            "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
+    lib.fabm_kernel_busy.argtypes = [vp, i, P(d)]
+    lib.fabm_kernel_busy.restype = i
     lib.fabm_stroboscope.argtypes = [vp, i64, i64, i, vp, d, d, d, i64, i, vp]
     lib.fabm_stroboscope.restype = i
     for f in ("fabm_create", "fabm_create_multi", "fabm_solve", "fabm_solve_batch",
@@ -254,6 +256,14 @@ def fabm_kernel_stats(handle, kind):
     return n.value, ms.value, fl.value
 
 
+def fabm_kernel_busy(handle, kind):
+    """Milliseconds during which the timed launches of one kind ran (overlaps once)."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ms = ctypes.c_double()
+    _check(load().fabm_kernel_busy(handle, k, ctypes.byref(ms)))
+    return ms.value
+
+
 # ---------------------------------------------------------- convenience ---
 
 class Solver:
@@ -326,8 +336,14 @@ class Solver:
         fabm_set_timing(self.handle, int(period))
 
     def kernel_stats(self) -> dict:
-        return {k: dict(zip(("launches", "ms", "flops"), fabm_kernel_stats(self.handle, k)))
-                for k in KERNEL_KINDS}
+        """Per kernel class: timed launches, their summed durations (ms), the time
+        they ran with overlaps counted once (busy_ms) and their algorithmic flops."""
+        out = {}
+        for k in KERNEL_KINDS:
+            st = dict(zip(("launches", "ms", "flops"), fabm_kernel_stats(self.handle, k)))
+            st["busy_ms"] = fabm_kernel_busy(self.handle, k)
+            out[k] = st
+        return out
 
     def solve(self, y0, y1=None) -> np.ndarray:
         """One trajectory; y1 = y'(0) for 1 < alpha < 2."""

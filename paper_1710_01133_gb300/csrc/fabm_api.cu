@@ -114,8 +114,10 @@ struct fabm_solver {
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
     DevBuf<unsigned long long> status;
-    cudaStream_t sR = nullptr, sG = nullptr;  // recurrence, far history
-    cudaEvent_t evR[kEvRing] = {}, evG[2] = {}, evFork = nullptr;
+    // sR: recurrence; sG, sG2: far history (the CUDA-core history of odd blocks
+    // runs on sG2, so that consecutive blocks' history launches overlap)
+    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr;
+    cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evFork = nullptr, evJoin = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
@@ -138,6 +140,7 @@ struct fabm_solver {
     int64_t k_launches[FABM_KERNEL_KINDS] = {};
     double k_ms[FABM_KERNEL_KINDS] = {};
     double k_flops[FABM_KERNEL_KINDS] = {};
+    double k_busy[FABM_KERNEL_KINDS] = {};  // union of the timed launches' intervals
 
     ~fabm_solver()
     {
@@ -151,10 +154,12 @@ struct fabm_solver {
         for (auto &e : evG)
             if (e) cudaEventDestroy(e);
         if (evFork) cudaEventDestroy(evFork);
+        if (evJoin) cudaEventDestroy(evJoin);
         if (gexec) cudaGraphExecDestroy(gexec);
         for (auto &e : ev_pool) cudaEventDestroy(e);
         if (sR) cudaStreamDestroy(sR);
         if (sG) cudaStreamDestroy(sG);
+        if (sG2) cudaStreamDestroy(sG2);
     }
 };
 
@@ -230,13 +235,33 @@ cudaError_t timed_launch(fabm_solver *s, int kind, cudaStream_t st, double flops
 // After the streams are idle: add up the event pairs of the given records.
 cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &recs)
 {
+    // per launch: duration, and start relative to the first timed launch, so
+    // that the time during which launches of a kind ran (overlapping launches
+    // counted once) can be formed as well
+    std::vector<std::pair<double, double>> iv[FABM_KERNEL_KINDS];
     for (size_t i = 0; i < recs.size(); ++i) {
-        float ms = 0.f;
+        float ms = 0.f, t0 = 0.f;
         cudaError_t e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
+        if (e == cudaSuccess && i > 0) e = cudaEventElapsedTime(&t0, s->ev_pool[0], s->ev_pool[2 * i]);
         if (e != cudaSuccess) return e;
         s->k_ms[recs[i].kind] += ms;
         s->k_launches[recs[i].kind] += 1;
         s->k_flops[recs[i].kind] += recs[i].flops;
+        iv[recs[i].kind].push_back({(double)t0, (double)t0 + ms});
+    }
+    for (int k = 0; k < FABM_KERNEL_KINDS; ++k) {
+        std::sort(iv[k].begin(), iv[k].end());
+        double busy = 0.0, lo = 0.0, hi = -1.0;
+        for (const auto &p : iv[k]) {
+            if (p.first > hi) {
+                if (hi > lo) busy += hi - lo;
+                lo = p.first, hi = p.second;
+            } else {
+                hi = std::max(hi, p.second);
+            }
+        }
+        if (hi > lo) busy += hi - lo;
+        s->k_busy[k] += busy;
     }
     return cudaSuccess;
 }
@@ -257,63 +282,92 @@ int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 // graph being captured): init, then per block the far history on stream G and
 // the recurrence (and, split path, the slicing of the finished segment) on
 // stream R.
+// Lag of the history launches: the history of block c covers the points
+// k < (c - lag) L and the recurrence sums the lag blocks before c.  With lag 2
+// (CUDA-core history kernels, long histories) the history of block c waits
+// only for the recurrence of block c-3, and the launches of consecutive blocks,
+// on two streams, overlap each other's tails and reductions; the tensor kernel
+// uses lag 1 (a 64-point segment is sliced once its block is done).
+// Lag 2 pays where the history bounds the solve: N x cols at least 2^19 for
+// the FP64 kernel (its per-block work then exceeds the recurrence's ~30 us),
+// 2^25 for the compensated-fp32 kernel (64x the FP64 rate).  Below that the
+// extra lag block only lengthens the recurrence.
+int history_lag(int hk, int64_t N, int64_t cols)
+{
+    if (hk == FABM_HIST_FP64) return N * cols >= (1LL << 19) ? 2 : 1;
+    if (hk == FABM_HIST_FP32C) return N * cols >= (1LL << 25) ? 2 : 1;
+    return 1;
+}
+
+// Enqueues one solve on the solver's streams (or records it into the graph
+// being captured): init, then per block the far history on sG / sG2 and the
+// recurrence (and, tensor path, the slicing of the finished segment) on sR.
 fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &w, int64_t nblk,
                           int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks, int hk)
 {
     const int L = s->L;
     const int64_t cols = bt.cols;
     const bool split = hk == FABM_HIST_TENSOR;
+    const int lag = history_lag(hk, Nmax, cols);
+    const int n_gbuf = lag + 1;  // G of block c is read by R(c) until H(c + lag + 1) starts
     s->sample_now = true;
     FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
                                [&] { return launch_init(s->rhs, bt, s->sR); }));
     for (int64_t c = 0; c < nblk; ++c) {
-        s->sample_now = (c % s->timing_period) == 0;
+        // timed blocks; with two history streams, runs of 8 consecutive blocks,
+        // so that the overlap of their history launches is measured
+        const int64_t ph = c % s->timing_period;
+        s->sample_now = ph == 0 || (lag == 2 && ph < 8);
         const double *Gc = nullptr;
-        if (c >= 2) {
-            double *Gbuf = s->G.p + (size_t)(c % 2) * 2 * L * cols;
+        const int64_t k_end = (c - lag) * L;
+        if (k_end > 0) {
+            double *Gbuf = s->G.p + (size_t)(c % n_gbuf) * 2 * L * cols;
+            const bool two = lag == 2;  // alternate history streams
+            cudaStream_t gs = (two && (c & 1)) ? s->sG2 : s->sG;
+            const size_t poff = two ? (size_t)(c & 1) * max_chunks * 2 * L * cols : 0;
             int n_chunks;
             int64_t kc;
-            const int64_t k_end = (c - 1) * L;
             // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
             const double flops = 4.0 * L * (double)k_end * (double)cols;
-            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(gs, s->evR[(c - lag - 1) % kEvRing], 0));
             if (split) {
                 n_chunks = (int)std::min<int64_t>(c - 1, split_chunks);
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
                     return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, n_ct,
-                                             (int)cols, n_chunks, s->spart.p, s->err.p, s->sG);
+                                             (int)cols, n_chunks, s->spart.p, s->err.p, gs);
                 }));
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
-                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, gs, 0.0, [&] {
+                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, gs);
                 }));
             } else if (hk == FABM_HIST_FP32C) {
                 plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
-                    return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, w.stride, c, n_chunks, kc,
-                                             s->spart.p, s->sG);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
+                    return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, w.stride, c, lag, n_chunks,
+                                             kc, s->spart.p + poff, gs);
                 }));
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
-                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, s->sG);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, gs, 0.0, [&] {
+                    return launch_combine_split(s->spart.p + poff, n_chunks, (int)cols, L, Gbuf, gs);
                 }));
             } else {
                 plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
-                    return launch_hist_fp64(bt, w, c, L, n_chunks, kc, s->part.p, s->sG);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
+                    return launch_hist_fp64(bt, w, c, L, lag, n_chunks, kc, s->part.p + poff, gs);
                 }));
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
-                    return launch_hist_reduce(s->part.p, n_chunks, L, (int)cols, Gbuf, s->sG);
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, gs, 0.0, [&] {
+                    return launch_hist_reduce(s->part.p + poff, n_chunks, L, (int)cols, Gbuf, gs);
                 }));
             }
-            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 2], s->sG));
-            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 2], 0));
+            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 3], gs));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 3], 0));
             Gc = Gbuf;
         }
-        // lag-1 block and in-block triangle: per target up to 2L points
+        // lag blocks and in-block triangle: per target up to (lag + 1) L points
         const int64_t lo = c * L, hi = std::min<int64_t>((c + 1) * L, Nmax);
         const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
-                              ((c >= 1 ? L : 0) + 0.5 * (double)(hi - lo + 1));
+                              ((double)std::min<int64_t>(c, lag) * L + 0.5 * (double)(hi - lo + 1));
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
-            return launch_recur(s->rhs, bt, w, s->k, c, L, s->precision == FABM_SPLIT, Gc, s->sR);
+            return launch_recur(s->rhs, bt, w, s->k, c, L, lag, s->precision == FABM_SPLIT, Gc,
+                                s->sR);
         }));
         if (split && c + 2 < nblk) {  // segment c is read by the blocks c+2 ..
             FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0, [&] {
@@ -366,9 +420,10 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     int64_t max_chunks = std::max<int64_t>(1, (int64_t)(64ull << 20) / (part_per_chunk * 8));
     max_chunks = std::min<int64_t>(max_chunks, 4096);
     FABM_CUDA_TRY(s->F.ensure(f_elems));
-    FABM_CUDA_TRY(s->G.ensure((size_t)2 * 2 * L * cols));
-    if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)max_chunks * part_per_chunk));
-    if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)max_chunks * part_per_chunk));
+    FABM_CUDA_TRY(s->G.ensure((size_t)3 * 2 * L * cols));
+    // two partial buffers: the history launches of blocks c and c+1 may overlap
+    if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)2 * max_chunks * part_per_chunk));
+    if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)2 * max_chunks * part_per_chunk));
     FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim * 2));  // y0, then y1
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
@@ -445,6 +500,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         if (est != FABM_OK) return est;
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sG2));
         FABM_CUDA_TRY(collect_timing(s, s->recs));
     } else {
         if (!s->gexec || s->gkey != key) {
@@ -456,10 +512,13 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             s->capturing = true;
             cudaError_t e = cudaEventRecord(s->evFork, s->sR);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG, s->evFork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG2, s->evFork, 0);
             fabm_status est = e == cudaSuccess ? enqueue() : FABM_ECUDA;
             if (est == FABM_OK) {
                 e = cudaEventRecord(s->evFork, s->sG);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evFork, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(s->evJoin, s->sG2);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoin, 0);
             }
             cudaError_t e2 = cudaStreamEndCapture(s->sR, &graph);
             s->capturing = false;
@@ -593,11 +652,13 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     // the recurrence is the serial chain: its CTAs are scheduled first
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->sR, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG2, cudaStreamNonBlocking);
     for (auto &ev : s->evR)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto &ev : s->evG)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evFork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
         s->recs.clear();
@@ -851,7 +912,17 @@ fabm_status fabm_set_timing(fabm_solver *s, int enable)
     s->timing_period = enable > 0 ? enable : 1;
     if (s->timing)
         for (int k = 0; k < FABM_KERNEL_KINDS; ++k)
-            if (k != FABM_KERNEL_WEIGHTS) s->k_launches[k] = 0, s->k_ms[k] = 0, s->k_flops[k] = 0;
+            if (k != FABM_KERNEL_WEIGHTS)
+                s->k_launches[k] = 0, s->k_ms[k] = 0, s->k_flops[k] = 0, s->k_busy[k] = 0;
+    return FABM_OK;
+}
+
+fabm_status fabm_kernel_busy(const fabm_solver *s, int kind, double *busy_ms)
+{
+    g_last_error.clear();
+    if (!s || !busy_ms) return fail(FABM_EINVAL, "NULL argument");
+    if (kind < 0 || kind >= FABM_KERNEL_KINDS) return fail(FABM_EINVAL, "kind %d unknown", kind);
+    *busy_ms = s->k_busy[kind];
     return FABM_OK;
 }
 

@@ -73,9 +73,9 @@ cudaError_t launch_weights(double alpha, int64_t N, double inv_g1, double inv_g2
 cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st);
 
 // a2 (FP64): partial far-history sums of target block c from the points
-// k in [0, (c-1)L), split into n_chunks chunks of kc points.
+// k in [0, (c-lag)L), split into n_chunks chunks of kc points.
 // part: n_chunks x 2 x L x cols (P then C).
-cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L,
+cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L, int lag,
                              int n_chunks, int64_t kc, double *part, cudaStream_t st);
 
 // a3: G[pc][a][col] = sum over chunks of part (fixed order).
@@ -83,11 +83,13 @@ cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols
                                cudaStream_t st);
 
 // a4 + a5: steps of block c (L = 32 or 64 targets) for every trajectory; G
-// holds the far history of block c (2 x L x cols) or is NULL when c < 2.
-// split = false: all in double; split = true: FP64 bases and corrector update,
-// short-range sums and f in fp32 (recur_block_split).
+// holds the far history of block c over the points k < (c - lag) L (2 x L x
+// cols) or is NULL when c <= lag; the lag blocks before block c are summed by
+// the recurrence (lag 1 or 2 for L = 32, 1 for L = 64).  split = false: all in
+// double; split = true: FP64 bases and corrector update, short-range sums and
+// f in float-float (recur_block_split).
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
-                         int64_t c, int L, bool split, const double *G, cudaStream_t st);
+                         int64_t c, int L, int lag, bool split, const double *G, cudaStream_t st);
 
 // Message returned by fabm_last_error() on the calling thread.
 void set_last_error(const char *msg);
@@ -125,11 +127,11 @@ cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int
 // y[i] = (float)x[i], i < n.
 cudaError_t launch_to_float(const double *x, int64_t n, float *y, cudaStream_t st);
 
-// Far history of block c (32 targets) over k < (c-1)*32 in compensated fp32;
+// Far history of block c (32 targets) over k < (c-lag)*32 in compensated fp32;
 // partials as float2 (sum, -compensation), n_chunks x 2 x 32 x cols.
 // wstride > 0: one order per component (weights of component i at WBf + i*wstride).
 cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf,
-                              int64_t wstride, int64_t c, int n_chunks, int64_t kc, float2 *part,
-                              cudaStream_t st);
+                              int64_t wstride, int64_t c, int lag, int n_chunks, int64_t kc,
+                              float2 *part, cudaStream_t st);
 
 }  // namespace fabm

@@ -42,11 +42,18 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
         // window index i <-> d = cL+2-t1 + i, i < nk+L-1
         const int64_t d_min = c * kL + 2 - t1;
         const int nwin = nk + kL - 1;
-        for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
-            const int v = i / nwin, ii = i % nwin;
-            const int64_t o = MULTI ? (int64_t)((col0 + v) % dim) * wstride : 0;
-            sB[v][ii] = WB[o + d_min + ii];
-            sA[v][ii] = WA[o + d_min + ii];
+        if constexpr (MULTI) {
+            for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
+                const int v = i / nwin, ii = i % nwin;
+                const int64_t o = (int64_t)((col0 + v) % dim) * wstride;
+                sB[v][ii] = WB[o + d_min + ii];
+                sA[v][ii] = WA[o + d_min + ii];
+            }
+        } else {
+            for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
+                sB[0][i] = WB[d_min + i];
+                sA[0][i] = WA[d_min + i];
+            }
         }
         for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;
@@ -114,11 +121,18 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
         // window index i <-> d = cL+2-t1 + i (see the double kernel)
         const int64_t d_min = c * kL + 2 - t1;
         const int nwin = nk + kL - 1;
-        for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
-            const int v = i / nwin, ii = i % nwin;
-            const int64_t o = MULTI ? (int64_t)((col0 + v) % dim) * wstride : 0;
-            sB[v][ii] = WB[o + d_min + ii];
-            sA[v][ii] = WA[o + d_min + ii];
+        if constexpr (MULTI) {
+            for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
+                const int v = i / nwin, ii = i % nwin;
+                const int64_t o = (int64_t)((col0 + v) % dim) * wstride;
+                sB[v][ii] = WB[o + d_min + ii];
+                sA[v][ii] = WA[o + d_min + ii];
+            }
+        } else {
+            for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
+                sB[0][i] = WB[d_min + i];
+                sA[0][i] = WA[d_min + i];
+            }
         }
         for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;

@@ -47,11 +47,12 @@ cudaError_t launch_to_float(const double *x, int64_t n, float *y, cudaStream_t s
 }
 
 cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float *WAf,
-                              int64_t wstride, int64_t c, int n_chunks, int64_t kc, float2 *part,
-                              cudaStream_t st)
+                              int64_t wstride, int64_t c, int lag, int n_chunks, int64_t kc,
+                              float2 *part, cudaStream_t st)
 {
-    const int64_t k_end = (c - 1) * hist::kL;
-    if (c < 2 || k_end <= 0) return cudaSuccess;
+    const int64_t k_end = (c - lag) * hist::kL;
+    if (lag < 1) return cudaErrorInvalidValue;
+    if (k_end <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
     if (wstride)
         hist_fp32c_kernel<true><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(

@@ -70,12 +70,12 @@ __global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks
 
 }  // namespace
 
-cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L,
+cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c, int L, int lag,
                              int n_chunks, int64_t kc, double *part, cudaStream_t st)
 {
-    const int64_t k_end = (c - 1) * L;
-    if (L != hist::kL) return cudaErrorInvalidValue;
-    if (c < 2 || k_end <= 0) return cudaSuccess;
+    const int64_t k_end = (c - lag) * L;
+    if (L != hist::kL || lag < 1) return cudaErrorInvalidValue;
+    if (k_end <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
     if (w.stride)
         hist_fp64_kernel<true><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(

@@ -11,25 +11,25 @@ __global__ void init_kernel(DevBatch bt)
     if (b < bt.B) init_one<Rhs, D>(bt, b);
 }
 
-template <class Rhs, int D, int TPL, bool SPLIT>
+template <class Rhs, int D, int TPL, bool SPLIT, int LAG>
 __global__ void __launch_bounds__(D *kWarp)
     recur_kernel(DevBatch bt, DevWeights w, StepConsts kc, int64_t c, const double *G)
 {
     if constexpr (SPLIT) {
-        __shared__ __align__(16) float smem_f[recur_split_smem_floats<D, TPL>()];
-        recur_block_split<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem_f);
+        __shared__ __align__(16) float smem_f[recur_split_smem_floats<D, TPL, LAG>()];
+        recur_block_split<Rhs, D, TPL, LAG>(bt, blockIdx.x, w, kc, c, G, smem_f);
     } else {
-        __shared__ double smem[recur_smem_doubles<D, TPL>()];
-        recur_block<Rhs, D, TPL>(bt, blockIdx.x, w, kc, c, G, smem);
+        __shared__ double smem[recur_smem_doubles<D, TPL, LAG>()];
+        recur_block<Rhs, D, TPL, LAG>(bt, blockIdx.x, w, kc, c, G, smem);
     }
 }
 
-template <int TPL, bool SPLIT>
+template <int TPL, bool SPLIT, int LAG>
 bool launch_recur_t(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
                     int64_t c, const double *G, cudaStream_t st)
 {
     return dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
-        recur_kernel<R, D, TPL, SPLIT><<<(unsigned)bt.B, D * kWarp, 0, st>>>(bt, w, k, c, G);
+        recur_kernel<R, D, TPL, SPLIT, LAG><<<(unsigned)bt.B, D * kWarp, 0, st>>>(bt, w, k, c, G);
     });
 }
 
@@ -46,15 +46,18 @@ cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st)
 }
 
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
-                         int64_t c, int L, bool split, const double *G, cudaStream_t st)
+                         int64_t c, int L, int lag, bool split, const double *G, cudaStream_t st)
 {
     bool ok = false;
-    if (L == kWarp)
-        ok = split ? launch_recur_t<1, true>(rhs, bt, w, k, c, G, st)
-                   : launch_recur_t<1, false>(rhs, bt, w, k, c, G, st);
-    else if (L == 2 * kWarp)
-        ok = split ? launch_recur_t<2, true>(rhs, bt, w, k, c, G, st)
-                   : launch_recur_t<2, false>(rhs, bt, w, k, c, G, st);
+    if (L == kWarp && lag == 1)
+        ok = split ? launch_recur_t<1, true, 1>(rhs, bt, w, k, c, G, st)
+                   : launch_recur_t<1, false, 1>(rhs, bt, w, k, c, G, st);
+    else if (L == kWarp && lag == 2)
+        ok = split ? launch_recur_t<1, true, 2>(rhs, bt, w, k, c, G, st)
+                   : launch_recur_t<1, false, 2>(rhs, bt, w, k, c, G, st);
+    else if (L == 2 * kWarp && lag == 1)
+        ok = split ? launch_recur_t<2, true, 1>(rhs, bt, w, k, c, G, st)
+                   : launch_recur_t<2, false, 1>(rhs, bt, w, k, c, G, st);
     return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 

@@ -28,6 +28,18 @@
 namespace fabm {
 
 
+// v[q] for a runtime q < D without indexing the array dynamically (which
+// would copy the kernel's parameter block to local memory).
+template <int D>
+__device__ inline double pick(const double (&v)[FABM_MAX_DIM], int q)
+{
+    double r = v[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k)
+        if (q == k) r = v[k];
+    return r;
+}
+
 __device__ inline void report_nonfinite(unsigned long long *status, int64_t step, int traj)
 {
     atomicMin(status, ((unsigned long long)step << 24) | (unsigned long long)traj);
@@ -60,27 +72,29 @@ __device__ inline void init_one(const DevBatch &bt, int b)
     if (!ok) report_nonfinite(bt.status, 0, b);
 }
 
-// Shared-memory doubles recur_block<*, D, TPL> needs.
-template <int D, int TPL>
+// Shared-memory doubles recur_block<*, D, TPL, LAG> needs.
+template <int D, int TPL, int LAG = 1>
 __host__ __device__ constexpr int recur_smem_doubles()
 {
-    return 2 * (2 * kWarp * TPL + 1) * D + 2 * D + (kWarp * TPL + 1) * D;
+    return 2 * ((LAG + 1) * kWarp * TPL + 1) * D + 2 * D + (LAG * kWarp * TPL + 1) * D;
 }
 
 // One block of steps for trajectory b of the batch, run by a CTA of at least D
-// warps; smem holds recur_smem_doubles<D, TPL>() doubles.
-template <class Rhs, int D, int TPL>
+// warps; smem holds recur_smem_doubles<D, TPL, LAG>() doubles.  The far part G
+// covers the points k < (c - LAG) L; the LAG blocks before block c are summed
+// here.
+template <class Rhs, int D, int TPL, int LAG = 1>
 __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, const StepConsts &kc,
                             int64_t c, const double *G, double *smem)
 {
     constexpr int L = kWarp * TPL;
     // weights pre-multiplied by h^alpha: the accumulators hold y0 + h^alpha * sum,
     // so adding the newest point to the owner's accumulator yields y^P directly
-    constexpr int W = 2 * L + 1;
-    double *sB = smem;                   // [D][2L+1], per component (its own order)
-    double *sA = sB + D * W;             // [D][2L+1]
+    constexpr int W = (LAG + 1) * L + 1;  // distances 0 .. (LAG+1) L
+    double *sB = smem;                   // [D][W], per component (its own order)
+    double *sA = sB + D * W;             // [D][W]
     double(*sy)[D] = reinterpret_cast<double(*)[D]>(sA + D * W);  // [2][D]
-    double(*sF)[D] = sy + 2;             // [L+1][D]: f of the lag-1 block and f_{m0}
+    double(*sF)[D] = sy + 2;             // [LAG L + 1][D]: f of the lag blocks and f_{m0}
     // component of this warp; warps beyond D (a CTA sized for a larger
     // dimension) mirror component 0 and write nothing
     const bool act = threadIdx.x / kWarp < D;
@@ -89,14 +103,16 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     const int64_t Nb = bt.N_each[b];
     const int64_t m0 = c * L;  // f_{m0} is the newest known point
     if (m0 >= Nb) return;      // trajectory finished (uniform over the CTA)
-    for (int j = threadIdx.x; j < D * W; j += blockDim.x) {
+    const int nW = w.stride ? D : 1;  // one weight set per order
+    for (int j = threadIdx.x; j < nW * W; j += blockDim.x) {
         const int q = j / W, jj = j % W;
-        sB[j] = kc.h_alpha[q] * w.B[q * w.stride + jj];
-        sA[j] = kc.h_alpha[q] * w.A[q * w.stride + jj];
+        const double hq = pick<D>(kc.h_alpha, q);
+        sB[j] = hq * w.B[q * w.stride + jj];
+        sA[j] = hq * w.A[q * w.stride + jj];
     }
-    // rows m0-L .. m0 of this trajectory's history, all loads in flight at once
-    for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
-        const int64_t row = m0 - L + j / D;
+    // rows m0-LAG*L .. m0 of this trajectory's history, all loads in flight at once
+    for (int j = threadIdx.x; j < (LAG * L + 1) * D; j += blockDim.x) {
+        const int64_t row = m0 - LAG * L + j / D;
         sF[j / D][j % D] = row >= 0 ? bt.F[row * bt.ldF + (int64_t)b * D + j % D] : 0.0;
     }
     __syncthreads();
@@ -106,10 +122,10 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
     for (int q = 0; q < kMaxParams; ++q) p[q] = bt.params[(int64_t)b * kMaxParams + q];
     const double y0 = bt.y0[(int64_t)b * D + i];
     const int64_t col = (int64_t)b * D + i;
-    const double ha = kc.h_alpha[i];
-    const double ha_ig2 = ha * kc.inv_gamma2[i];
+    const double ha = pick<D>(kc.h_alpha, i);
+    const double ha_ig2 = ha * pick<D>(kc.inv_gamma2, i);
     const double *wD = w.D + i * w.stride;
-    sB += i * W, sA += i * W;  // this warp's component
+    if (w.stride) sB += i * W, sA += i * W;  // this warp's component's order
 
     double accP[TPL], accC[TPL], aux[TPL];
     const double f0 = bt.F[col];
@@ -126,19 +142,19 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
         accP[t] = fma(ha, gP, Tm);
         accC[t] = fma(ha, gC, Tm);
     }
-    if (c >= 1) {  // lag-1 block: k = m0-L+j, d = m-k = L+1+a-j in [2, 2L]
-        for (int j = 0; j < L; ++j) {
+    if (c >= 1) {  // lag blocks: k = m0-LAG*L+j, d = m-k = LAG*L+1+a-j in [2, (LAG+1)L]
+        for (int j = 0; j < LAG * L; ++j) {
             const double fk = sF[j][i];
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
-                const int d = L + 1 + lane + kWarp * t - j;
+                const int d = LAG * L + 1 + lane + kWarp * t - j;
                 accP[t] = fma(sB[d], fk, accP[t]);
                 accC[t] = fma(sA[d], fk, accC[t]);
             }
         }
     }
 
-    double fk = sF[L][i];
+    double fk = sF[LAG * L][i];
     const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
     double *Yb = bt.Y + (int64_t)b * (bt.N + 1) * D;
     for (int s = 0; s < steps; ++s) {
@@ -209,36 +225,39 @@ __device__ void recur_block(const DevBatch &bt, int b, const DevWeights &w, cons
 // and a float-float operation completes in fewer cycles than one FP64
 // operation, so the chain is shorter and wide batches no longer saturate the
 // FP64 pipe.
-template <int D, int TPL>
+template <int D, int TPL, int LAG = 1>
 __host__ __device__ constexpr int recur_split_smem_floats()
 {
-    return 4 * (2 * kWarp * TPL + 1) * D + 4 * D + 2 * (kWarp * TPL + 1) * D;
+    return 4 * ((LAG + 1) * kWarp * TPL + 1) * D + 4 * D + 2 * (LAG * kWarp * TPL + 1) * D;
 }
 
-// smem: recur_split_smem_floats<D, TPL>() floats, 8-byte aligned
-template <class Rhs, int D, int TPL>
+// smem: recur_split_smem_floats<D, TPL, LAG>() floats, 8-byte aligned; LAG as
+// for recur_block
+template <class Rhs, int D, int TPL, int LAG = 1>
 __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w,
                                   const StepConsts &kc, int64_t c, const double *G, float *smem)
 {
     constexpr int L = kWarp * TPL;
-    constexpr int W = 2 * L + 1;
-    FF *sB = reinterpret_cast<FF *>(smem);  // [D][2L+1]  h^alpha_i B_i(d)
-    FF *sA = sB + D * W;                    // [D][2L+1]  h^alpha_i A_i(d)
+    constexpr int W = (LAG + 1) * L + 1;
+    FF *sB = reinterpret_cast<FF *>(smem);  // [D][W]  h^alpha_i B_i(d)
+    FF *sA = sB + D * W;                    // [D][W]  h^alpha_i A_i(d)
     FF(*sy)[D] = reinterpret_cast<FF(*)[D]>(sA + D * W);  // [2][D]
-    FF(*sF)[D] = sy + 2;                    // [L+1][D]: f of the lag-1 block and f_{m0}
+    FF(*sF)[D] = sy + 2;                    // [LAG L + 1][D]: f of the lag blocks and f_{m0}
     const bool act = threadIdx.x / kWarp < D;
     const int i = act ? threadIdx.x / kWarp : 0;
     const int lane = threadIdx.x % kWarp;
     const int64_t Nb = bt.N_each[b];
     const int64_t m0 = c * L;
     if (m0 >= Nb) return;
-    for (int j = threadIdx.x; j < D * W; j += blockDim.x) {
+    const int nW = w.stride ? D : 1;  // one weight set per order
+    for (int j = threadIdx.x; j < nW * W; j += blockDim.x) {
         const int q = j / W, jj = j % W;
-        sB[j] = ff_from_double(kc.h_alpha[q] * w.B[q * w.stride + jj]);
-        sA[j] = ff_from_double(kc.h_alpha[q] * w.A[q * w.stride + jj]);
+        const double hq = pick<D>(kc.h_alpha, q);
+        sB[j] = ff_from_double(hq * w.B[q * w.stride + jj]);
+        sA[j] = ff_from_double(hq * w.A[q * w.stride + jj]);
     }
-    for (int j = threadIdx.x; j < (L + 1) * D; j += blockDim.x) {
-        const int64_t row = m0 - L + j / D;
+    for (int j = threadIdx.x; j < (LAG * L + 1) * D; j += blockDim.x) {
+        const int64_t row = m0 - LAG * L + j / D;
         sF[j / D][j % D] =
             ff_from_double(row >= 0 ? bt.F[row * bt.ldF + (int64_t)b * D + j % D] : 0.0);
     }
@@ -253,11 +272,11 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
     }
     const double y0 = bt.y0[(int64_t)b * D + i];
     const int64_t col = (int64_t)b * D + i;
-    const double ha = kc.h_alpha[i];
-    const FF ha_ig2 = ff_from_double(ha * kc.inv_gamma2[i]);
+    const double ha = pick<D>(kc.h_alpha, i);
+    const FF ha_ig2 = ff_from_double(ha * pick<D>(kc.inv_gamma2, i));
     const double f0 = bt.F[col];
     const double *wD = w.D + i * w.stride;
-    sB += i * W, sA += i * W;  // this warp's component
+    if (w.stride) sB += i * W, sA += i * W;  // this warp's component's order
 
     double baseC[TPL];
     FF bP[TPL], bC[TPL], aux[TPL], nP[TPL], nC[TPL], inc[TPL], fo[TPL];
@@ -275,19 +294,19 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
         bC[t] = ff_from_double(baseC[t]);
         nP[t] = nC[t] = inc[t] = fo[t] = FF(0);
     }
-    if (c >= 1) {  // lag-1 block: k = m0-L+j, d = L+1+a-j in [2, 2L]
-        for (int j = 0; j < L; ++j) {
+    if (c >= 1) {  // lag blocks: k = m0-LAG*L+j, d = LAG*L+1+a-j in [2, (LAG+1)L]
+        for (int j = 0; j < LAG * L; ++j) {
             const FF fk = sF[j][i];
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
-                const int d = L + 1 + lane + kWarp * t - j;
+                const int d = LAG * L + 1 + lane + kWarp * t - j;
                 nP[t] = ff_fma(sB[d], fk, nP[t]);
                 nC[t] = ff_fma(sA[d], fk, nC[t]);
             }
         }
     }
 
-    FF fk = sF[L][i];
+    FF fk = sF[LAG * L][i];
     const int steps = (int)(Nb - m0 < L ? Nb - m0 : L);
     for (int s = 0; s < steps; ++s) {
         // add the newest point k = m0+s to every pending target

@@ -172,11 +172,11 @@ extern "C" fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64
             kc_pts = (kc_pts + 31) / 32 * 32;
             const int n_chunks = (int)((k_end + kc_pts - 1) / kc_pts);
             double *Gbuf = S + kOffG + (c % 2) * 2 * kNaL * dim;
-            NA_TRY(launch_hist_fp64(bt, w, c, kNaL, n_chunks, kc_pts, S + kOffPart, st));
+            NA_TRY(launch_hist_fp64(bt, w, c, kNaL, 1, n_chunks, kc_pts, S + kOffPart, st));
             NA_TRY(launch_hist_reduce(S + kOffPart, n_chunks, kNaL, dim, Gbuf, st));
             Gc = Gbuf;
         }
-        NA_TRY(launch_recur(rhs_id, bt, w, kc, c, kNaL, false, Gc, st));
+        NA_TRY(launch_recur(rhs_id, bt, w, kc, c, kNaL, 1, false, Gc, st));
     }
     NA_TRY(cudaStreamSynchronize(st));
     unsigned long long status = 0;
