@@ -483,8 +483,9 @@ def main():
     if rank == 0:
         units = w.steps_traj() * ws  # replicas: every rank solves its own copy
         clocks = clk.summary()
-        dom = max(("history", "recurrence", "combine", "slice", "init"),
-                  key=lambda k: kstats[k]["busy_ms"] or kstats[k]["ms"])
+        # the kinds that do the method's arithmetic (both are timed on the same
+        # sampled blocks; combine, slice and init only move or convert data)
+        dom = max(("history", "recurrence"), key=lambda k: kstats[k]["busy_ms"] or kstats[k]["ms"])
         line_roof = roofline(dom, kstats[dom], args.precision, clocks, w)
         h2d = w.B * w.dim * 8 + w.B * 8 * 8 + w.B * 8
         d2h = w.B * (w.N + 1) * w.dim * 8 + 8

@@ -215,10 +215,13 @@ int64_t fabm_last_launch_count(const fabm_solver *s);
 enum {
     FABM_KERNEL_WEIGHTS = 0,     /* weight generation (fabm_create)                    */
     FABM_KERNEL_INIT = 1,        /* y_0, f_0                                           */
-    FABM_KERNEL_HISTORY = 2,     /* far-history sums (the O(N^2) part)                 */
+    FABM_KERNEL_HISTORY = 2,     /* history sums (the O(N^2) part): far segments and,  */
+                                 /* tensor path, the newest segment                    */
     FABM_KERNEL_COMBINE = 3,     /* fixed-order combination of history partial sums    */
-    FABM_KERNEL_RECURRENCE = 4,  /* in-block predictor/corrector steps                 */
-    FABM_KERNEL_SLICE = 5,       /* split path: f of a finished block -> bf16 slices   */
+    FABM_KERNEL_RECURRENCE = 4,  /* in-block predictor/corrector steps (tensor path:   */
+                                 /* also the table of the time-only part of f)         */
+    FABM_KERNEL_SLICE = 5,       /* split path conversions: f of a finished block ->   */
+                                 /* bf16 slices; float-float y -> double at the end    */
     FABM_KERNEL_KINDS = 6
 };
 

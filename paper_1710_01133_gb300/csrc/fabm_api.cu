@@ -77,6 +77,7 @@ struct DevBuf {
 
 constexpr int kMaxBlockL = 1024;
 constexpr int kEvRing = 4;
+constexpr int kAuxRing = 4;  // forcing tables computed up to 3 blocks ahead
 
 }  // namespace
 
@@ -97,12 +98,15 @@ struct fabm_solver {
     int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     int L = kRecurL;                   // block length of the last solve
+    int cols_warps = 1;                // warps per CTA of the column recurrence (tensor path)
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
     DevBuf<double> wB, wA, wD;
     // split path: fp32 weights (narrow kernel), Hankel weight tiles per lag and
-    // their exponents (tensor kernel)
+    // their exponents (tensor kernel), float-float h^a B(d), h^a A(d) for
+    // d <= 64 and h^a D(m) (column recurrence)
     DevBuf<float> wBf, wAf;
+    DevBuf<float2> wBff, wAff, wDff;
     DevBuf<__nv_bfloat16> wH;
     DevBuf<int> wHe;
     int64_t g_max = 0;
@@ -111,13 +115,17 @@ struct fabm_solver {
     DevBuf<__nv_bfloat16> Fs;  // split: f slices
     DevBuf<int> Fe;            // split: f exponents
     DevBuf<float2> spart;      // split: float-float partials
+    DevBuf<float2> auxb;       // tensor path: forcing tables of kAuxRing blocks
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
     DevBuf<unsigned long long> status;
     // sR: recurrence; sG, sG2: far history (the CUDA-core history of odd blocks
     // runs on sG2, so that consecutive blocks' history launches overlap)
     cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr;
-    cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evFork = nullptr, evJoin = nullptr;
+    // evN: the newest-segment history launch of the tensor path (on sR); evA:
+    // the forcing tables (tensor path, on sG2)
+    cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evN[3] = {}, evA[kAuxRing] = {};
+    cudaEvent_t evFork = nullptr, evJoin = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
@@ -145,13 +153,17 @@ struct fabm_solver {
     ~fabm_solver()
     {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
-        wBf.release(), wAf.release();
+        wBf.release(), wAf.release(), wBff.release(), wAff.release(), wDff.release();
         F.release(), Ystage.release(), G.release(), part.release();
-        Fs.release(), Fe.release(), spart.release(), err.release();
+        Fs.release(), Fe.release(), spart.release(), auxb.release(), err.release();
         y0.release(), par.release(), nEach.release(), status.release();
         for (auto &e : evR)
             if (e) cudaEventDestroy(e);
         for (auto &e : evG)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : evN)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : evA)
             if (e) cudaEventDestroy(e);
         if (evFork) cudaEventDestroy(evFork);
         if (evJoin) cudaEventDestroy(evJoin);
@@ -301,7 +313,8 @@ int history_lag(int hk, int64_t N, int64_t cols)
 
 // Enqueues one solve on the solver's streams (or records it into the graph
 // being captured): init, then per block the far history on sG / sG2 and the
-// recurrence (and, tensor path, the slicing of the finished segment) on sR.
+// recurrence (and, tensor path, the newest segment's history and the slicing
+// of the finished segment) on sR.
 fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &w, int64_t nblk,
                           int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks, int hk)
 {
@@ -312,15 +325,59 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
     const int n_gbuf = lag + 1;  // G of block c is read by R(c) until H(c + lag + 1) starts
     s->sample_now = true;
     FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
-                               [&] { return launch_init(s->rhs, bt, s->sR); }));
+                               [&] { return launch_init(s->rhs, bt, s->sR, split); }));
+    // tensor path with forcing: the tables of the time-only part of f, on sG2,
+    // up to kAuxRing - 1 blocks ahead of the recurrence
+    const bool tables = split && rhs_has_forcing(s->rhs, bt.dim);
+    auto enqueue_aux = [&](int64_t c) -> fabm_status {
+        float2 *X = s->auxb.p + (size_t)(c % kAuxRing) * kSplitSeg * bt.B;
+        if (c >= kAuxRing) FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG2, s->evR[(c - kAuxRing) % kEvRing], 0));
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sG2, 0.0, [&] {
+            return launch_aux_table(s->rhs, bt, s->h, c, X, s->sG2);
+        }));
+        FABM_CUDA_TRY(cudaEventRecord(s->evA[c % kAuxRing], s->sG2));
+        return FABM_OK;
+    };
+    if (tables)
+        for (int64_t c = 0; c < std::min<int64_t>(nblk, kAuxRing); ++c) {
+            const fabm_status st = enqueue_aux(c);
+            if (st != FABM_OK) return st;
+        }
     for (int64_t c = 0; c < nblk; ++c) {
         // timed blocks; with two history streams, runs of 8 consecutive blocks,
         // so that the overlap of their history launches is measured
         const int64_t ph = c % s->timing_period;
         s->sample_now = ph == 0 || (lag == 2 && ph < 8);
-        const double *Gc = nullptr;
-        const int64_t k_end = (c - lag) * L;
-        if (k_end > 0) {
+        const void *Gc = nullptr;
+        if (split && c >= 1) {
+            // far part (segments 0 .. c-2) on sG beside the recurrence of block
+            // c-1; the newest segment c-1 on sR once it is sliced; the combine
+            // on sG after both
+            float2 *Gbuf = reinterpret_cast<float2 *>(s->G.p) + (size_t)(c % n_gbuf) * 2 * L * cols;
+            const int n_far = (int)std::min<int64_t>(c - 1, split_chunks);
+            if (n_far > 0) {
+                const double flops = 4.0 * L * (double)((c - 1) * L) * (double)cols;
+                FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
+                    return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, 0, (int)(c - 1),
+                                             0, n_far, n_ct, (int)cols, s->spart.p, s->err.p, s->sG);
+                }));
+            }
+            const double nflops = 4.0 * L * (double)L * (double)cols;
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, nflops, [&] {
+                return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, (int)(c - 1), 1,
+                                         n_far, 1, n_ct, (int)cols, s->spart.p, s->err.p, s->sR);
+            }));
+            FABM_CUDA_TRY(cudaEventRecord(s->evN[c % 3], s->sR));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evN[c % 3], 0));
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sG, 0.0, [&] {
+                return launch_combine_split_ff(s->spart.p, n_far + 1, (int)cols, L, Gbuf, s->sG);
+            }));
+            FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 3], s->sG));
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 3], 0));
+            Gc = Gbuf;
+        } else if (!split && (c - lag) * L > 0) {
+            const int64_t k_end = (c - lag) * L;
             double *Gbuf = s->G.p + (size_t)(c % n_gbuf) * 2 * L * cols;
             const bool two = lag == 2;  // alternate history streams
             cudaStream_t gs = (two && (c & 1)) ? s->sG2 : s->sG;
@@ -330,17 +387,8 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
             const double flops = 4.0 * L * (double)k_end * (double)cols;
             FABM_CUDA_TRY(cudaStreamWaitEvent(gs, s->evR[(c - lag - 1) % kEvRing], 0));
-            if (split) {
-                n_chunks = (int)std::min<int64_t>(c - 1, split_chunks);
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
-                    return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, n_ct,
-                                             (int)cols, n_chunks, s->spart.p, s->err.p, gs);
-                }));
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, gs, 0.0, [&] {
-                    return launch_combine_split(s->spart.p, n_chunks, (int)cols, L, Gbuf, gs);
-                }));
-            } else if (hk == FABM_HIST_FP32C) {
-                plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
+            plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
+            if (hk == FABM_HIST_FP32C) {
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
                     return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, w.stride, c, lag, n_chunks,
                                              kc, s->spart.p + poff, gs);
@@ -349,7 +397,6 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                     return launch_combine_split(s->spart.p + poff, n_chunks, (int)cols, L, Gbuf, gs);
                 }));
             } else {
-                plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
                     return launch_hist_fp64(bt, w, c, L, lag, n_chunks, kc, s->part.p + poff, gs);
                 }));
@@ -361,22 +408,39 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 3], 0));
             Gc = Gbuf;
         }
-        // lag blocks and in-block triangle: per target up to (lag + 1) L points
+        // lag blocks (CUDA-core paths) and the in-block triangle: per target up
+        // to (rlag + 1) L points
+        const int rlag = split ? 0 : lag;
         const int64_t lo = c * L, hi = std::min<int64_t>((c + 1) * L, Nmax);
         const double rflops = 4.0 * (double)cols * (double)(hi - lo) *
-                              ((double)std::min<int64_t>(c, lag) * L + 0.5 * (double)(hi - lo + 1));
+                              ((double)std::min<int64_t>(c, rlag) * L + 0.5 * (double)(hi - lo + 1));
+        const float2 *X = nullptr;
+        if (tables) {
+            X = s->auxb.p + (size_t)(c % kAuxRing) * kSplitSeg * bt.B;
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evA[c % kAuxRing], 0));
+        }
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
-            return launch_recur(s->rhs, bt, w, s->k, c, L, lag, s->precision == FABM_SPLIT, Gc,
-                                s->sR);
+            if (split)
+                return launch_recur_cols(s->rhs, bt, s->wBff.p, s->wAff.p, s->wDff.p, s->k, c,
+                                         static_cast<const float2 *>(Gc), X, s->cols_warps, s->sR);
+            return launch_recur(s->rhs, bt, w, s->k, c, L, lag, s->precision == FABM_SPLIT,
+                                static_cast<const double *>(Gc), s->sR);
         }));
-        if (split && c + 2 < nblk) {  // segment c is read by the blocks c+2 ..
+        if (split && c + 1 < nblk) {  // segment c is read by the blocks c+1 ..
             FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0, [&] {
                 return launch_slice_f(bt, n_ct, c, s->Fs.p, s->Fe.p, s->sR);
             }));
         }
         FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
+        if (tables && c + kAuxRing < nblk) {
+            const fabm_status st = enqueue_aux(c + kAuxRing);
+            if (st != FABM_OK) return st;
+        }
     }
     s->sample_now = true;
+    if (split)  // y = Taylor part + the float-float increments, in double
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0,
+                                   [&] { return launch_finish_y(bt, s->h, s->sR); }));
     return FABM_OK;
 }
 
@@ -431,15 +495,24 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int n_ct = (int)((cols + 127) / 128);
     int split_chunks = 1;
     if (split) {
-        // leave SMs for the recurrence CTAs that run beside the tensor kernel
-        // (one tensor CTA fills an SM's register file): about one SM per 12
-        // trajectories, only where the column tiles do not need every SM
+        // leave SMs for the recurrence warps that run beside the tensor kernel
+        // (one tensor CTA fills an SM's register file): one SM per 8 warps of
+        // 32/dim trajectories, only where the column tiles do not need every SM
         int reserve = s->sm_reserve;
-        if (reserve < 0) reserve = n_ct <= 16 ? (int)std::min<int64_t>((B + 11) / 12, 40) : 0;
+        if (reserve < 0) {
+            const int64_t warps = (B + kWarp / dim - 1) / (kWarp / dim);
+            reserve = n_ct <= 16 ? (int)std::clamp<int64_t>((warps + 7) / 8, 4, 40) : 0;
+        }
         split_chunks = std::max(1, (148 - reserve) / n_ct);
+        // recurrence CTAs sized to fill the SMs the tensor CTAs leave free
+        const int free_sms = std::max(4, 152 - n_ct * split_chunks);
+        s->cols_warps = std::clamp((recur_cols_warps(dim, B) + free_sms - 1) / free_sms, 1, 12);
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
-        FABM_CUDA_TRY(s->spart.ensure(split_part_elems(split_chunks, (int)cols)));
+        // far chunks and one chunk for the newest segment
+        FABM_CUDA_TRY(s->spart.ensure(split_part_elems(split_chunks + 1, (int)cols)));
+        if (rhs_has_forcing(s->rhs, dim))
+            FABM_CUDA_TRY(s->auxb.ensure((size_t)kAuxRing * kSplitSeg * B));
         FABM_CUDA_TRY(s->err.ensure(1));
         FABM_CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(unsigned int), s->sR));
     }
@@ -487,15 +560,19 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const std::vector<uintptr_t> key = {
         (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
         (uintptr_t)s->timing_period, (uintptr_t)hk, (uintptr_t)s->chunk_ctas,
-        (uintptr_t)(s->sm_reserve + 1), (uintptr_t)Y,
+        (uintptr_t)(s->sm_reserve + 1), (uintptr_t)s->cols_warps, (uintptr_t)Y,
         (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
-        (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p};
+        (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p};
     auto enqueue = [&]() -> fabm_status {
         return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk);
     };
     if (!s->use_graphs) {
         s->recs.clear();
+        // the side streams start after this solve's inputs are on the device
+        FABM_CUDA_TRY(cudaEventRecord(s->evFork, s->sR));
+        FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evFork, 0));
+        FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG2, s->evFork, 0));
         fabm_status est = enqueue();
         if (est != FABM_OK) return est;
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
@@ -657,6 +734,10 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto &ev : s->evG)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (auto &ev : s->evN)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (auto &ev : s->evA)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evFork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin, cudaEventDisableTiming);
     if (e == cudaSuccess) {
@@ -681,11 +762,21 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
         if (e == cudaSuccess) e = launch_to_float(s->wA.p, (int64_t)wlen, s->wAf.p, s->sR);
         if (e == cudaSuccess) e = prepare_hist_split();
         s->g_max = multi ? 0 : (N + kSplitSeg - 1) / kSplitSeg - 1;  // no tensor tiles when multi
-        if (e == cudaSuccess && s->g_max >= 2) {
+        if (e == cudaSuccess && s->g_max >= 1) {
             e = s->wH.ensure((size_t)(s->g_max + 1) * 2 * 3 * 15 * 64);
             if (e == cudaSuccess) e = s->wHe.ensure((size_t)(s->g_max + 1) * 2);
             if (e == cudaSuccess)
                 e = launch_hankel_weights(s->wB.p, s->wA.p, s->g_max, s->wH.p, s->wHe.p, s->sR);
+        }
+        if (e == cudaSuccess && !multi) {
+            const double ha = s->k.h_alpha[0];
+            e = prepare_recur_cols(rhs_id, dim);
+            if (e == cudaSuccess) e = s->wBff.ensure(kSplitSeg + 1);
+            if (e == cudaSuccess) e = s->wAff.ensure(kSplitSeg + 1);
+            if (e == cudaSuccess) e = s->wDff.ensure((size_t)s->w_ext + 1);
+            if (e == cudaSuccess) e = launch_ff_weights(s->wB.p, ha, kSplitSeg + 1, s->wBff.p, s->sR);
+            if (e == cudaSuccess) e = launch_ff_weights(s->wA.p, ha, kSplitSeg + 1, s->wAff.p, s->sR);
+            if (e == cudaSuccess) e = launch_ff_weights(s->wD.p, ha, s->w_ext + 1, s->wDff.p, s->sR);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->sR);

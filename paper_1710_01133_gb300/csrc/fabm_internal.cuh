@@ -14,7 +14,9 @@
 // Time is cut into blocks of L targets: block c holds m = cL+1 .. cL+L.  The
 // history kernels sum the "far" part (k < (c-1)L) of every block while the
 // recurrence kernel of the previous block runs; the recurrence adds the lag-1
-// block and the block's own triangle, step by step.
+// block and the block's own triangle, step by step.  On the tensor-history
+// path (L = 64) a second, one-segment history launch adds the lag-1 block once
+// the previous block is done, and the recurrence adds only its own triangle.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -51,7 +53,9 @@ struct DevBatch {
     const double *y0;      // B x dim
     const double *y1;      // B x dim, y'(0) for 1 < alpha < 2, or NULL (Taylor part y0)
     const double *params;  // B x kMaxParams
-    double *F;             // history f_k, (N+1) x ldF, row k = time k
+    double *F;             // history f_k, (N+1) x ldF, row k = time k; on the
+                           // tensor-history path each slot holds a float-float
+                           // pair (float2) instead of a double
     int64_t ldF;           // row stride of F (>= cols)
     double *Y;             // output, B x (N+1) x dim (trajectory-major)
     unsigned long long *status;  // [0] = first non-finite (step << 24 | traj), ~0 if none
@@ -69,8 +73,9 @@ struct StepConsts {
 cudaError_t launch_weights(double alpha, int64_t N, double inv_g1, double inv_g2, double *B,
                            double *A, double *D, cudaStream_t st);
 
-// y_0 into Y, f_0 = f(0, y_0) into F row 0.
-cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st);
+// y_0 into Y, f_0 = f(0, y_0) into F row 0 (as a float-float pair when
+// f_pairs, the tensor-history path).
+cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st, bool f_pairs = false);
 
 // a2 (FP64): partial far-history sums of target block c from the points
 // k in [0, (c-lag)L), split into n_chunks chunks of kc points.
@@ -82,12 +87,11 @@ cudaError_t launch_hist_fp64(const DevBatch &bt, const DevWeights &w, int64_t c,
 cudaError_t launch_hist_reduce(const double *part, int n_chunks, int L, int cols, double *G,
                                cudaStream_t st);
 
-// a4 + a5: steps of block c (L = 32 or 64 targets) for every trajectory; G
-// holds the far history of block c over the points k < (c - lag) L (2 x L x
-// cols) or is NULL when c <= lag; the lag blocks before block c are summed by
-// the recurrence (lag 1 or 2 for L = 32, 1 for L = 64).  split = false: all in
-// double; split = true: FP64 bases and corrector update, short-range sums and
-// f in float-float (recur_block_split).
+// a4 + a5: steps of block c (L = 32 targets) for every trajectory; G holds the
+// far history of block c over the points k < (c - lag) L (2 x L x cols) or is
+// NULL when c <= lag; the lag blocks (lag 1 or 2) before block c are summed by
+// the recurrence.  split = false: all in double; split = true: FP64 bases and
+// corrector update, short-range sums and f in float-float (recur_block_split).
 cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const StepConsts &k,
                          int64_t c, int L, int lag, bool split, const double *G, cudaStream_t st);
 
@@ -100,7 +104,7 @@ void set_last_error(const char *msg);
 cudaError_t launch_slice_f(const DevBatch &bt, int n_ct, int64_t seg, __nv_bfloat16 *Fs, int *Ef,
                            cudaStream_t st);
 
-// Hankel weight tiles and exponents for the lags 2..g_max.
+// Hankel weight tiles and exponents for the lags 1..g_max.
 cudaError_t launch_hankel_weights(const double *WB, const double *WA, int64_t g_max,
                                   __nv_bfloat16 *WH, int *Ew, cudaStream_t st);
 
@@ -111,16 +115,50 @@ cudaError_t prepare_hist_split();
 // float2 elements of the partial-sum buffer for n_chunks chunks.
 size_t split_part_elems(int n_chunks, int cols);
 
-// Far history of block c over segments 0..c-2 on tensor cores; n_chunks
-// chunks of segments (1 <= n_chunks <= c-1) per column tile of 128.
+// History of block c over the segments seg0 .. seg0+n_seg-1 (all before block
+// c) on tensor cores: n_chunks chunks of segments (1 <= n_chunks <= n_seg) per
+// column tile of 128, written to the partial chunks chunk0 .. chunk0+n_chunks-1.
+// The far part of block c is seg0 = 0, n_seg = c-1; the newest segment is
+// seg0 = c-1, n_seg = 1.
 cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
-                              const int *Ew, int64_t c, int n_ct, int cols, int n_chunks,
-                              float2 *part, unsigned int *err, cudaStream_t st);
+                              const int *Ew, int64_t c, int seg0, int n_seg, int chunk0,
+                              int n_chunks, int n_ct, int cols, float2 *part, unsigned int *err,
+                              cudaStream_t st);
 
-// G[kind][t][col] (double) = sum of the float-float partials over chunks, for
-// blocks of L targets.
+// G[kind][t][col] = sum of the float-float partials over chunks, for blocks
+// of L targets: rounded to double, or (_ff) kept as float-float pairs.
 cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
                                  cudaStream_t st);
+cudaError_t launch_combine_split_ff(const float2 *part, int n_chunks, int cols, int L,
+                                    float2 *G, cudaStream_t st);
+
+// out[i] = scale * W[i] as a float-float pair, i < n.
+cudaError_t launch_ff_weights(const double *W, double scale, int64_t n, float2 *out,
+                              cudaStream_t st);
+
+// a4 + a5 on the tensor-history path, one lane per column (recurrence_cols.cu):
+// the 64 steps of block c given G, the history of every point k < 64c as
+// float-float pairs [2][64][cols] (NULL for c = 0).  WB, WA: h^a B(d), h^a A(d)
+// for d = 0..64; WD: h^a D(m), m = 0..N; all float-float pairs, one order.
+// warps_per_cta (1..12) warps of 32/dim trajectories per CTA.  X: the table
+// of the time-only part of f for block c (launch_aux_table), required when
+// rhs_has_forcing(rhs), else ignored.  y's slots receive float-float
+// increments; launch_finish_y turns them into y after the last block.
+cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, const float2 *WA,
+                              const float2 *WD, const StepConsts &k, int64_t c, const float2 *G,
+                              const float2 *X, int warps_per_cta, cudaStream_t st);
+// The right-hand side has a time-dependent part (forcing).
+bool rhs_has_forcing(int rhs, int dim);
+// X[a][b] = aux(t_{64c+1+a}, params of b) as float-float pairs, a < 64, b < B.
+cudaError_t launch_aux_table(int rhs, const DevBatch &bt, double h, int64_t c, float2 *X,
+                             cudaStream_t st);
+// y = T + increment in double for rows 1 .. N_each of every trajectory.
+cudaError_t launch_finish_y(const DevBatch &bt, double h, cudaStream_t st);
+// Kernel attributes (dynamic shared memory) of the column recurrence for one
+// right-hand side; call before the first launch, outside any graph capture.
+cudaError_t prepare_recur_cols(int rhs, int dim);
+// Warps the column recurrence needs for B trajectories of dimension dim.
+int recur_cols_warps(int dim, int64_t B);
 
 // ---- split path for narrow batches (compensated fp32 on CUDA cores) ----
 

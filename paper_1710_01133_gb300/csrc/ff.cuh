@@ -70,6 +70,26 @@ __device__ inline FF ff_fma(FF w, FF f, FF acc)
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
 }
 
+// acc += w*f for sums of many products (Ogita, Rump and Oishi's Dot2): acc.hi
+// is the running sum, acc.lo collects the rounding errors of the additions
+// and the low-order parts of the products; only one addition per term sits on
+// the loop-carried chain.  The sum is accurate to about (n 2^-24)^2 of the sum
+// of |terms| for n terms; ff_norm turns acc into a normalised value.
+__device__ inline void dot2_acc(FF &acc, FF w, FF f)
+{
+    const float p = __fmul_rn(w.hi, f.hi);
+    float e = __fmaf_rn(w.hi, f.hi, -p);
+    e = __fmaf_rn(w.hi, f.lo, e);
+    e = __fmaf_rn(w.lo, f.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float z = __fsub_rn(s, acc.hi);
+    const float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, z)), __fsub_rn(p, z));
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+    acc.hi = s;
+}
+
+__device__ inline FF ff_norm(FF a) { return two_sum(a.hi, a.lo); }
+
 __device__ inline bool operator<=(FF x, FF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo); }
 __device__ inline bool operator>=(FF x, FF y) { return y <= x; }
 

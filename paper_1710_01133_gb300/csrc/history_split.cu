@@ -48,6 +48,8 @@
 // own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "fabm_internal.cuh"
 #include "sm100_ptx.cuh"
 
@@ -80,9 +82,10 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((exp_clamp
 
 // f of segment `seg` (points seg*64 .. seg*64+63) -> three bf16 slices in the
 // operand layout [seg][ct][slice][k1 = j'/8][col 128][j'%8], j' = 63 - j, and
-// the exponent E per column in Ef[seg][ct][col].  grid = cols_pad/32, block =
-// 256 = 32 columns x 8 groups of 8 points.
-__global__ void __launch_bounds__(256) slice_f_kernel(const double *__restrict__ F, int64_t ldF,
+// the exponent E per column in Ef[seg][ct][col].  On this path the recurrence
+// stores f as float-float pairs (hi, lo).  grid = cols_pad/32, block = 256 =
+// 32 columns x 8 groups of 8 points.
+__global__ void __launch_bounds__(256) slice_f_kernel(const float2 *__restrict__ F, int64_t ldF,
                                                       int64_t n_rows, int cols, int n_ct,
                                                       int64_t seg,
                                                       __nv_bfloat16 *__restrict__ Fs,
@@ -97,9 +100,9 @@ __global__ void __launch_bounds__(256) slice_f_kernel(const double *__restrict__
     for (int k0 = 0; k0 < 8; ++k0) {
         const int j = 63 - (8 * k1 + k0);
         const int64_t row = seg * kSeg + j;
-        double f = (col < cols && row < n_rows) ? F[row * ldF + col] : 0.0;
-        hi[k0] = (float)f;
-        lo[k0] = (float)(f - (double)hi[k0]);
+        const float2 f = (col < cols && row < n_rows) ? F[row * ldF + col] : make_float2(0.f, 0.f);
+        hi[k0] = f.x;
+        lo[k0] = f.y;
         m = fmaxf(m, fabsf(hi[k0]));
     }
     smax[k1][cl] = m;
@@ -142,9 +145,10 @@ __global__ void __launch_bounds__(256) slice_f_kernel(const double *__restrict__
 
 // ------------------------------------------------- Hankel weight tiles ---
 
-// For every lag g in [2, g_max]: D0 = 64 g - 62, exponent E_w = ilogb of the
-// tile's largest weight + 1 per kind, and the Hankel core matrices of the three slices of W(D0 + t),
-// t = 8h + r0 + c0.  WH[g][kind][slice][h][r0][c0]; Ew[g][kind].
+// For every lag g in [1, g_max]: D0 = 64 g - 62, exponent E_w = ilogb of the
+// tile's largest weight + 1 per kind, and the Hankel core matrices of the three
+// slices of W(D0 + t), t = 8h + r0 + c0.  WH[g][kind][slice][h][r0][c0];
+// Ew[g][kind].  Lag 1 (distances 2..128) serves the newest segment.
 // One thread per (g, kind, h, r0) row.
 __global__ void hankel_weights_kernel(const double *__restrict__ WB, const double *__restrict__ WA,
                                       int64_t g_max, __nv_bfloat16 *__restrict__ WH,
@@ -155,7 +159,7 @@ __global__ void hankel_weights_kernel(const double *__restrict__ WB, const doubl
          r += (int64_t)gridDim.x * blockDim.x) {
         const int r0 = (int)(r % 8), h = (int)((r / 8) % kHk), kind = (int)((r / (8 * kHk)) % 2);
         const int64_t g = r / (8 * kHk * 2);
-        if (g < 2) continue;
+        if (g < 1) continue;
         const double *W = kind ? WA : WB;
         const int64_t D0 = 64 * g - 62;
         // the tile spans the distances D0 .. D0+126; the weights are monotone in
@@ -201,7 +205,9 @@ struct SplitArgs {
     int64_t c;                // target block: m = 64c+1 .. 64c+64
     int n_ct;
     int cols;
-    int n_seg;                // segments 0 .. n_seg-1 (= c-1)
+    int seg0;                 // segments seg0 .. seg0+n_seg-1
+    int n_seg;
+    int chunk0;               // CTA row y writes partial chunk chunk0 + y
     int n_chunks;             // gridDim.y
     float2 *part;             // [chunk][2][64][cols] (sum, -compensation)
     unsigned int *err;
@@ -222,8 +228,8 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ct = blockIdx.x, ch = blockIdx.y;
-    const int s_lo = (int)((int64_t)ch * a.n_seg / a.n_chunks);
-    const int s_hi = (int)((int64_t)(ch + 1) * a.n_seg / a.n_chunks);
+    const int s_lo = a.seg0 + (int)((int64_t)ch * a.n_seg / a.n_chunks);
+    const int s_hi = a.seg0 + (int)((int64_t)(ch + 1) * a.n_seg / a.n_chunks);
     const int nseg = s_hi - s_lo;
 
     if (threadIdx.x == 0) {
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
             }
         }
         if (ok && col < a.cols) {
-            float2 *out = a.part + ((int64_t)(ch * 2 + kind) * kSeg) * a.cols + col;
+            float2 *out = a.part + ((int64_t)((a.chunk0 + ch) * 2 + kind) * kSeg) * a.cols + col;
 #pragma unroll
             for (int t = 0; t < kEpiT; ++t) {
                 const uint32_t cw = cmp2[t / 2];
@@ -474,11 +480,12 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float x, float y)
 
 // a3: G[kind][t][col] = sum over chunks of (hi + lo), in float-float; R lanes
 // share one output, each summing chunks r, r+R, ... in ascending order, then a
-// fixed xor tree; rounded once to double.  Every thread runs the same number of
+// fixed xor tree; rounded once to double (Out = double) or kept as the
+// float-float pair (Out = float2).  Every thread runs the same number of
 // rounds, so the shuffles always see full warps.
-template <int R>
+template <int R, class Out>
 __global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chunks, int64_t n_out,
-                                     double *__restrict__ G)
+                                     Out *__restrict__ G)
 {
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int r = (int)(gtid % R);
@@ -509,7 +516,12 @@ __global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chun
             const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
             ff_add(hi, lo, ohi, olo);
         }
-        if (r == 0 && o < n_out) G[o] = (double)hi + (double)lo;
+        if (r == 0 && o < n_out) {
+            if constexpr (std::is_same_v<Out, double>)
+                G[o] = (double)hi + (double)lo;
+            else
+                G[o] = make_float2(hi, lo);  // normalised by ff_add
+        }
     }
 }
 
@@ -519,7 +531,8 @@ cudaError_t launch_slice_f(const DevBatch &bt, int n_ct, int64_t seg, __nv_bfloa
                            cudaStream_t st)
 {
     const unsigned blocks = (unsigned)(n_ct * kMC / 32);
-    slice_f_kernel<<<blocks, 256, 0, st>>>(bt.F, bt.ldF, bt.N + 1, bt.cols, n_ct, seg, Fs, Ef);
+    slice_f_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float2 *>(bt.F), bt.ldF,
+                                           bt.N + 1, bt.cols, n_ct, seg, Fs, Ef);
     return cudaGetLastError();
 }
 
@@ -546,19 +559,22 @@ cudaError_t prepare_hist_split()
 size_t split_part_elems(int n_chunks, int cols) { return (size_t)n_chunks * 2 * kSeg * cols; }
 
 cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
-                              const int *Ew, int64_t c, int n_ct, int cols, int n_chunks,
-                              float2 *part, unsigned int *err, cudaStream_t st)
+                              const int *Ew, int64_t c, int seg0, int n_seg, int chunk0,
+                              int n_chunks, int n_ct, int cols, float2 *part, unsigned int *err,
+                              cudaStream_t st)
 {
-    const int n_seg = (int)(c - 1);
-    if (c < 2 || n_seg < 1) return cudaSuccess;
-    if (n_chunks < 1 || n_chunks > n_seg) return cudaErrorInvalidValue;
-    SplitArgs a{Fs, Ef, WH, Ew, c, n_ct, cols, n_seg, n_chunks, part, err};
+    if (n_seg < 1) return cudaSuccess;
+    // segments lie before block c: lag g = c - seg >= 1
+    if (seg0 < 0 || seg0 + n_seg > c || n_chunks < 1 || n_chunks > n_seg || chunk0 < 0)
+        return cudaErrorInvalidValue;
+    SplitArgs a{Fs, Ef, WH, Ew, c, n_ct, cols, seg0, n_seg, chunk0, n_chunks, part, err};
     hist_split_kernel<<<dim3((unsigned)n_ct, (unsigned)n_chunks), kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
-                                 cudaStream_t st)
+template <class Out>
+cudaError_t launch_combine_t(const float2 *part, int n_chunks, int cols, int L, Out *G,
+                             cudaStream_t st)
 {
     const int64_t n_out = 2LL * L * cols;
     const int threads = 128;
@@ -567,11 +583,46 @@ cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int
         return (unsigned)(b > 152 * 16 ? 152 * 16 : b);
     };
     if (n_chunks >= 256)
-        combine_split_kernel<32><<<blocks_for(32), threads, 0, st>>>(part, n_chunks, n_out, G);
+        combine_split_kernel<32, Out><<<blocks_for(32), threads, 0, st>>>(part, n_chunks, n_out, G);
     else if (n_chunks >= 32)
-        combine_split_kernel<8><<<blocks_for(8), threads, 0, st>>>(part, n_chunks, n_out, G);
+        combine_split_kernel<8, Out><<<blocks_for(8), threads, 0, st>>>(part, n_chunks, n_out, G);
     else
-        combine_split_kernel<1><<<blocks_for(1), threads, 0, st>>>(part, n_chunks, n_out, G);
+        combine_split_kernel<1, Out><<<blocks_for(1), threads, 0, st>>>(part, n_chunks, n_out, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
+                                 cudaStream_t st)
+{
+    return launch_combine_t(part, n_chunks, cols, L, G, st);
+}
+
+cudaError_t launch_combine_split_ff(const float2 *part, int n_chunks, int cols, int L,
+                                    float2 *G, cudaStream_t st)
+{
+    return launch_combine_t(part, n_chunks, cols, L, G, st);
+}
+
+namespace {
+__global__ void ff_weights_kernel(const double *__restrict__ W, double scale, int64_t n,
+                                  float2 *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = scale * W[i];
+        const float hi = __double2float_rn(v);
+        out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+}  // namespace
+
+cudaError_t launch_ff_weights(const double *W, double scale, int64_t n, float2 *out,
+                              cudaStream_t st)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) return cudaSuccess;
+    ff_weights_kernel<<<(unsigned)blocks, 256, 0, st>>>(W, scale, n, out);
     return cudaGetLastError();
 }
 

@@ -5,10 +5,10 @@ namespace fabm {
 namespace {
 
 template <class Rhs, int D>
-__global__ void init_kernel(DevBatch bt)
+__global__ void init_kernel(DevBatch bt, bool f_pairs)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < bt.B) init_one<Rhs, D>(bt, b);
+    if (b < bt.B) init_one<Rhs, D>(bt, b, f_pairs);
 }
 
 template <class Rhs, int D, int TPL, bool SPLIT, int LAG>
@@ -35,12 +35,12 @@ bool launch_recur_t(int rhs, const DevBatch &bt, const DevWeights &w, const Step
 
 }  // namespace
 
-cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st)
+cudaError_t launch_init(int rhs, const DevBatch &bt, cudaStream_t st, bool f_pairs)
 {
     const int threads = 128;
     const unsigned blocks = (unsigned)((bt.B + threads - 1) / threads);
     bool ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
-        init_kernel<R, D><<<blocks, threads, 0, st>>>(bt);
+        init_kernel<R, D><<<blocks, threads, 0, st>>>(bt, f_pairs);
     });
     return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
@@ -55,9 +55,6 @@ cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const
     else if (L == kWarp && lag == 2)
         ok = split ? launch_recur_t<1, true, 2>(rhs, bt, w, k, c, G, st)
                    : launch_recur_t<1, false, 2>(rhs, bt, w, k, c, G, st);
-    else if (L == 2 * kWarp && lag == 1)
-        ok = split ? launch_recur_t<2, true, 1>(rhs, bt, w, k, c, G, st)
-                   : launch_recur_t<2, false, 1>(rhs, bt, w, k, c, G, st);
     return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 

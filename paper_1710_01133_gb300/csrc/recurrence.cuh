@@ -51,9 +51,9 @@ __device__ inline bool finite_bits(double x)
     return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
 }
 
-// y_0 and f_0 = f(0, y_0) of trajectory b.
+// y_0 and f_0 = f(0, y_0) of trajectory b; f_pairs: F holds float-float pairs.
 template <class Rhs, int D>
-__device__ inline void init_one(const DevBatch &bt, int b)
+__device__ inline void init_one(const DevBatch &bt, int b, bool f_pairs = false)
 {
     double y[D], p[kMaxParams];
 #pragma unroll
@@ -66,7 +66,13 @@ __device__ inline void init_one(const DevBatch &bt, int b)
     for (int i = 0; i < D; ++i) {
         const double f = Rhs::template one<D>(i, y, p, aux);
         bt.Y[(int64_t)b * (bt.N + 1) * D + i] = y[i];
-        bt.F[(int64_t)b * D + i] = f;
+        if (f_pairs) {
+            const float hi = __double2float_rn(f);
+            reinterpret_cast<float2 *>(bt.F)[(int64_t)b * D + i] =
+                make_float2(hi, __double2float_rn(f - (double)hi));
+        } else {
+            bt.F[(int64_t)b * D + i] = f;
+        }
         ok = ok && finite_bits(y[i]) && finite_bits(f);
     }
     if (!ok) report_nonfinite(bt.status, 0, b);

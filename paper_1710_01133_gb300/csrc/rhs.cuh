@@ -14,23 +14,28 @@ namespace fabm {
 //   aux(t, p)            the part of f that depends on t only (a forcing term,
 //                        or 0); evaluated once per grid point, off the serial
 //                        chain of the recurrence
+//   kForcing             aux depends on t (the tensor path tabulates it ahead
+//                        of the recurrence instead of evaluating it inline)
 //   one<D>(i, y, p, aux) component i of f(t, y) given aux = aux(t, p)
 // Component-wise evaluation lets the recurrence run the components of one
 // trajectory on different warps.
 
 struct RhsConst {  // f_i = p0
+    static constexpr bool kForcing = false;
     __device__ static double aux(double, const double *p) { return p[0]; }
     template <int D, class T>
     __device__ static T one(int, const T *, const T *, T aux) { return aux; }
 };
 
 struct RhsTime {  // f_i = t
+    static constexpr bool kForcing = true;
     __device__ static double aux(double t, const double *) { return t; }
     template <int D, class T>
     __device__ static T one(int, const T *, const T *, T aux) { return aux; }
 };
 
 struct RhsLinear {  // f_i = -p0 y_i
+    static constexpr bool kForcing = false;
     __device__ static double aux(double, const double *) { return 0.0; }
     template <int D, class T>
     __device__ static T one(int i, const T *y, const T *p, T)
@@ -40,6 +45,7 @@ struct RhsLinear {  // f_i = -p0 y_i
 };
 
 struct RhsLorenz {  // p = (sigma, rho, beta)
+    static constexpr bool kForcing = false;
     __device__ static double aux(double, const double *) { return 0.0; }
     template <int D, class T>
     __device__ static T one(int i, const T *y, const T *p, T)
@@ -51,6 +57,7 @@ struct RhsLorenz {  // p = (sigma, rho, beta)
 };
 
 struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 + F cos(omega t)
+    static constexpr bool kForcing = true;
     __device__ static double aux(double t, const double *p) { return p[2] * cos(p[1] * t); }
     template <int D, class T>
     __device__ static T one(int i, const T *y, const T *p, T aux)
@@ -62,6 +69,7 @@ struct RhsDuffing {  // p = (gamma, omega, F): x' = y, y' = -gamma y - x - x^3 +
 };
 
 struct RhsManufactured {  // f = p0 t^p1 + t^p2 - y
+    static constexpr bool kForcing = true;
     __device__ static double aux(double t, const double *p) { return p[0] * pow(t, p[1]) + pow(t, p[2]); }
     template <int D, class T>
     __device__ static T one(int, const T *y, const T *, T aux)
@@ -71,6 +79,7 @@ struct RhsManufactured {  // f = p0 t^p1 + t^p2 - y
 };
 
 struct RhsLcr {  // Sec. 5, Eq. sys.LRC; p = (sigma, omega, a, b, f)
+    static constexpr bool kForcing = true;
     __device__ static double aux(double t, const double *p) { return p[4] * sin(p[1] * t); }
     template <int D, class T>
     __device__ static T one(int i, const T *y, const T *p, T aux)

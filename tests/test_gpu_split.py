@@ -73,6 +73,24 @@ def test_split_duffing_batch_several_column_tiles(gpu_lib, parity, hist):
         parity(rel_err(got[b, : n + 1], ref[j, : n + 1]), TOL_SPLIT, b)
 
 
+def test_split_lorenz_batch_partial_warps(gpu_lib, parity):
+    """23 Lorenz trajectories on the tensor path: the column recurrence puts 10
+    trajectories (30 columns) in a warp, so the warps hold 10, 10 and 3 of them
+    and two lanes of each warp idle; lengths differ inside a warp, including
+    one that ends inside the first block and one that ends on a block edge."""
+    w = lorenz_long().subset(np.arange(23), N=2000)
+    ne = np.full(w.B, w.N, dtype=np.int64)
+    ne[::6] = 777
+    ne[[1, 13, 21]] = [5, 1280, 1999]
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
+                        history="tensor") as s:
+        got = s.solve_batch(w.y0, N_each=ne)
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0, params=w.params, N_each=ne)
+    for b in range(w.B):
+        n = ne[b]
+        parity(rel_err(got[b, : n + 1], ref[b, : n + 1]), TOL_SPLIT, b)
+
+
 @pytest.mark.parametrize("hist", HISTS)
 def test_split_matches_fp64_gpu_on_lcr(gpu_lib, parity, hist):
     w = lcr_sweep(B=16, N=4000)
