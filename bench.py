@@ -391,6 +391,8 @@ def main():
                     help="before the warm-up, let the library's autotuner pick the history "
                          "kernel settings on solves truncated to N_PROBE steps (0: off)")
     ap.add_argument("--k-max", type=int, default=14, help="served-mix: N = 2^k, k <= k_max")
+    ap.add_argument("--recurrence", default="auto", choices=["auto", "columns", "targets"],
+                    help="split precision, tensor history: layout of the recurrence")
     args = ap.parse_args()
     if args.workload == "served-mix":
         if args.precision is None:
@@ -419,7 +421,8 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fabm.load()
-    solver = fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision=args.precision)
+    solver = fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision=args.precision,
+                         recurrence=args.recurrence)
     wstats = solver.kernel_stats()["weights"]
     tuned = None
     if args.autotune > 0:

@@ -154,6 +154,25 @@ enum {
 fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel);
 int fabm_get_history_kernel(const fabm_solver *s);
 
+/* Step layouts of the split-precision recurrence on the tensor-history path
+ * (fabm_set_recurrence_layout); both compute the same steps in float-float. */
+enum {
+    FABM_REC_AUTO = 0,     /* COLUMNS when the batch has at least 152 warps of columns
+                              (152 * 32/dim trajectories) or N * columns >= 2^28
+                              (the history dominates), else TARGETS                 */
+    FABM_REC_COLUMNS = 1,  /* one lane per column (trajectory, component), 32/dim
+                              trajectories per warp: fewest instructions per step    */
+    FABM_REC_TARGETS = 2   /* one lane per target, one CTA of dim warps per
+                              trajectory: most parallelism for narrow batches        */
+};
+
+/* Choose the recurrence layout (one of FABM_REC_*) for later solves on the
+ * tensor-history path; other paths ignore it.  FABM_EINVAL for other values,
+ * FABM_EBUSY while another thread uses the solver. */
+fabm_status fabm_set_recurrence_layout(fabm_solver *s, int layout);
+/* The layout set on the solver (FABM_REC_*), or -1 for NULL. */
+int fabm_get_recurrence_layout(const fabm_solver *s);
+
 /* Autotuner: times a solve of the caller's batch (B, y0, traj_params as for
  * fabm_solve_batch) truncated to n_probe steps for each candidate setting and
  * keeps the fastest on the solver.  Candidates: for FABM_FP64, the split-k CTA

@@ -18,6 +18,7 @@ FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, F
 FABM_FP64, FABM_SPLIT = 0, 1
 FABM_HIST_AUTO, FABM_HIST_FP64, FABM_HIST_TENSOR, FABM_HIST_FP32C = range(4)
 HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3}
+RECURRENCE = {"auto": 0, "columns": 1, "targets": 2}
 RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
        "lcr": 6}
 PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
@@ -29,7 +30,8 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_result", "fabm_server_stats", "fabm_server_destroy", "fabm_autotune",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
-            "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy")
+            "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
+            "fabm_set_recurrence_layout", "fabm_get_recurrence_layout")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -102,6 +104,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_autotune.restype = i
     lib.fabm_set_history_kernel.argtypes = [vp, i]
     lib.fabm_get_history_kernel.argtypes = [vp]
+    lib.fabm_set_recurrence_layout.argtypes = [vp, i]
+    lib.fabm_get_recurrence_layout.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
     lib.fabm_kernel_busy.argtypes = [vp, i, P(d)]
@@ -113,7 +117,8 @@ def load(build_if_missing: bool = True):
               "fabm_destroy", "fabm_set_block",
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
-              "fabm_get_history_kernel"):
+              "fabm_get_history_kernel", "fabm_set_recurrence_layout",
+              "fabm_get_recurrence_layout"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -239,6 +244,16 @@ def fabm_get_history_kernel(handle) -> int:
     return load().fabm_get_history_kernel(handle)
 
 
+def fabm_set_recurrence_layout(handle, layout):
+    """Recurrence layout of the tensor-history path: "auto", "columns" or "targets"."""
+    k = RECURRENCE[layout] if isinstance(layout, str) else int(layout)
+    _check(load().fabm_set_recurrence_layout(handle, k))
+
+
+def fabm_get_recurrence_layout(handle) -> int:
+    return load().fabm_get_recurrence_layout(handle)
+
+
 def fabm_set_graphs(handle, enable: bool):
     _check(load().fabm_set_graphs(handle, int(bool(enable))))
 
@@ -270,7 +285,7 @@ class Solver:
     """Owns one fabm_solver.  ``rhs`` and ``precision`` are names or ids."""
 
     def __init__(self, rhs, dim, alpha, h, N, params=None, precision="fp64", block=None,
-                 history=None):
+                 history=None, recurrence=None):
         self.rhs = RHS[rhs] if isinstance(rhs, str) else int(rhs)
         self.dim, self.h, self.N = int(dim), float(h), int(N)
         self.alpha = tuple(float(a) for a in alpha) if np.ndim(alpha) > 0 else float(alpha)
@@ -281,6 +296,8 @@ class Solver:
             fabm_set_block(self.handle, block)
         if history is not None:
             fabm_set_history_kernel(self.handle, history)
+        if recurrence is not None:
+            fabm_set_recurrence_layout(self.handle, recurrence)
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -98,7 +98,9 @@ struct fabm_solver {
     int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     int L = kRecurL;                   // block length of the last solve
-    int cols_warps = 1;                // warps per CTA of the column recurrence (tensor path)
+    int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
+    int cols_warps = 1;                // tensor path: warps per CTA of the column recurrence,
+                                       // or 0 for the lane-per-target layout
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
     DevBuf<double> wB, wA, wD;
@@ -495,18 +497,28 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int n_ct = (int)((cols + 127) / 128);
     int split_chunks = 1;
     if (split) {
-        // leave SMs for the recurrence warps that run beside the tensor kernel
-        // (one tensor CTA fills an SM's register file): one SM per 8 warps of
-        // 32/dim trajectories, only where the column tiles do not need every SM
+        // recurrence layout: one lane per column for wide batches, and where
+        // the history dominates (its SMs matter more than the recurrence's
+        // latency); one lane per target for short, narrow runs (more
+        // parallelism, more instructions)
+        const int cwarps = recur_cols_warps(dim, B);
+        const bool columns =
+            s->rec_layout == FABM_REC_COLUMNS ||
+            (s->rec_layout == FABM_REC_AUTO && (cwarps >= 152 || (double)Nmax * cols >= 0x1p28));
+        // leave SMs for the recurrence that runs beside the tensor kernel (one
+        // tensor CTA fills an SM's register file), only where the column tiles
+        // do not need every SM: one SM per 8 column warps, or per 12
+        // trajectories of the lane-per-target layout
         int reserve = s->sm_reserve;
         if (reserve < 0) {
-            const int64_t warps = (B + kWarp / dim - 1) / (kWarp / dim);
-            reserve = n_ct <= 16 ? (int)std::clamp<int64_t>((warps + 7) / 8, 4, 40) : 0;
+            const int64_t want = columns ? std::clamp<int64_t>((cwarps + 7) / 8, 4, 40)
+                                         : std::min<int64_t>((B + 11) / 12, 40);
+            reserve = n_ct <= 16 ? (int)want : 0;
         }
         split_chunks = std::max(1, (148 - reserve) / n_ct);
-        // recurrence CTAs sized to fill the SMs the tensor CTAs leave free
+        // column layout: CTAs sized to fill the SMs the tensor CTAs leave free
         const int free_sms = std::max(4, 152 - n_ct * split_chunks);
-        s->cols_warps = std::clamp((recur_cols_warps(dim, B) + free_sms - 1) / free_sms, 1, 12);
+        s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 12) : 0;
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
         // far chunks and one chunk for the newest segment
@@ -888,6 +900,20 @@ fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
 }
 
 int fabm_get_history_kernel(const fabm_solver *s) { return s ? s->hist_kernel : -1; }
+
+fabm_status fabm_set_recurrence_layout(fabm_solver *s, int layout)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (layout != FABM_REC_AUTO && layout != FABM_REC_COLUMNS && layout != FABM_REC_TARGETS)
+        return fail(FABM_EINVAL, "recurrence layout %d: 0 (auto), 1 (columns) or 2 (targets)", layout);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->rec_layout = layout;
+    return FABM_OK;
+}
+
+int fabm_get_recurrence_layout(const fabm_solver *s) { return s ? s->rec_layout : -1; }
 
 int fabm_get_block(const fabm_solver *s) { return s ? s->L : 0; }
 

@@ -140,7 +140,8 @@ cudaError_t launch_ff_weights(const double *W, double scale, int64_t n, float2 *
 // the 64 steps of block c given G, the history of every point k < 64c as
 // float-float pairs [2][64][cols] (NULL for c = 0).  WB, WA: h^a B(d), h^a A(d)
 // for d = 0..64; WD: h^a D(m), m = 0..N; all float-float pairs, one order.
-// warps_per_cta (1..12) warps of 32/dim trajectories per CTA.  X: the table
+// warps_per_cta (1..12) warps of 32/dim trajectories per CTA, or 0: one lane
+// per target, a CTA of dim warps per trajectory (narrow batches).  X: the table
 // of the time-only part of f for block c (launch_aux_table), required when
 // rhs_has_forcing(rhs), else ignored.  y's slots receive float-float
 // increments; launch_finish_y turns them into y after the last block.

@@ -213,6 +213,125 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
     }
 }
 
+// The same block with one lane per target (targets a and a+32 on lane a), one
+// CTA of D warps per trajectory: for narrow batches, where one lane per column
+// leaves the GPU mostly idle.  Every pending target adds the newest point as
+// it appears; the owner of the next target runs the step, the components
+// exchange y through shared memory.  Same inputs and outputs as
+// recur_cols_kernel.
+template <class Rhs, int D>
+__global__ void __launch_bounds__(D *kWarp)
+    recur_targets_kernel(DevBatch bt, const float2 *__restrict__ WB, const float2 *__restrict__ WA,
+                         const float2 *__restrict__ WD, StepConsts kc, int64_t c,
+                         const float2 *__restrict__ G, const float2 *__restrict__ X)
+{
+    constexpr int TPL = kColL / kWarp;
+    __shared__ FF sB[kColL + 1], sA[kColL + 1];
+    __shared__ FF sy[2][D];
+    const int b = blockIdx.x;
+    const int i = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int64_t Nb = bt.N_each[b];
+    const int64_t m0 = c * kColL;
+    if (m0 >= Nb) return;  // trajectory finished (uniform over the CTA)
+    for (int d = threadIdx.x; d <= kColL; d += blockDim.x) sB[d] = ld_ff(WB + d), sA[d] = ld_ff(WA + d);
+
+    double p[kMaxParams];
+    FF pf[kMaxParams];
+#pragma unroll
+    for (int q = 0; q < kMaxParams; ++q) {
+        p[q] = bt.params[(int64_t)b * kMaxParams + q];
+        pf[q] = ff_from_double(p[q]);
+    }
+    const int64_t col = (int64_t)b * D + i;
+    const float2 *F2 = reinterpret_cast<const float2 *>(bt.F);
+    const double y0 = bt.y0[col];
+    const double y1 = bt.y1 ? bt.y1[col] : 0.0;
+    const FF ha = ff_from_double(kc.h_alpha[0]);
+    const FF ha_ig2 = ff_from_double(kc.h_alpha[0] * kc.inv_gamma2[0]);
+    const FF f0 = ld_ff(F2 + col);
+    const FF aux0 = Rhs::kForcing ? FF(0) : ff_from_double(Rhs::aux(0.0, p));
+
+    FF T[TPL], bP[TPL], bC[TPL], ax[TPL], nP[TPL], nC[TPL], rc[TPL], fo[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int a = lane + kWarp * t;
+        const int64_t m = m0 + 1 + a;
+        T[t] = bt.y1 ? ff_from_double(fma((double)m * kc.h, y1, y0)) : ff_from_double(y0);
+        const FF gP = G ? ld_ff(G + (int64_t)a * bt.cols + col) : FF(0);
+        const FF gC = G ? ld_ff(G + (int64_t)(kColL + a) * bt.cols + col) : FF(0);
+        bP[t] = ha * gP;
+        bC[t] = ff_fma(ld_ff(WD + m), f0, ha * gC);
+        ax[t] = Rhs::kForcing ? ld_ff(X + (int64_t)a * bt.B + b) : aux0;
+        nP[t] = nC[t] = rc[t] = fo[t] = FF(0);
+    }
+    FF fk = ld_ff(F2 + m0 * bt.ldF + col);  // the newest known point, f_{cL}
+    __syncthreads();
+
+    const int steps = (int)(Nb - m0 < kColL ? Nb - m0 : kColL);
+    for (int s = 0; s < steps; ++s) {
+        // every pending target adds the point cL+s; targets already done add
+        // the weight of distance 0, which is 0
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int d = lane + kWarp * t - s + 1;
+            const int dd = d > 0 ? d : 0;
+            dot2_acc(nP[t], sB[dd], fk);
+            dot2_acc(nC[t], sA[dd], fk);
+        }
+        const int owner = s % kWarp, slot = s / kWarp;  // uniform over the CTA
+        FF yp(0), ncor(0), tt(0), bc(0), axs(0);
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (t == slot) yp = T[t] + (bP[t] + ff_norm(nP[t])), ncor = ff_norm(nC[t]), tt = T[t],
+                           bc = bC[t], axs = ax[t];
+        FF fn(0), r(0);
+        if constexpr (D == 1) {
+            if (lane == owner) {
+                const FF fp = Rhs::template one<D>(0, &yp, pf, axs);
+                r = bc + ff_fma(ha_ig2, fp, ncor);
+                const FF yc = tt + r;
+                fn = Rhs::template one<D>(0, &yc, pf, axs);
+            }
+        } else {
+            if (lane == owner) sy[0][i] = yp;
+            __syncthreads();
+            if (lane == owner) {
+                FF y[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) y[q] = sy[0][q];
+                const FF fp = Rhs::template one<D>(i, y, pf, axs);
+                r = bc + ff_fma(ha_ig2, fp, ncor);
+                sy[1][i] = tt + r;
+            }
+            __syncthreads();
+            if (lane == owner) {
+                FF y[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) y[q] = sy[1][q];
+                fn = Rhs::template one<D>(i, y, pf, axs);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (t == slot && lane == owner) rc[t] = r, fo[t] = fn;
+        fk = shfl_ff(fn, owner);
+    }
+
+    // the block's increments of y and f, one target per lane
+    float2 *Yb = reinterpret_cast<float2 *>(bt.Y + (int64_t)b * (bt.N + 1) * D);
+    float2 *Fw = reinterpret_cast<float2 *>(bt.F);
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int a = lane + kWarp * t;
+        if (a < steps) {
+            const int64_t m = m0 + 1 + a;
+            Yb[m * D + i] = make_float2(rc[t].hi, rc[t].lo);
+            Fw[m * bt.ldF + col] = make_float2(fo[t].hi, fo[t].lo);
+            if (!(finite_f(rc[t].hi) && finite_f(fo[t].hi))) report_nonfinite(bt.status, m, b);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t prepare_recur_cols(int rhs, int dim)
@@ -237,11 +356,16 @@ cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, con
                               const float2 *WD, const StepConsts &k, int64_t c, const float2 *G,
                               const float2 *X, int warps_per_cta, cudaStream_t st)
 {
-    if (warps_per_cta < 1 || warps_per_cta > kMaxWarps) return cudaErrorInvalidValue;
+    if (warps_per_cta < 0 || warps_per_cta > kMaxWarps) return cudaErrorInvalidValue;
     bool need_x = false;
     const bool ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
         need_x = R::kForcing;
         if (need_x && !X) return;
+        if (warps_per_cta == 0) {  // one lane per target
+            recur_targets_kernel<R, D><<<(unsigned)bt.B, D * kWarp, 0, st>>>(bt, WB, WA, WD, k, c,
+                                                                             G, X);
+            return;
+        }
         const int warps = recur_cols_warps(D, bt.B);
         const unsigned blocks = (unsigned)((warps + warps_per_cta - 1) / warps_per_cta);
         recur_cols_kernel<R, D><<<blocks, warps_per_cta * kWarp, cols_smem_bytes(D, warps_per_cta),

@@ -64,3 +64,5 @@ def test_null_handles_are_rejected_or_ignored():
     assert lib.fabm_solve(None, None, None) == fabm.FABM_EINVAL
     assert lib.fabm_set_block(None, 32) == fabm.FABM_EINVAL
     assert lib.fabm_get_block(None) == 0
+    assert lib.fabm_set_recurrence_layout(None, 1) == fabm.FABM_EINVAL
+    assert lib.fabm_get_recurrence_layout(None) == -1

@@ -17,6 +17,8 @@ from fabm_workloads import (duffing_sweep, lcr_sweep, lorenz_long, lorenz_single
 pytestmark = pytest.mark.gpu
 TOL_SPLIT = 1e-6
 HISTS = ["tensor", "fp32c"]
+# history kernel and, on the tensor path, the recurrence layout
+PATHS = [("tensor", "columns"), ("tensor", "targets"), ("fp32c", None)]
 
 
 def rel_err(got, ref):
@@ -26,11 +28,12 @@ def rel_err(got, ref):
     return float(np.max(np.abs(np.asarray(got) - ref) / scale))
 
 
-@pytest.mark.parametrize("hist", HISTS)
+@pytest.mark.parametrize("hist,rec", PATHS)
 @pytest.mark.parametrize("N", [1, 31, 32, 33, 63, 64, 65, 128, 129, 193, 1000])
-def test_split_constant_rhs_closed_form(gpu_lib, N, hist):
+def test_split_constant_rhs_closed_form(gpu_lib, N, hist, rec):
     alpha, h = 0.7, 0.01
-    with gpu_lib.Solver("const", 1, alpha, h, N, [1.5], precision="split", history=hist) as s:
+    with gpu_lib.Solver("const", 1, alpha, h, N, [1.5], precision="split", history=hist,
+                        recurrence=rec) as s:
         y = s.solve([0.25])
     t = np.arange(N + 1) * h
     ex = 0.25 + 1.5 * t ** alpha / math.gamma(alpha + 1)
@@ -55,15 +58,16 @@ def test_split_lorenz_prefix(gpu_lib, parity, hist):
     parity(rel_err(got, ref), TOL_SPLIT, "")
 
 
-@pytest.mark.parametrize("hist", HISTS)
-def test_split_duffing_batch_several_column_tiles(gpu_lib, parity, hist):
+@pytest.mark.parametrize("hist,rec", PATHS)
+def test_split_duffing_batch_several_column_tiles(gpu_lib, parity, hist, rec):
     """300 trajectories x 2 = 600 columns: five 128-column tiles, the last one
     ragged; uneven lengths."""
     w = duffing_sweep(B=300, N=3000)
     ne = np.full(w.B, w.N, dtype=np.int64)
     ne[::7] = 1777
     ne[3] = 1
-    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist) as s:
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split", history=hist,
+                        recurrence=rec) as s:
         got = s.solve_batch(w.y0, traj_params=w.traj_params, N_each=ne)
     idx = np.r_[0:8, 150:154, 292:300]
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
@@ -73,7 +77,8 @@ def test_split_duffing_batch_several_column_tiles(gpu_lib, parity, hist):
         parity(rel_err(got[b, : n + 1], ref[j, : n + 1]), TOL_SPLIT, b)
 
 
-def test_split_lorenz_batch_partial_warps(gpu_lib, parity):
+@pytest.mark.parametrize("rec", ["columns", "targets"])
+def test_split_lorenz_batch_partial_warps(gpu_lib, parity, rec):
     """23 Lorenz trajectories on the tensor path: the column recurrence puts 10
     trajectories (30 columns) in a warp, so the warps hold 10, 10 and 3 of them
     and two lanes of each warp idle; lengths differ inside a warp, including
@@ -83,7 +88,7 @@ def test_split_lorenz_batch_partial_warps(gpu_lib, parity):
     ne[::6] = 777
     ne[[1, 13, 21]] = [5, 1280, 1999]
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
-                        history="tensor") as s:
+                        history="tensor", recurrence=rec) as s:
         got = s.solve_batch(w.y0, N_each=ne)
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0, params=w.params, N_each=ne)
     for b in range(w.B):
@@ -117,6 +122,34 @@ def test_split_deterministic(gpu_lib, hist):
         a = s.solve(w.y0[0])
         b = s.solve(w.y0[0])
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("rec", ["columns", "targets"])
+def test_recurrence_layouts_agree_on_a_sweep(gpu_lib, parity, rec):
+    """LCR sweep on the tensor path with either recurrence layout, against the
+    oracle over the non-chaotic horizon, and both layouts against each other."""
+    w = lcr_sweep(B=96, N=3000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
+                        history="tensor", recurrence=rec) as s:
+        got = s.solve_batch(w.y0, traj_params=w.traj_params)
+        assert gpu_lib.fabm_get_recurrence_layout(s.handle) == gpu_lib.RECURRENCE[rec]
+    idx = np.r_[0:3, 60:63, 93:96]
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
+                             traj_params=w.traj_params[idx])
+    for j, b in enumerate(idx):
+        parity(rel_err(got[b, : w.compare_steps + 1], ref[j, : w.compare_steps + 1]), TOL_SPLIT, b)
+    other = "targets" if rec == "columns" else "columns"
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
+                        history="tensor", recurrence=other) as s:
+        alt = s.solve_batch(w.y0, traj_params=w.traj_params)
+    n = w.compare_steps + 1
+    assert rel_err(got[:, :n], alt[:, :n]) < TOL_SPLIT
+
+
+def test_recurrence_layout_rejects_unknown(gpu_lib):
+    with gpu_lib.Solver("linear", 1, 0.8, 1e-3, 100, [1.0], precision="split") as s:
+        with pytest.raises(gpu_lib.FabmError):
+            gpu_lib.fabm_set_recurrence_layout(s.handle, 7)
 
 
 def test_auto_history_kernel_choice(gpu_lib):
