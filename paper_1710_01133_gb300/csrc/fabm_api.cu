@@ -123,11 +123,14 @@ struct fabm_solver {
     DevBuf<unsigned long long> status;
     // sR: recurrence; sG, sG2: far history (the CUDA-core history of odd blocks
     // runs on sG2, so that consecutive blocks' history launches overlap)
-    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr;
+    // sC: device-to-host copies of finished rows while the solve goes on
+    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr, sC = nullptr;
+    double *out_stream = nullptr;  // pinned host output of the solve being enqueued, or NULL
+    int64_t out_group = 1;         // blocks per streamed copy
     // evN: the newest-segment history launch of the tensor path (on sR); evA:
     // the forcing tables (tensor path, on sG2)
     cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evN[3] = {}, evA[kAuxRing] = {};
-    cudaEvent_t evFork = nullptr, evJoin = nullptr;
+    cudaEvent_t evFork = nullptr, evJoin = nullptr, evJoinC = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
@@ -169,11 +172,13 @@ struct fabm_solver {
             if (e) cudaEventDestroy(e);
         if (evFork) cudaEventDestroy(evFork);
         if (evJoin) cudaEventDestroy(evJoin);
+        if (evJoinC) cudaEventDestroy(evJoinC);
         if (gexec) cudaGraphExecDestroy(gexec);
         for (auto &e : ev_pool) cudaEventDestroy(e);
         if (sR) cudaStreamDestroy(sR);
         if (sG) cudaStreamDestroy(sG);
         if (sG2) cudaStreamDestroy(sG2);
+        if (sC) cudaStreamDestroy(sC);
     }
 };
 
@@ -434,15 +439,30 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             }));
         }
         FABM_CUDA_TRY(cudaEventRecord(s->evR[c % kEvRing], s->sR));
+        if (s->out_stream && ((c + 1) % s->out_group == 0 || c + 1 == nblk)) {
+            // rows of the blocks c0 .. c are final: (tensor path: to double, then)
+            // to the host, beside the next blocks
+            const int64_t c0 = c / s->out_group * s->out_group;
+            const int64_t r_lo = c0 == 0 ? 0 : c0 * L + 1, r_hi = std::min<int64_t>((c + 1) * L, bt.N);
+            FABM_CUDA_TRY(cudaStreamWaitEvent(s->sC, s->evR[c % kEvRing], 0));
+            if (split)
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sC, 0.0, [&] {
+                    return launch_finish_y(bt, s->h, std::max<int64_t>(r_lo, 1), r_hi, s->sC);
+                }));
+            const size_t pitch = sizeof(double) * (size_t)(bt.N + 1) * bt.dim;
+            FABM_CUDA_TRY(cudaMemcpy2DAsync(s->out_stream + r_lo * bt.dim, pitch, bt.Y + r_lo * bt.dim,
+                                            pitch, sizeof(double) * (size_t)(r_hi - r_lo + 1) * bt.dim,
+                                            (size_t)bt.B, cudaMemcpyDeviceToHost, s->sC));
+        }
         if (tables && c + kAuxRing < nblk) {
             const fabm_status st = enqueue_aux(c + kAuxRing);
             if (st != FABM_OK) return st;
         }
     }
     s->sample_now = true;
-    if (split)  // y = Taylor part + the float-float increments, in double
+    if (split && !s->out_stream)  // y = Taylor part + the float-float increments, in double
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, s->sR, 0.0,
-                                   [&] { return launch_finish_y(bt, s->h, s->sR); }));
+                                   [&] { return launch_finish_y(bt, s->h, 1, bt.N, s->sR); }));
     return FABM_OK;
 }
 
@@ -533,6 +553,20 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         FABM_CUDA_TRY(s->Ystage.ensure((size_t)B * (N + 1) * dim));
         Y = s->Ystage.p;
     }
+    // a large output into pinned host memory, every trajectory to N: copied
+    // block group by block group on sC while the solve goes on (a group is at
+    // least 8 MB), instead of once at the end
+    s->out_stream = nullptr;
+    const size_t out_bytes = sizeof(double) * (size_t)B * (N + 1) * dim;
+    if (!out_on_device && all_full && out_bytes >= (64u << 20)) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost) {
+            s->out_stream = out;
+            const size_t block_bytes = sizeof(double) * (size_t)B * L * dim;
+            s->out_group = (int64_t)std::max<size_t>(1, ((8u << 20) + block_bytes - 1) / block_bytes);
+        }
+        cudaGetLastError();  // an unregistered pointer is not an error here
+    }
     FABM_CUDA_TRY(cudaMemcpyAsync(s->y0.p, y0, sizeof(double) * B * dim, cudaMemcpyHostToDevice, s->sR));
     // y'(0) (1 < alpha < 2): zeros when not given, so that one cached graph
     // serves solves with and without it
@@ -575,7 +609,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)(s->sm_reserve + 1), (uintptr_t)s->cols_warps, (uintptr_t)Y,
         (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
-        (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p};
+        (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
+        (uintptr_t)s->out_stream, (uintptr_t)s->out_group};
     auto enqueue = [&]() -> fabm_status {
         return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk);
     };
@@ -585,11 +620,13 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         FABM_CUDA_TRY(cudaEventRecord(s->evFork, s->sR));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evFork, 0));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG2, s->evFork, 0));
+        FABM_CUDA_TRY(cudaStreamWaitEvent(s->sC, s->evFork, 0));
         fabm_status est = enqueue();
         if (est != FABM_OK) return est;
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG2));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sC));
         FABM_CUDA_TRY(collect_timing(s, s->recs));
     } else {
         if (!s->gexec || s->gkey != key) {
@@ -602,12 +639,15 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             cudaError_t e = cudaEventRecord(s->evFork, s->sR);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG, s->evFork, 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG2, s->evFork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sC, s->evFork, 0);
             fabm_status est = e == cudaSuccess ? enqueue() : FABM_ECUDA;
             if (est == FABM_OK) {
                 e = cudaEventRecord(s->evFork, s->sG);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evFork, 0);
                 if (e == cudaSuccess) e = cudaEventRecord(s->evJoin, s->sG2);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoin, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(s->evJoinC, s->sC);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoinC, 0);
             }
             cudaError_t e2 = cudaStreamEndCapture(s->sR, &graph);
             s->capturing = false;
@@ -641,7 +681,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         if (tout) return fail(FABM_ETIMEOUT, "a history kernel gave up waiting on a barrier");
     }
 
-    if (!out_on_device) {
+    if (!out_on_device && !s->out_stream) {
         const size_t row = (size_t)(N + 1) * dim;
         if (all_full) {
             FABM_CUDA_TRY(cudaMemcpy(out, Y, sizeof(double) * row * B, cudaMemcpyDeviceToHost));
@@ -742,6 +782,7 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->sR, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sC, cudaStreamNonBlocking);
     for (auto &ev : s->evR)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto &ev : s->evG)
@@ -752,6 +793,7 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evFork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoinC, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
         s->recs.clear();

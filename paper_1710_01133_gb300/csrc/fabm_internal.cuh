@@ -153,8 +153,10 @@ bool rhs_has_forcing(int rhs, int dim);
 // X[a][b] = aux(t_{64c+1+a}, params of b) as float-float pairs, a < 64, b < B.
 cudaError_t launch_aux_table(int rhs, const DevBatch &bt, double h, int64_t c, float2 *X,
                              cudaStream_t st);
-// y = T + increment in double for rows 1 .. N_each of every trajectory.
-cudaError_t launch_finish_y(const DevBatch &bt, double h, cudaStream_t st);
+// y = T + increment in double for the rows m_lo .. m_hi (1 <= m_lo, m_hi <= N)
+// of every trajectory, rows past its N_each excepted.
+cudaError_t launch_finish_y(const DevBatch &bt, double h, int64_t m_lo, int64_t m_hi,
+                            cudaStream_t st);
 // Kernel attributes (dynamic shared memory) of the column recurrence for one
 // right-hand side; call before the first launch, outside any graph capture.
 cudaError_t prepare_recur_cols(int rhs, int dim);

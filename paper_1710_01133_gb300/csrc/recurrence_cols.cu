@@ -70,17 +70,17 @@ __global__ void aux_kernel(DevBatch bt, double h, int64_t c, float2 *__restrict_
     }
 }
 
-// y_m = T(t_m) + (hi + lo) in double for m = 1 .. N_each[b], where the column
-// recurrence left the float-float increment (hi, lo) in y's slot; T = y0, or
-// y0 + t y'(0) for 1 < alpha < 2.
-__global__ void finish_y_kernel(DevBatch bt, double h)
+// y_m = T(t_m) + (hi + lo) in double for m = m_lo .. min(m_hi, N_each[b])
+// (m_lo >= 1), where the recurrence left the float-float increment (hi, lo) in
+// y's slot; T = y0, or y0 + t y'(0) for 1 < alpha < 2.
+__global__ void finish_y_kernel(DevBatch bt, double h, int64_t m_lo, int64_t m_hi)
 {
-    const int64_t per_traj = bt.N * bt.dim;
+    const int64_t per_traj = (m_hi - m_lo + 1) * bt.dim;
     const int64_t n = (int64_t)bt.B * per_traj;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = e / per_traj, r = e % per_traj;
-        const int64_t m = 1 + r / bt.dim;
+        const int64_t m = m_lo + r / bt.dim;
         const int i = (int)(r % bt.dim);
         if (m > bt.N_each[b]) continue;
         double *slot = bt.Y + (b * (bt.N + 1) + m) * bt.dim + i;
@@ -393,13 +393,15 @@ cudaError_t launch_aux_table(int rhs, const DevBatch &bt, double h, int64_t c, f
     return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_finish_y(const DevBatch &bt, double h, cudaStream_t st)
+cudaError_t launch_finish_y(const DevBatch &bt, double h, int64_t m_lo, int64_t m_hi,
+                            cudaStream_t st)
 {
-    const int64_t n = (int64_t)bt.B * bt.N * bt.dim;
+    if (m_lo < 1 || m_hi > bt.N) return cudaErrorInvalidValue;
+    if (m_hi < m_lo) return cudaSuccess;
+    const int64_t n = (int64_t)bt.B * (m_hi - m_lo + 1) * bt.dim;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) return cudaSuccess;
-    finish_y_kernel<<<(unsigned)blocks, 256, 0, st>>>(bt, h);
+    finish_y_kernel<<<(unsigned)blocks, 256, 0, st>>>(bt, h, m_lo, m_hi);
     return cudaGetLastError();
 }
 
