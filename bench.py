@@ -217,10 +217,13 @@ def roofline(kind, ks, precision, clocks, w):
     else:
         peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
         achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        note = ("FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
+                "(probe: 1.19 TFLOP/s at 1.96 GHz)")
+        if precision == "fp64x2":
+            note += ("; achieved counts algorithmic multiply-adds, each of which costs ten "
+                     "FP64 operations in double-double")
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": achieved / peak if peak else None,
-                    "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
-                                 "(probe: 1.19 TFLOP/s at 1.96 GHz)"})
+                    "frac": achieved / peak if peak else None, "peak_note": note})
     key = {"history": f"history_{'split' if precision == 'split' else 'fp64'}",
            "recurrence": "recurrence"}.get(kind)
     traffic = _profile_traffic(key, f"{kind}_{precision}_{w.name}") if key else None
@@ -378,7 +381,7 @@ def main():
     ap.add_argument("--impl", default="fabm", choices=["fabm", "reference"])
     ap.add_argument("--workload", default="lorenz-single",
                     choices=sorted(WORKLOADS) + ["served-mix"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "split"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "split", "fp64x2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-steps", type=int, default=None,
                     help="override the workload's N (small cases for profiling)")
@@ -498,7 +501,8 @@ def main():
             "unit": "steps*traj/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64x2" if args.precision == "fp64x2" else "f64",
+            "data": "synthetic",
             "config": _config(w, args),
             "history_gmac_s": w.history_macs() * ws / (step_ms * 1e-3) / 1e9,
             "roofline": line_roof,

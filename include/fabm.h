@@ -52,11 +52,18 @@ typedef enum {
 /* Arithmetic of the history sums. */
 enum {
     FABM_FP64 = 0,  /* every step in IEEE double                                   */
-    FABM_SPLIT = 1  /* history sums in compensated reduced precision: three-term bf16
+    FABM_SPLIT = 1, /* history sums in compensated reduced precision: three-term bf16
                        split on tensor cores (wide batches) or compensated fp32 on
                        CUDA cores (narrow batches); the weights, the per-step
                        predictor and corrector updates and the running history
                        accumulator stay in double */
+    FABM_FP64X2 = 2 /* the extended-precision mode the paper runs in long double
+                       (Sec. 4, "memory saving"): weights in double-double from
+                       binary128 (fabm_weights_x2), far-history sums in
+                       double-double (exact products, compensated sums, combined
+                       across chunks in double-double) and rounded once; the
+                       steps of a block in double as in FABM_FP64.  About ten FP64
+                       operations per history multiply-add */
 };
 
 /* Right-hand sides f(t, y) (params in this order; dim as stated). */
@@ -91,9 +98,10 @@ enum {
  *   N          number of steps, 1 <= N <= 2^31
  *   rhs_id     one of FABM_RHS_*
  *   params     n_params doubles (copied), the rhs parameters
- *   precision  FABM_FP64 or FABM_SPLIT
+ *   precision  FABM_FP64, FABM_SPLIT or FABM_FP64X2
  *   out        receives the solver handle
- * Computes the weights b, a, c on the device.  Errors: FABM_EINVAL for any
+ * Computes the weights b, a, c on the device (FABM_FP64X2: on the host, in
+ * binary128, then uploaded as double-double).  Errors: FABM_EINVAL for any
  * argument out of range, FABM_ENOMEM, FABM_ECUDA. */
 fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
                         const double *params, int n_params, int precision, fabm_solver **out);
@@ -141,11 +149,13 @@ const char *fabm_last_error(void);
 /* History kernels (fabm_set_history_kernel). */
 enum {
     FABM_HIST_AUTO = 0,    /* FP64 precision: FABM_HIST_FP64; split precision: tensor
-                              cores for batches of at least 64 columns, else FP32C   */
+                              cores for batches of at least 64 columns, else FP32C;
+                              FP64X2 precision: FABM_HIST_X2                         */
     FABM_HIST_FP64 = 1,    /* double on CUDA cores (FP64 precision only)             */
     FABM_HIST_TENSOR = 2,  /* three-term bf16 split on tcgen05 tensor cores, exact
                               per 64-point segment (split precision)                  */
-    FABM_HIST_FP32C = 3    /* compensated fp32 on CUDA cores (split precision)       */
+    FABM_HIST_FP32C = 3,   /* compensated fp32 on CUDA cores (split precision)       */
+    FABM_HIST_X2 = 4       /* double-double on CUDA cores (FP64X2 precision only)    */
 };
 
 /* Choose the history kernel (one of FABM_HIST_*; must fit the precision).
@@ -175,7 +185,8 @@ int fabm_get_recurrence_layout(const fabm_solver *s);
 
 /* Autotuner: times a solve of the caller's batch (B, y0, traj_params as for
  * fabm_solve_batch) truncated to n_probe steps for each candidate setting and
- * keeps the fastest on the solver.  Candidates: for FABM_FP64, the split-k CTA
+ * keeps the fastest on the solver.  Candidates: for FABM_FP64 (FABM_FP64X2: its
+ * double-double kernel), the split-k CTA
  * target of the history kernel (304, 608, 1216 CTAs); for FABM_SPLIT, the
  * tensor-core kernel with 0, 16 or 32 SMs (or an automatic number) kept free
  * for the recurrence running beside it, and the compensated-fp32 kernel at the
@@ -207,6 +218,15 @@ fabm_status fabm_set_graphs(fabm_solver *s, int enable);
  * the predictor weights of Eq. abm and the corrector weights of Sec. 2 in the
  * distance form d = (n+1) - k used by the kernels.  Any of B, A, D may be NULL. */
 fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D);
+
+/* The weights B(d), A(d), D(m) of fabm_copy_weights for d, m = 0..n in
+ * double-double: hi is the double nearest the value, lo the rounded rest
+ * (about 1e-27 relative for n <= 2^20).  Evaluated on the host in binary128
+ * from cancellation-free rewrites of the printed differences; needs no GPU.
+ * Arrays of n+1 doubles each.  FABM_EINVAL unless 0 < alpha < 2, n >= 0 and no
+ * pointer is NULL. */
+fabm_status fabm_weights_x2(double alpha, int64_t n, double *B_hi, double *B_lo, double *A_hi,
+                            double *A_lo, double *D_hi, double *D_lo);
 
 /* Stroboscopic samples of solved trajectories, the sampling behind the
  * bifurcation diagram of Sec. 5 (the attractor of the forced LCR system seen

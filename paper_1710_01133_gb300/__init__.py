@@ -15,13 +15,13 @@ import numpy as np
 from . import build as _build
 
 FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, FABM_EBUSY = range(7)
-FABM_FP64, FABM_SPLIT = 0, 1
+FABM_FP64, FABM_SPLIT, FABM_FP64X2 = 0, 1, 2
 FABM_HIST_AUTO, FABM_HIST_FP64, FABM_HIST_TENSOR, FABM_HIST_FP32C = range(4)
-HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3}
+HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3, "x2": 4}
 RECURRENCE = {"auto": 0, "columns": 1, "targets": 2}
 RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
        "lcr": 6}
-PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT}
+PRECISION = {"fp64": FABM_FP64, "split": FABM_SPLIT, "fp64x2": FABM_FP64X2}
 _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_last_error", "fabm_set_block", "fabm_get_block", "fabm_last_launch_count",
             "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats", "fabm_set_graphs",
@@ -31,7 +31,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
-            "fabm_set_recurrence_layout", "fabm_get_recurrence_layout")
+            "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_set_history_kernel.argtypes = [vp, i]
     lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_set_recurrence_layout.argtypes = [vp, i]
+    lib.fabm_weights_x2.argtypes = [d, i64] + [P(d)] * 6
+    lib.fabm_weights_x2.restype = i
     lib.fabm_get_recurrence_layout.argtypes = [vp]
     lib.fabm_solve_noalloc.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d)]
     lib.fabm_kernel_stats.argtypes = [vp, i, P(i64), P(d), P(d)]
@@ -219,6 +221,14 @@ def fabm_copy_weights(handle, n):
     B, A, D = np.empty(n), np.empty(n), np.empty(n)
     _check(load().fabm_copy_weights(handle, int(n), _dp(B), _dp(A), _dp(D)))
     return B, A, D
+
+
+def fabm_weights_x2(alpha: float, n: int):
+    """Double-double weights (B_hi, B_lo, A_hi, A_lo, D_hi, D_lo), n+1 entries
+    each, computed on the host in binary128 (no GPU needed)."""
+    out = [np.empty(int(n) + 1) for _ in range(6)]
+    _check(load().fabm_weights_x2(float(alpha), int(n), *[_dp(a) for a in out]))
+    return tuple(out)
 
 
 def fabm_last_launch_count(handle) -> int:

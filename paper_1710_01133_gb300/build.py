@@ -1,6 +1,7 @@
 """Build libfabm.so (the CUDA library behind include/fabm.h) in-tree for sm_103a.
 
-Each .cu file under csrc/ is compiled by nvcc in parallel and linked into
+Each .cu file under csrc/ is compiled by nvcc (each .c file, host code, by the
+C compiler) in parallel and linked into
 ``_build/libfabm.so`` next to this file.  Rebuilds only when a source or header
 is newer than the library.  Usage: ``python -m paper_1710_01133_gb300.build``.
 """
@@ -31,7 +32,7 @@ def _nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.c")))
 
 
 def _stale() -> bool:
@@ -50,11 +51,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
+        if src.endswith(".c"):
+            cmd = [shutil.which("gcc") or "cc", "-O2", "-std=gnu11", "-fPIC", "-fno-fast-math",
+                   "-I" + os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+        else:
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+            raise RuntimeError(f"compiling {src} failed:\n{r.stderr}")
         if verbose and r.stderr:
             print(r.stderr, file=sys.stderr)
         return obj
@@ -63,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+           "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lm", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -104,6 +104,7 @@ struct fabm_solver {
     StepConsts k{};
     int64_t w_ext = 0;  // weights valid for index 0..w_ext
     DevBuf<double> wB, wA, wD;
+    DevBuf<double> wBl, wAl, wDl;  // FP64X2: low parts of the double-double weights
     // split path: fp32 weights (narrow kernel), Hankel weight tiles per lag and
     // their exponents (tensor kernel), float-float h^a B(d), h^a A(d) for
     // d <= 64 and h^a D(m) (column recurrence)
@@ -158,6 +159,7 @@ struct fabm_solver {
     ~fabm_solver()
     {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
+        wBl.release(), wAl.release(), wDl.release();
         wBf.release(), wAf.release(), wBff.release(), wAff.release(), wDff.release();
         F.release(), Ystage.release(), G.release(), part.release();
         Fs.release(), Fe.release(), spart.release(), auxb.release(), err.release();
@@ -289,6 +291,7 @@ cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &
 int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 {
     if (s->precision == FABM_FP64) return FABM_HIST_FP64;
+    if (s->precision == FABM_FP64X2) return FABM_HIST_X2;
     // one order per component: every column tile would need its own weight
     // operand, so the tensor kernel (one weight operand per tile) is not used
     if (s->multi) return FABM_HIST_FP32C;
@@ -313,7 +316,7 @@ int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 // extra lag block only lengthens the recurrence.
 int history_lag(int hk, int64_t N, int64_t cols)
 {
-    if (hk == FABM_HIST_FP64) return N * cols >= (1LL << 19) ? 2 : 1;
+    if (hk == FABM_HIST_FP64 || hk == FABM_HIST_X2) return N * cols >= (1LL << 19) ? 2 : 1;
     if (hk == FABM_HIST_FP32C) return N * cols >= (1LL << 25) ? 2 : 1;
     return 1;
 }
@@ -395,7 +398,16 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             const double flops = 4.0 * L * (double)k_end * (double)cols;
             FABM_CUDA_TRY(cudaStreamWaitEvent(gs, s->evR[(c - lag - 1) % kEvRing], 0));
             plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
-            if (hk == FABM_HIST_FP32C) {
+            if (hk == FABM_HIST_X2) {
+                double2 *xp = reinterpret_cast<double2 *>(s->part.p) + poff;
+                const DevWeightsLo wl{s->wBl.p, s->wAl.p, s->wDl.p};
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
+                    return launch_hist_x2(bt, w, wl, c, lag, n_chunks, kc, xp, gs);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, gs, 0.0, [&] {
+                    return launch_reduce_x2(xp, n_chunks, (int)cols, Gbuf, gs);
+                }));
+            } else if (hk == FABM_HIST_FP32C) {
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, gs, flops, [&] {
                     return launch_hist_fp32c(bt, s->wBf.p, s->wAf.p, w.stride, c, lag, n_chunks,
                                              kc, s->spart.p + poff, gs);
@@ -509,6 +521,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     FABM_CUDA_TRY(s->G.ensure((size_t)3 * 2 * L * cols));
     // two partial buffers: the history launches of blocks c and c+1 may overlap
     if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)2 * max_chunks * part_per_chunk));
+    if (hk == FABM_HIST_X2) FABM_CUDA_TRY(s->part.ensure((size_t)4 * max_chunks * part_per_chunk));
     if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)2 * max_chunks * part_per_chunk));
     FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim * 2));  // y0, then y1
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
@@ -738,7 +751,7 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     }
     if (!(h > 0.0) || !std::isfinite(h)) return fail(FABM_EINVAL, "h %g must be positive", h);
     if (N < 1 || N > (1LL << 31)) return fail(FABM_EINVAL, "N %lld outside 1..2^31", (long long)N);
-    if (precision != FABM_FP64 && precision != FABM_SPLIT)
+    if (precision != FABM_FP64 && precision != FABM_SPLIT && precision != FABM_FP64X2)
         return fail(FABM_EINVAL, "precision %d unknown", precision);
     fabm_status st = check_rhs(rhs_id, dim, n_params);
     if (st != FABM_OK) return st;
@@ -794,7 +807,27 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evFork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoinC, cudaEventDisableTiming);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && precision == FABM_FP64X2) {
+        // double-double weights from binary128 on the host: high parts into
+        // wB, wA, wD, low parts into wBl, wAl, wDl
+        e = s->wBl.ensure(wlen);
+        if (e == cudaSuccess) e = s->wAl.ensure(wlen);
+        if (e == cudaSuccess) e = s->wDl.ensure(wlen);
+        std::vector<double> hb(wlen), lb(wlen), ha(wlen), la(wlen), hd(wlen), ld(wlen);
+        for (int q = 0; q < n_sets && e == cudaSuccess; ++q) {
+            const size_t o = (size_t)q * (s->w_ext + 1);
+            if (fabm_weights_x2(alpha_c[q], s->w_ext, &hb[o], &lb[o], &ha[o], &la[o], &hd[o], &ld[o]) !=
+                FABM_OK)
+                e = cudaErrorInvalidValue;
+        }
+        const size_t nb = sizeof(double) * wlen;
+        if (e == cudaSuccess) e = cudaMemcpy(s->wB.p, hb.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->wBl.p, lb.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->wA.p, ha.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->wAl.p, la.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->wD.p, hd.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->wDl.p, ld.data(), nb, cudaMemcpyHostToDevice);
+    } else if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
         s->recs.clear();
         for (int q = 0; q < n_sets && e == cudaSuccess; ++q) {
@@ -912,7 +945,8 @@ fabm_status fabm_set_block(fabm_solver *s, int L)
     if (L == kSplitSeg && s->precision == FABM_SPLIT)
         hk = FABM_HIST_TENSOR;
     else if (L == kRecurL)
-        hk = s->precision == FABM_SPLIT ? FABM_HIST_FP32C : FABM_HIST_FP64;
+        hk = s->precision == FABM_SPLIT ? FABM_HIST_FP32C
+                                        : (s->precision == FABM_FP64X2 ? FABM_HIST_X2 : FABM_HIST_FP64);
     else
         return fail(FABM_EINVAL,
                     "block length %d: 32 (fp64 or fp32c history) or 64 (tensor history, split "
@@ -931,6 +965,7 @@ fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     const bool ok = kernel == FABM_HIST_AUTO ||
                     (s->precision == FABM_FP64 && kernel == FABM_HIST_FP64) ||
+                    (s->precision == FABM_FP64X2 && kernel == FABM_HIST_X2) ||
                     (s->precision == FABM_SPLIT &&
                      (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_FP32C));
     if (!ok) return fail(FABM_EINVAL, "history kernel %d does not fit precision %d", kernel, s->precision);
@@ -990,8 +1025,9 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     std::vector<Cand> cands;
     const int ctas_opts[] = {152 * 2, 152 * 4, 152 * 8};
     // at most 8 candidates are reported
-    if (s->precision == FABM_FP64) {
-        for (int c : ctas_opts) cands.push_back({FABM_HIST_FP64, c});
+    if (s->precision == FABM_FP64 || s->precision == FABM_FP64X2) {
+        const int k = s->precision == FABM_FP64 ? FABM_HIST_FP64 : FABM_HIST_X2;
+        for (int c : ctas_opts) cands.push_back({k, c});
     } else {
         // tensor kernel: "ctas" carries the SM reserve (-1 automatic, 0, 16, 32)
         for (int r : {-1, 0, 16, 32}) cands.push_back({FABM_HIST_TENSOR, r});

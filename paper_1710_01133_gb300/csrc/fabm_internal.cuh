@@ -163,6 +163,24 @@ cudaError_t prepare_recur_cols(int rhs, int dim);
 // Warps the column recurrence needs for B trajectories of dimension dim.
 int recur_cols_warps(int dim, int64_t B);
 
+// ---- FP64X2 precision (double-double history) ----
+
+// Low parts of the double-double weights; the high parts are the DevWeights
+// vectors (same layout and stride).
+struct DevWeightsLo {
+    const double *B;
+    const double *A;
+    const double *D;
+};
+
+// a2 in double-double: partial far-history sums of target block c (32 targets)
+// over k < (c-lag)*32 as (hi, lo) pairs, n_chunks x 2 x 32 x cols.
+cudaError_t launch_hist_x2(const DevBatch &bt, const DevWeights &w, const DevWeightsLo &wl,
+                           int64_t c, int lag, int n_chunks, int64_t kc, double2 *part,
+                           cudaStream_t st);
+// a3: G = sum over chunks in double-double, rounded once to double.
+cudaError_t launch_reduce_x2(const double2 *part, int n_chunks, int cols, double *G, cudaStream_t st);
+
 // ---- split path for narrow batches (compensated fp32 on CUDA cores) ----
 
 // y[i] = (float)x[i], i < n.
