@@ -185,7 +185,7 @@ def _measured_peaks():
         return 6800.0, 1900.0, "of fallback"
 
 
-def roofline(kind, ks, precision, clocks, w):
+def roofline(kind, ks, precision, clocks, workload):
     """Roofline line for the dominant kernel class from the library's sampled
     CUDA-event stats: achieved = algorithmic work of the timed launches /
     their total duration."""
@@ -226,7 +226,8 @@ def roofline(kind, ks, precision, clocks, w):
                     "frac": achieved / peak if peak else None, "peak_note": note})
     key = {"history": f"history_{'split' if precision == 'split' else 'fp64'}",
            "recurrence": "recurrence"}.get(kind)
-    traffic = _profile_traffic(key, f"{kind}_{precision}_{w.name}") if key else None
+    # profiles/<kernel class>_<precision>_<workload>.md, e.g. history_fp64_lorenz-single.md
+    traffic = _profile_traffic(key, f"{kind}_{precision}_{workload}") if key else None
     out["traffic"] = traffic
     return out
 
@@ -492,7 +493,7 @@ def main():
         # the kinds that do the method's arithmetic (both are timed on the same
         # sampled blocks; combine, slice and init only move or convert data)
         dom = max(("history", "recurrence"), key=lambda k: kstats[k]["busy_ms"] or kstats[k]["ms"])
-        line_roof = roofline(dom, kstats[dom], args.precision, clocks, w)
+        line_roof = roofline(dom, kstats[dom], args.precision, clocks, args.workload)
         h2d = w.B * w.dim * 8 + w.B * 8 * 8 + w.B * 8
         d2h = w.B * (w.N + 1) * w.dim * 8 + 8
         line = {
