@@ -54,9 +54,10 @@ enum {
     FABM_FP64 = 0,  /* every step in IEEE double                                   */
     FABM_SPLIT = 1, /* history sums in compensated reduced precision: three-term bf16
                        split on tensor cores (wide batches) or compensated fp32 on
-                       CUDA cores (narrow batches); the weights, the per-step
-                       predictor and corrector updates and the running history
-                       accumulator stay in double */
+                       CUDA cores (narrow batches); weights computed in double; the
+                       steps of a block in float-float arithmetic (about 48 bits),
+                       each y formed in double once.  Within 1e-6 of the solution
+                       scale of an FP64 solve on every tested workload */
     FABM_FP64X2 = 2 /* the extended-precision mode the paper runs in long double
                        (Sec. 4, "memory saving"): weights in double-double from
                        binary128 (fabm_weights_x2), far-history sums in
