@@ -115,6 +115,7 @@ struct fabm_solver {
     int64_t g_max = 0;
     // per-batch workspace
     DevBuf<double> F, Ystage, G, part, y0, par;
+    DevBuf<float> Ff;          // compensated-fp32 history: f rounded to float
     DevBuf<__nv_bfloat16> Fs;  // split: f slices
     DevBuf<int> Fe;            // split: f exponents
     DevBuf<float2> spart;      // split: float-float partials
@@ -161,7 +162,7 @@ struct fabm_solver {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
         wBl.release(), wAl.release(), wDl.release();
         wBf.release(), wAf.release(), wBff.release(), wAff.release(), wDff.release();
-        F.release(), Ystage.release(), G.release(), part.release();
+        F.release(), Ff.release(), Ystage.release(), G.release(), part.release();
         Fs.release(), Fe.release(), spart.release(), auxb.release(), err.release();
         y0.release(), par.release(), nEach.release(), status.release();
         for (auto &e : evR)
@@ -522,7 +523,10 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     // two partial buffers: the history launches of blocks c and c+1 may overlap
     if (hk == FABM_HIST_FP64) FABM_CUDA_TRY(s->part.ensure((size_t)2 * max_chunks * part_per_chunk));
     if (hk == FABM_HIST_X2) FABM_CUDA_TRY(s->part.ensure((size_t)4 * max_chunks * part_per_chunk));
-    if (hk == FABM_HIST_FP32C) FABM_CUDA_TRY(s->spart.ensure((size_t)2 * max_chunks * part_per_chunk));
+    if (hk == FABM_HIST_FP32C) {
+        FABM_CUDA_TRY(s->spart.ensure((size_t)2 * max_chunks * part_per_chunk));
+        FABM_CUDA_TRY(s->Ff.ensure(f_elems));
+    }
     FABM_CUDA_TRY(s->y0.ensure((size_t)B * dim * 2));  // y0, then y1
     FABM_CUDA_TRY(s->par.ensure((size_t)B * kMaxParams));
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
@@ -611,6 +615,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     bt.y1 = s->alpha > 1.0 ? s->y0.p + B * dim : nullptr;
     bt.params = s->par.p;
     bt.F = s->F.p;
+    bt.Ff = hk == FABM_HIST_FP32C ? s->Ff.p : nullptr;
     bt.ldF = cols;
     bt.Y = Y;
     bt.status = s->status.p;
@@ -620,7 +625,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)B, (uintptr_t)nblk, (uintptr_t)L, (uintptr_t)s->timing,
         (uintptr_t)s->timing_period, (uintptr_t)hk, (uintptr_t)s->chunk_ctas,
         (uintptr_t)(s->sm_reserve + 1), (uintptr_t)s->cols_warps, (uintptr_t)Y,
-        (uintptr_t)s->F.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
+        (uintptr_t)s->F.p, (uintptr_t)s->Ff.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
         (uintptr_t)s->out_stream, (uintptr_t)s->out_group};

@@ -57,6 +57,8 @@ struct DevBatch {
                            // tensor-history path each slot holds a float-float
                            // pair (float2) instead of a double
     int64_t ldF;           // row stride of F (>= cols)
+    float *Ff;             // compensated-fp32 history path: f rounded to float, same
+                           // layout as F (written by the split recurrence), or NULL
     double *Y;             // output, B x (N+1) x dim (trajectory-major)
     unsigned long long *status;  // [0] = first non-finite (step << 24 | traj), ~0 if none
 };

@@ -96,16 +96,22 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
 }
 
 // One CTA of 32 * kHistCols threads: chunk `chunk` of the far history of
-// block c for the columns col0 .. col0+3, in compensated fp32.
+// block c for the columns col0 .. col0+3, in compensated fp32.  Ff: f rounded
+// to float (same layout as F), read instead of converting F when not NULL.
+// The next tile's f and weights are loaded into registers while the current
+// tile is summed, so the staging latency hides behind the arithmetic.
 // MULTI as for hist_fp64_block.
 template <bool MULTI = false>
-__device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ldF, int cols,
-                                        const float *__restrict__ WB,
+__device__ inline void hist_fp32c_block(const double *__restrict__ F, const float *__restrict__ Ff,
+                                        int64_t ldF, int cols, const float *__restrict__ WB,
                                         const float *__restrict__ WA, int64_t c, int64_t kc,
                                         int64_t k_end, float2 *__restrict__ part, int64_t chunk,
                                         int col0, int64_t wstride = 0, int dim = 1)
 {
     constexpr int NW = MULTI ? kColsPerCta : 1;  // weight windows
+    constexpr int kThreads = kWarp * kColsPerCta;
+    constexpr int kRF = kTile * kColsPerCta / kThreads;            // f values per thread
+    constexpr int kRW = (NW * (kTile + kL) + kThreads - 1) / kThreads;  // weights per thread and kind
     __shared__ float sF[kTile * kColsPerCta];
     __shared__ float sB[NW][kTile + kL], sA[NW][kTile + kL];
     const int64_t k0 = chunk * kc;
@@ -114,31 +120,50 @@ __device__ inline void hist_fp32c_block(const double *__restrict__ F, int64_t ld
     const int w = threadIdx.x / kWarp;
     const int a = threadIdx.x % kWarp;  // target m = cL+1+a
     float sp = 0.f, cp = 0.f, sc = 0.f, cc = 0.f;
+    float rf[kRF], rb[kRW], ra[kRW];
 
+    // the tile starting at t0 into registers: window index i <-> d = cL+2-t1 + i
+    auto fetch = [&](int64_t t0) {
+        const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
+        const int nk = (int)(t1 - t0), nwin = nk + kL - 1;
+        const int64_t d_min = c * kL + 2 - t1;
+#pragma unroll
+        for (int u = 0; u < kRW; ++u) {
+            const int i = threadIdx.x + u * kThreads;
+            const int v = MULTI ? i / nwin : 0, ii = MULTI ? i % nwin : i;
+            const bool in = MULTI ? i < NW * nwin : i < nwin;
+            const int64_t o = MULTI ? (int64_t)((col0 + v) % dim) * wstride : 0;
+            rb[u] = in ? WB[o + d_min + ii] : 0.f;
+            ra[u] = in ? WA[o + d_min + ii] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kRF; ++u) {
+            const int i = threadIdx.x + u * kThreads;
+            const int k = i / kColsPerCta, j = i % kColsPerCta;
+            float f = 0.f;
+            if (k < nk && j < ncol)
+                f = Ff ? Ff[(t0 + k) * ldF + col0 + j] : (float)F[(t0 + k) * ldF + col0 + j];
+            rf[u] = f;
+        }
+    };
+
+    if (k0 < k1) fetch(k0);
     for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
         const int64_t t1 = t0 + kTile < k1 ? t0 + kTile : k1;
-        const int nk = (int)(t1 - t0);
-        // window index i <-> d = cL+2-t1 + i (see the double kernel)
-        const int64_t d_min = c * kL + 2 - t1;
-        const int nwin = nk + kL - 1;
-        if constexpr (MULTI) {
-            for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
-                const int v = i / nwin, ii = i % nwin;
-                const int64_t o = (int64_t)((col0 + v) % dim) * wstride;
-                sB[v][ii] = WB[o + d_min + ii];
-                sA[v][ii] = WA[o + d_min + ii];
-            }
-        } else {
-            for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
-                sB[0][i] = WB[d_min + i];
-                sA[0][i] = WA[d_min + i];
+        const int nk = (int)(t1 - t0), nwin = nk + kL - 1;
+#pragma unroll
+        for (int u = 0; u < kRW; ++u) {
+            const int i = threadIdx.x + u * kThreads;
+            if (MULTI ? i < NW * nwin : i < nwin) {
+                const int v = MULTI ? i / nwin : 0, ii = MULTI ? i % nwin : i;
+                sB[v][ii] = rb[u];
+                sA[v][ii] = ra[u];
             }
         }
-        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
-            const int k = i / kColsPerCta, j = i % kColsPerCta;
-            sF[i] = j < ncol ? (float)F[(t0 + k) * ldF + col0 + j] : 0.f;
-        }
+#pragma unroll
+        for (int u = 0; u < kRF; ++u) sF[threadIdx.x + u * kThreads] = rf[u];
         __syncthreads();
+        if (t1 < k1) fetch(t1);  // next tile in flight during the sums below
         if (w < ncol) {
             const float *fb = sF + w;
             const float *wb = sB[MULTI ? w : 0], *wa = sA[MULTI ? w : 0];

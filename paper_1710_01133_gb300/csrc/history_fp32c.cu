@@ -4,8 +4,8 @@
 // chunks, like the double-precision kernel but in fp32, which GB300 runs at
 // 64 times the double rate.
 //
-// f (staged from the double history) and the weights are rounded to fp32
-// (2^-24 relative); each thread adds 16 products in plain fp32 and folds the
+// f (the recurrence's float copy of the double history) and the weights are
+// in fp32 (2^-24 relative); each thread adds 16 products in plain fp32 and folds the
 // group into a Kahan-compensated fp32 sum, so the rounding of a chunk's sum
 // stays within a few units of 2^-24 of its magnitude.  Each chunk writes
 // (sum, -compensation) pairs that the float-float combine adds up in a fixed
@@ -20,12 +20,12 @@ namespace {
 // grid = (n_chunks, ceil(cols / kColsPerCta)); block = 32 * kColsPerCta.
 template <bool MULTI>
 __global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
-    hist_fp32c_kernel(const double *__restrict__ F, int64_t ldF, int cols,
-                      const float *__restrict__ WB, const float *__restrict__ WA, int64_t c,
-                      int64_t kc, int64_t k_end, float2 *__restrict__ part, int64_t wstride,
-                      int dim)
+    hist_fp32c_kernel(const double *__restrict__ F, const float *__restrict__ Ff, int64_t ldF,
+                      int cols, const float *__restrict__ WB, const float *__restrict__ WA,
+                      int64_t c, int64_t kc, int64_t k_end, float2 *__restrict__ part,
+                      int64_t wstride, int dim)
 {
-    hist::f32c::hist_fp32c_block<MULTI>(F, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
+    hist::f32c::hist_fp32c_block<MULTI>(F, Ff, ldF, cols, WB, WA, c, kc, k_end, part, blockIdx.x,
                                         blockIdx.y * hist::kColsPerCta, wstride, dim);
 }
 
@@ -56,10 +56,10 @@ cudaError_t launch_hist_fp32c(const DevBatch &bt, const float *WBf, const float 
     dim3 grid((unsigned)n_chunks, (unsigned)((bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta));
     if (wstride)
         hist_fp32c_kernel<true><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
-            bt.F, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, wstride, bt.dim);
+            bt.F, bt.Ff, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, wstride, bt.dim);
     else
         hist_fp32c_kernel<false><<<grid, kWarp * hist::kColsPerCta, 0, st>>>(
-            bt.F, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, 0, 1);
+            bt.F, bt.Ff, bt.ldF, bt.cols, WBf, WAf, c, kc, k_end, part, 0, 1);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,7 @@ __device__ inline void init_one(const DevBatch &bt, int b, bool f_pairs = false)
         } else {
             bt.F[(int64_t)b * D + i] = f;
         }
+        if (bt.Ff) bt.Ff[(int64_t)b * D + i] = (float)f;
         ok = ok && finite_bits(y[i]) && finite_bits(f);
     }
     if (!ok) report_nonfinite(bt.status, 0, b);
@@ -373,6 +374,7 @@ __device__ void recur_block_split(const DevBatch &bt, int b, const DevWeights &w
                 const double fd = ff_to_double(fo[t]);
                 Yb[mm * D + i] = yc;
                 bt.F[mm * bt.ldF + col] = fd;
+                if (bt.Ff) bt.Ff[mm * bt.ldF + col] = (float)fd;  // the fp32 history's input
                 if (!(finite_bits(yc) && finite_bits(fd))) report_nonfinite(bt.status, mm, b);
             }
         }

@@ -45,7 +45,7 @@ struct SlotDev {
     int64_t N, w_ext;
     int64_t *Nb;  // device copy of N (read by the recurrence)
     double *F, *Y, *y0, *params, *WB, *WA, *WD, *G;
-    float *WBf, *WAf;
+    float *WBf, *WAf, *Ff;  // split slots: fp32 weights and f rounded to float
     void *part;  // double (FP64) or float2 (split) partials
     StepConsts kc;
     double alpha, inv_g1;
@@ -72,6 +72,7 @@ __device__ inline DevBatch slot_batch(const SlotDev &s)
     bt.y0 = s.y0;
     bt.params = s.params;
     bt.F = s.F;
+    bt.Ff = s.Ff;
     bt.ldF = s.dim;
     bt.Y = s.Y;
     bt.status = s.status;
@@ -177,18 +178,44 @@ __device__ void hist_warp_f32c(const SlotDev &s, const Item &it, float *sF, floa
 {
     using hist::kL;
     constexpr int kT = hist::f32c::kTile, kG = hist::f32c::kGroup;
+    constexpr int kRF = kT / kWarp, kRW = (kT + kL + kWarp - 1) / kWarp;
     const int a = threadIdx.x % kWarp, q = it.pad, dim = s.dim;
     const int64_t k_end = (it.c - 1) * kSL;
     const int64_t k0 = (int64_t)it.chunk * it.kc;
     const int64_t k1 = k0 + it.kc < k_end ? k0 + it.kc : k_end;
     float sp = 0.f, cp = 0.f, sc = 0.f, cc = 0.f;
-    for (int64_t t0 = k0; t0 < k1; t0 += kT) {
+    // the next tile's f (the recurrence's float copy) and weights are loaded
+    // into registers while the current tile is summed
+    float rf[kRF], rb[kRW], ra[kRW];
+    auto fetch = [&](int64_t t0) {
         const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
         const int nk = (int)(t1 - t0);
         const int64_t d_min = it.c * kL + 2 - t1;
-        for (int i = a; i < nk + kL - 1; i += kWarp) sB[i] = s.WBf[d_min + i], sA[i] = s.WAf[d_min + i];
-        for (int i = a; i < nk; i += kWarp) sF[i] = (float)s.F[(t0 + i) * dim + q];
+#pragma unroll
+        for (int u = 0; u < kRW; ++u) {
+            const int i = a + u * kWarp;
+            rb[u] = i < nk + kL - 1 ? s.WBf[d_min + i] : 0.f;
+            ra[u] = i < nk + kL - 1 ? s.WAf[d_min + i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kRF; ++u) {
+            const int i = a + u * kWarp;
+            rf[u] = i < nk ? s.Ff[(t0 + i) * dim + q] : 0.f;
+        }
+    };
+    if (k0 < k1) fetch(k0);
+    for (int64_t t0 = k0; t0 < k1; t0 += kT) {
+        const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
+        const int nk = (int)(t1 - t0);
+#pragma unroll
+        for (int u = 0; u < kRW; ++u) {
+            const int i = a + u * kWarp;
+            if (i < nk + kL - 1) sB[i] = rb[u], sA[i] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kRF; ++u) sF[a + u * kWarp] = rf[u];
         __syncwarp();
+        if (t1 < k1) fetch(t1);
         const int base = a + nk - 1;
         int j = 0;
         for (; j + kG <= nk; j += kG) {
@@ -376,8 +403,10 @@ size_t slot_bytes(const Req &r, int hk, int64_t *w_ext_out)
     add(sizeof(double) * FABM_MAX_DIM);                     // y0
     add(sizeof(double) * kMaxParams);                       // params
     for (int i = 0; i < 3; ++i) add(sizeof(double) * (w_ext + 1));  // WB WA WD
-    if (hk == FABM_HIST_FP32C)
+    if (hk == FABM_HIST_FP32C) {
         for (int i = 0; i < 2; ++i) add(sizeof(float) * (w_ext + 1));
+        add(sizeof(float) * (r.N + 1) * r.dim);             // Ff
+    }
     add(sizeof(double) * (r.N + 1) * r.dim);                // F
     add(sizeof(double) * (r.N + 1) * r.dim);                // Y
     add(sizeof(double) * 2 * 2 * kSL * r.dim);              // G
@@ -404,10 +433,11 @@ void slot_layout(Slot &s, int hk, int64_t w_ext)
     d.WB = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
     d.WA = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
     d.WD = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
-    d.WBf = d.WAf = nullptr;
+    d.WBf = d.WAf = d.Ff = nullptr;
     if (hk == FABM_HIST_FP32C) {
         d.WBf = reinterpret_cast<float *>(take(sizeof(float) * (w_ext + 1)));
         d.WAf = reinterpret_cast<float *>(take(sizeof(float) * (w_ext + 1)));
+        d.Ff = reinterpret_cast<float *>(take(sizeof(float) * (r.N + 1) * r.dim));
     }
     d.F = reinterpret_cast<double *>(take(sizeof(double) * (r.N + 1) * r.dim));
     d.Y = reinterpret_cast<double *>(take(sizeof(double) * (r.N + 1) * r.dim));
@@ -572,6 +602,8 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             if (const Ckpt *k = s.req.ckpt.get()) {  // resumed: the saved state
                 const size_t rows = k->F.size() / s.req.dim;
                 SRV_TRY(cudaMemcpyAsync(s.dev.F, k->F.data(), sizeof(double) * rows * s.req.dim, cudaMemcpyHostToDevice, S->sR));
+                if (s.dev.Ff)  // the float copy the fp32 history reads
+                    SRV_TRY(launch_to_float(s.dev.F, (int64_t)(rows * s.req.dim), s.dev.Ff, S->sR));
                 SRV_TRY(cudaMemcpyAsync(s.dev.Y, k->Y.data(), sizeof(double) * rows * s.req.dim, cudaMemcpyHostToDevice, S->sR));
                 SRV_TRY(cudaMemcpyAsync(s.dev.G, k->G.data(), sizeof(double) * k->G.size(), cudaMemcpyHostToDevice, S->sR));
                 SRV_TRY(cudaMemcpyAsync(s.dev.status, &k->status, sizeof k->status, cudaMemcpyHostToDevice, S->sR));
