@@ -329,6 +329,10 @@ fabm_status fabm_server_poll(fabm_server *s, int64_t ticket, int *state);
  * FABM_EBUSY if it has not finished; the request's own error if it failed
  * (FABM_ENONFINITE, or FABM_ENOMEM when it can never fit the budget). */
 fabm_status fabm_server_result(fabm_server *s, int64_t ticket, double *out);
+/* Step the server (fabm_server_step, advancing every admitted request) until
+ * the request has finished, then fabm_server_result into out.  Errors as
+ * fabm_server_result, or a step's error; FABM_EINVAL for an unknown ticket. */
+fabm_status fabm_server_wait(fabm_server *s, int64_t ticket, double *out);
 /* Checkpoint of a waiting or running request at the current block boundary:
  * its problem, the index of the next block, the history f and solution rows
  * computed so far, the far-history sums of the next block and its status,

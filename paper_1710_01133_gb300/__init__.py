@@ -31,7 +31,8 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_stroboscope", "fabm_server_checkpoint", "fabm_server_resume",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
-            "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2")
+            "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
+            "fabm_server_wait")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
     lib.fabm_server_step.argtypes = [vp, P(i), P(i)]
     lib.fabm_server_poll.argtypes = [vp, i64, P(i)]
     lib.fabm_server_result.argtypes = [vp, i64, P(d)]
+    lib.fabm_server_wait.argtypes = [vp, i64, P(d)]
     lib.fabm_server_stats.argtypes = [vp, P(i64), P(i64), P(ctypes.c_size_t)]
     lib.fabm_server_destroy.argtypes = [vp]
     lib.fabm_server_checkpoint.argtypes = [vp, i64, vp, ctypes.c_size_t, P(ctypes.c_size_t)]
@@ -96,7 +98,7 @@ def load(build_if_missing: bool = True):
     lib.fabm_server_shape.argtypes = [vp, i64, P(i64), P(i)]
     lib.fabm_server_finished.argtypes = [vp, P(i64), i, P(i)]
     for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
-              "fabm_server_result", "fabm_server_stats", "fabm_server_destroy",
+              "fabm_server_result", "fabm_server_wait", "fabm_server_stats", "fabm_server_destroy",
               "fabm_server_checkpoint", "fabm_server_resume", "fabm_server_cancel",
               "fabm_server_shape", "fabm_server_finished"):
         getattr(lib, f).restype = i
@@ -470,6 +472,13 @@ class Server:
         N, dim = self.shape(ticket)
         out = np.empty((N + 1, dim))
         _check(load().fabm_server_result(self.handle, int(ticket), _dp(out)))
+        return out
+
+    def wait(self, ticket) -> np.ndarray:
+        """Step the server until the request has finished; its (N+1, dim) result."""
+        N, dim = self.shape(ticket)
+        out = np.empty((N + 1, dim))
+        _check(load().fabm_server_wait(self.handle, int(ticket), _dp(out)))
         return out
 
     def checkpoint(self, ticket) -> bytes:

@@ -779,6 +779,21 @@ fabm_status fabm_server_result(fabm_server *S, int64_t ticket, double *out)
     return FABM_OK;
 }
 
+fabm_status fabm_server_wait(fabm_server *S, int64_t ticket, double *out)
+{
+    set_last_error("");
+    if (!S || !out) return srv_fail(FABM_EINVAL, "NULL argument");
+    for (;;) {
+        int state = 0;
+        const fabm_status st = fabm_server_poll(S, ticket, &state);
+        if (st != FABM_OK) return st;
+        if (state == FABM_REQ_DONE || state == FABM_REQ_FAILED) break;
+        const fabm_status ss = fabm_server_step(S, nullptr, nullptr);
+        if (ss != FABM_OK) return ss;
+    }
+    return fabm_server_result(S, ticket, out);
+}
+
 fabm_status fabm_server_checkpoint(fabm_server *S, int64_t ticket, void *buf, size_t cap,
                                    size_t *size)
 {

@@ -206,6 +206,25 @@ def test_checkpoint_errors(gpu_lib):
         assert e.value.status == gpu_lib.FABM_EINVAL
 
 
+def test_wait_steps_until_the_request_finishes(gpu_lib, parity):
+    """fabm_server_wait on one request of a mix: the others advance with it and
+    stay correct; a failed request reports its error; unknown tickets fail."""
+    with gpu_lib.Server(8 << 30) as srv:
+        tickets = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX]
+        got = srv.wait(tickets[1])                     # linear, 1000 steps
+        assert srv.poll(tickets[0]) == gpu_lib.FABM_REQ_RUNNING   # lorenz, 3000 steps
+        rest = [srv.wait(t) for t in tickets[2:]] + [srv.wait(tickets[0])]
+        with pytest.raises(gpu_lib.FabmError):
+            srv.wait(tickets[1])                       # already collected
+        bad = srv.submit("linear", 1, 0.9, 0.1, 5000, [1.0], (-50.0,))
+        with pytest.raises(gpu_lib.FabmError) as e:
+            srv.wait(bad)
+        assert e.value.status == gpu_lib.FABM_ENONFINITE
+    r, d, a, h, N, y0, p = MIX[1]
+    parity(rel_err(got, oracle.solve(r, a, h, N, y0, params=p)), 1e-12, "wait")
+    assert rest[-1].shape == (MIX[0][4] + 1, 3)
+
+
 def test_finished_lists_each_request_once(gpu_lib):
     with gpu_lib.Server(8 << 30) as srv:
         tickets = [srv.submit(r, d, a, h, N, y0, p) for r, d, a, h, N, y0, p in MIX]
