@@ -253,11 +253,23 @@ def cpu_baseline(w, target_s=12.0):
                        traj_params=sub.traj_params, threads=ntraj)
     dt = time.perf_counter() - t0
     full_time = dt * (w.N / n) ** 2 * (w.B / ntraj)
-    return {"value": w.steps_traj() / full_time, "unit": "steps*traj/s", "cores": ntraj,
+    line = {"value": w.steps_traj() / full_time, "unit": "steps*traj/s", "cores": ntraj,
             "kind": "oracle",
             "sample": f"{ntraj} trajectory(ies) x first {n} of {w.N} steps in {dt:.2f} s, "
                       f"extrapolated to {w.B} x {w.N} by N^2 (host has {cores} cores)",
             "history_gmac_s": w.history_macs() / full_time / 1e9}
+    if w.B == 1 and np.ndim(w.alpha) == 0 and w.alpha <= 1.0 and cores > 1:
+        # the paper's Alg. 2 layout for reference: the k-sums of every step split
+        # over the host's threads, same sample
+        threads = min(cores, 16)
+        t0 = time.perf_counter()
+        oracle.solve_threaded(sub.rhs, sub.alpha, sub.h, n, sub.y0[0], params=sub.params,
+                              threads=threads)
+        dtt = time.perf_counter() - t0
+        ft = dtt * (w.N / n) ** 2
+        line["threaded_k"] = {"value": w.steps_traj() / ft, "threads": threads,
+                              "sample": f"first {n} steps in {dtt:.2f} s, extrapolated by N^2"}
+    return line
 
 
 def run_reference(args, w):

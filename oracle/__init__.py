@@ -61,6 +61,7 @@ def _load():
         lib.fabm_oracle_constants.argtypes = [d, d, P(d), P(d)]
         lib.fabm_oracle_rhs.argtypes = [i, i, d, P(d), P(d), i, P(d)]
         lib.fabm_oracle_solve.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), P(d), i]
+        lib.fabm_oracle_solve_threaded.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), i]
         lib.fabm_oracle_solve_w.argtypes = [i, d, i64, i, P(d), i, P(d), P(d), P(d), d, d,
                                             P(d), P(d), P(d), i]
         lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d), P(d),
@@ -148,6 +149,19 @@ def solve(name: str, alpha, h: float, N: int, y0, params=None,
     out = np.empty((N + 1, y0.size))
     _check(_load().fabm_oracle_solve(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
                                      _dp(y1), _dp(out), int(compensated)), "solve")
+    return out
+
+
+def solve_threaded(name: str, alpha: float, h: float, N: int, y0, params=None,
+                   threads: int = 4):
+    """One trajectory (0 < alpha <= 1) with every step's k-sums split over
+    `threads` threads (the paper's Alg. 2 layout); a timing reference, equal to
+    solve() up to the order of the additions."""
+    y0 = _f64(y0).reshape(-1)
+    rid, p = _rhs(name, y0.size, params)
+    out = np.empty((N + 1, y0.size))
+    _check(_load().fabm_oracle_solve_threaded(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
+                                              _dp(out), int(threads)), "solve_threaded")
     return out
 
 

@@ -306,6 +306,127 @@ int fabm_oracle_solve(int dim, double alpha, double h, int64_t N, int rhs, const
     return st;
 }
 
+/* ------------------------------------------- threaded k-reduction --- */
+
+/* A timing reference only (the CPU baseline's "Alg. 2" leg): one trajectory
+ * with the k-sums of every step split over T threads, as the paper's
+ * MPI+OpenMP version splits the history index over the threads of a node
+ * (Alg. 2).  Thread t sums the contiguous share t of k = 0..n (compensated),
+ * thread 0 adds the T partial sums in thread order with TwoSum and takes the
+ * step; two barriers per step.  The result equals fabm_oracle_solve's up to
+ * the order of the additions (the tests check 1e-13 of the solution scale). */
+typedef struct {
+    int dim, rhs, tid, nthreads;
+    double h, h_alpha, inv_gamma2;
+    int64_t N;
+    const double *p, *w, *y0;
+    double *out, *fw, *part; /* part[tid][2][dim]: predictor then corrector partials */
+    pthread_barrier_t *bar;
+    /* start gate: the workers run only once every thread has been created */
+    pthread_mutex_t *mu;
+    pthread_cond_t *cv;
+    int *go, *ok;
+} orc_thr_job;
+
+static void *orc_thr_worker(void *arg)
+{
+    orc_thr_job *j = (orc_thr_job *)arg;
+    pthread_mutex_lock(j->mu);
+    while (!*j->go) pthread_cond_wait(j->cv, j->mu);
+    const int ok = *j->ok;
+    pthread_mutex_unlock(j->mu);
+    if (!ok) return NULL;
+    const int dim = j->dim, T = j->nthreads;
+    const double *b = j->w, *a = j->w + j->N, *c = j->w + 2 * j->N;
+    double yp[8], fpv[8], yc[8];
+    for (int64_t n = 0; n < j->N; ++n) {
+        const int64_t k0 = (n + 1) * j->tid / T, k1 = (n + 1) * (j->tid + 1) / T - 1;
+        double *mine = j->part + (size_t)j->tid * 2 * dim;
+        for (int i = 0; i < dim; ++i) {
+            mine[i] = orc_hist_dot(b, n, j->fw + i, dim, k0, k1, 1);
+            /* corrector: k = 1..n (k = 0 carries c_n, added by thread 0) */
+            mine[dim + i] = orc_hist_dot(a, n, j->fw + i, dim, k0 > 1 ? k0 : 1, k1, 1);
+        }
+        pthread_barrier_wait(j->bar);
+        if (j->tid == 0) {
+            const double t1 = (double)(n + 1) * j->h;
+            for (int i = 0; i < dim; ++i) {
+                double s = 0.0, e = 0.0;
+                for (int t = 0; t < T; ++t) {
+                    double q;
+                    two_sum(s, j->part[(size_t)t * 2 * dim + i], &s, &q);
+                    e += q;
+                }
+                yp[i] = j->y0[i] + j->h_alpha * (s + e);
+            }
+            orc_rhs(j->rhs, dim, t1, yp, j->p, fpv);
+            for (int i = 0; i < dim; ++i) {
+                double pr = c[n] * j->fw[i], s = pr, e = fma(c[n], j->fw[i], -pr);
+                for (int t = 0; t < T; ++t) {
+                    double q;
+                    two_sum(s, j->part[(size_t)t * 2 * dim + dim + i], &s, &q);
+                    e += q;
+                }
+                yc[i] = j->y0[i] + j->h_alpha * ((s + e) + fpv[i] * j->inv_gamma2);
+                j->out[(n + 1) * dim + i] = yc[i];
+            }
+            orc_rhs(j->rhs, dim, t1, yc, j->p, j->fw + (n + 1) * dim);
+        }
+        pthread_barrier_wait(j->bar);
+    }
+    return NULL;
+}
+
+/* One trajectory (0 < alpha <= 1) with the k-sums split over n_threads threads;
+ * the threads are started once and meet at two barriers per step. */
+int fabm_oracle_solve_threaded(int dim, double alpha, double h, int64_t N, int rhs,
+                               const double *params, int n_params, const double *y0, double *out,
+                               int n_threads)
+{
+    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !(alpha > 0.0 && alpha <= 1.0) ||
+        n_threads < 1 || n_threads > 256 || !orc_rhs_dim_ok(rhs, dim, n_params))
+        return ORC_EINVAL;
+    double *w = (double *)malloc((size_t)3 * N * sizeof(double));
+    double *fw = (double *)malloc((size_t)(N + 1) * dim * sizeof(double));
+    double *part = (double *)malloc((size_t)n_threads * 2 * dim * sizeof(double));
+    orc_thr_job *jobs = (orc_thr_job *)malloc(sizeof(orc_thr_job) * (size_t)n_threads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    int st = (w && fw && part && jobs && th) ? ORC_OK : ORC_ENOMEM;
+    double ha = 0.0, ig2 = 0.0;
+    if (st == ORC_OK) st = fabm_oracle_weights(alpha, N, w, w + N, w + 2 * N);
+    if (st == ORC_OK) st = fabm_oracle_constants(alpha, h, &ha, &ig2);
+    pthread_barrier_t bar;
+    pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+    pthread_cond_t cv = PTHREAD_COND_INITIALIZER;
+    int go = 0, ok = 0;
+    if (st == ORC_OK && pthread_barrier_init(&bar, NULL, (unsigned)n_threads) != 0) st = ORC_ENOMEM;
+    if (st == ORC_OK) {
+        for (int i = 0; i < dim; ++i) out[i] = y0[i];
+        orc_rhs(rhs, dim, 0.0, y0, params, fw);
+        int started = 0;
+        for (int t = 0; t < n_threads; ++t) {
+            jobs[t] = (orc_thr_job){dim, rhs, t, n_threads, h, ha, ig2, N, params, w, y0, out, fw,
+                                    part, &bar, &mu, &cv, &go, &ok};
+            if (t > 0) {
+                if (pthread_create(&th[t], NULL, orc_thr_worker, &jobs[t]) != 0) break;
+                ++started;
+            }
+        }
+        /* open the gate: run if every thread exists, else let the started ones return */
+        pthread_mutex_lock(&mu);
+        ok = started == n_threads - 1;
+        go = 1;
+        pthread_cond_broadcast(&cv);
+        pthread_mutex_unlock(&mu);
+        if (ok) orc_thr_worker(&jobs[0]);
+        else st = ORC_ENOMEM;
+        for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+        pthread_barrier_destroy(&bar);
+    }
+    free(w), free(fw), free(part), free(jobs), free(th);
+    return st;
+}
+
 /* ------------------------------------------------------------- batches --- */
 
 typedef struct {

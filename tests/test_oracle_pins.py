@@ -465,3 +465,18 @@ def test_multi_order_lcr_equilibria():
     for E in ([x, yv], [-x, -yv]):
         traj = oracle.solve("lcr", [0.9, 0.7], 0.01, 300, E, params=[s, g["omega"], a, b, 0.0])
         assert np.max(np.abs(traj - np.array(E))) < 1e-12
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_k_reduction_equals_the_sequential_oracle(threads):
+    """The Alg. 2-style timing variant splits every step's k-sums over threads:
+    one thread reproduces the sequential oracle bit for bit, more threads
+    change only the order of the additions."""
+    w = lorenz_single(N=1500)
+    ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    got = oracle.solve_threaded(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params,
+                                threads=threads)
+    if threads == 1:
+        assert np.array_equal(got, ref)
+    scale = np.max(np.abs(ref), axis=0)
+    assert np.max(np.abs(got - ref) / scale) < 1e-13
