@@ -153,11 +153,38 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_tokens(src: str) -> str:
+    """The source without comments and with whitespace collapsed, so that only
+    code changes change a kernel's hash (string and character literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        ch = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif ch in "\"'":
+            j = i + 1
+            while j < n and src[j] != ch:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(ch)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_sha(key: str) -> str:
+    """sha256 over the code (comments and whitespace removed) of the files a
+    kernel class is built from."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[key]:
-        with open(os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1710_01133_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_tokens(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -1,7 +1,10 @@
-// a2 + a3 on tensor cores ("split" precision): the far part of the hereditary
-// sums of Sec. 2 of arXiv:1710.01133 as bf16 tcgen05 MMAs that are exact per
-// 64-point segment, accumulated across segments in compensated fp32 and
-// combined across CTAs in float-float, then rounded once to double.
+// a2 + a3 on tensor cores ("split" precision): the hereditary sums of Sec. 2
+// of arXiv:1710.01133 over every point before a 64-target block, as bf16
+// tcgen05 MMAs that are exact per 64-point segment, accumulated across
+// segments in compensated fp32 and combined across CTAs in float-float (kept
+// as float-float pairs for the recurrence).  Per block the kernel runs twice:
+// over the far segments beside the previous block's recurrence, and over the
+// newest segment once that recurrence has finished.
 //
 // Number format.  Time is cut into segments of kSeg = 64 points (one
 // recurrence block each).  For a segment and a column, f is written on a
