@@ -3,12 +3,20 @@
 //
 // Schedule of one solve (Sec. 2 of arXiv:1710.01133 evaluated block by block):
 //   init                      y_0, f_0
-//   for each block c of L targets:
+//   for each block c of L targets (CUDA-core history kernels, L = 32):
 //     stream G:  wait R(c-2); history(c) over k < (c-1)L; combine -> G[c%2]
-//     stream R:  wait G(c);   recurrence(c)
+//     stream R:  wait G(c);   recurrence(c), which adds the lag-1 block itself
+//   (long FP64 solves: lag 2, the history of consecutive blocks on two streams)
+//   tensor history, L = 64:
+//     stream G:  wait R(c-2); far history(c) over segments 0..c-2; wait N(c);
+//                combine of far and newest partials -> G[c%2] (float-float)
+//     stream R:  slice segment c-1; N(c): newest segment c-1; wait G(c);
+//                recurrence(c) over its own triangle only
+//     stream G2: forcing tables up to three blocks ahead
+//     stream C:  finished rows of y to pinned host memory (large outputs)
 // The history of block c+1 therefore runs while the recurrence of block c
-// runs; the recurrence adds the lag-1 block itself.  This replaces the
-// per-step MPI_Allreduce of the paper's Algorithm 1 by one hand-off per block.
+// runs.  This replaces the per-step MPI_Allreduce of the paper's Algorithm 1
+// by one hand-off per block.
 #include <cuda_runtime.h>
 
 #include <algorithm>
