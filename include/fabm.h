@@ -130,6 +130,10 @@ fabm_status fabm_solve(fabm_solver *s, const double *y0, double *out);
  *   out          B x (N+1) x dim doubles, trajectory-major; rows past N_each[b]
  *                are not written.  Host memory, or device memory (allocated by
  *                the caller on the solver's device) when out_on_device != 0.
+ *                Pinned host memory (cudaHostAlloc or registered) of 64 MB or
+ *                more, with every trajectory running to N, is filled while the
+ *                solve runs, group of blocks by group of blocks; other host
+ *                memory is filled once at the end.
  * Synchronous.  B = 0 is allowed and does nothing. */
 fabm_status fabm_solve_batch(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
                              const int64_t *N_each, double *out, int out_on_device);
