@@ -172,8 +172,8 @@ int fabm_get_history_kernel(const fabm_solver *s);
 /* Step layouts of the split-precision recurrence on the tensor-history path
  * (fabm_set_recurrence_layout); both compute the same steps in float-float. */
 enum {
-    FABM_REC_AUTO = 0,     /* COLUMNS when the batch has at least 152 warps of columns
-                              (152 * 32/dim trajectories) or N * columns >= 2^28
+    FABM_REC_AUTO = 0,     /* COLUMNS when the batch has at least 96 warps of columns
+                              (96 * 32/dim trajectories) or N * columns >= 2^28
                               (the history dominates), else TARGETS                 */
     FABM_REC_COLUMNS = 1,  /* one lane per column (trajectory, component), 32/dim
                               trajectories per warp: fewest instructions per step    */

@@ -549,7 +549,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         const int cwarps = recur_cols_warps(dim, B);
         const bool columns =
             s->rec_layout == FABM_REC_COLUMNS ||
-            (s->rec_layout == FABM_REC_AUTO && (cwarps >= 152 || (double)Nmax * cols >= 0x1p28));
+            (s->rec_layout == FABM_REC_AUTO && (cwarps >= 96 || (double)Nmax * cols >= 0x1p28));
         // leave SMs for the recurrence that runs beside the tensor kernel (one
         // tensor CTA fills an SM's register file), only where the column tiles
         // do not need every SM: one SM per 8 column warps, or per 12

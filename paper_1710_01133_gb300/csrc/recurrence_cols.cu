@@ -98,7 +98,9 @@ __global__ void finish_y_kernel(DevBatch bt, double h, int64_t m_lo, int64_t m_h
 // F: float-float pairs in the double-sized slots of bt.F; G: combined history
 // of block c, [2][64][cols] float-float pairs, or NULL for block 0; X: the
 // forcing table of block c ([64][B] pairs, aux_kernel) when Rhs::kForcing.
-template <class Rhs, int D>
+// Y1: bt.y1 is set (1 < alpha < 2, Taylor part y0 + t y'(0)); a template
+// parameter so that the solves without it carry no FP64 work per step.
+template <class Rhs, int D, bool Y1>
 __global__ void __launch_bounds__(kMaxWarps *kWarp)
     recur_cols_kernel(DevBatch bt, const float2 *__restrict__ WB, const float2 *__restrict__ WA,
                       const float2 *__restrict__ WD, StepConsts kc, int64_t c,
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
     // time-independent aux (a constant, or 0) once per lane
     const FF aux0 = Rhs::kForcing ? FF(0) : ff_from_double(Rhs::aux(0.0, p));
     const double y0 = bt.y0[bb * D + i];
-    const double y1 = bt.y1 ? bt.y1[bb * D + i] : 0.0;
+    const double y1 = Y1 ? bt.y1[bb * D + i] : 0.0;
     const FF T0 = ff_from_double(y0);
     const FF ha = ff_from_double(kc.h_alpha[0]);
     const FF ha_ig2 = ff_from_double(kc.h_alpha[0] * kc.inv_gamma2[0]);
@@ -177,7 +179,8 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
             if (a0 + r < wsteps) {  // uniform over the warp
                 const FF ax = Rhs::kForcing ? ld_ff(X + (int64_t)(a0 + r) * bt.B + bb) : aux0;
                 // Taylor part of the initial data: y0, or y0 + t y'(0) for 1 < alpha < 2
-                const FF T = bt.y1 ? ff_from_double(fma((double)(m0 + 1 + a0 + r) * kc.h, y1, y0)) : T0;
+                FF T = T0;
+                if constexpr (Y1) T = ff_from_double(fma((double)(m0 + 1 + a0 + r) * kc.h, y1, y0));
                 const FF yp = T + (bP[r] + ff_norm(accP[r]));
                 FF y[D];
 #pragma unroll
@@ -338,14 +341,17 @@ cudaError_t prepare_recur_cols(int rhs, int dim)
 {
     cudaError_t e = cudaSuccess;
     const bool ok = dispatch_rhs(rhs, dim, [&]<class R, int D>() {
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, recur_cols_kernel<R, D>);
-        if (e == cudaSuccess && fa.numRegs * kMaxWarps * kWarp > 65536)
-            e = cudaErrorInvalidConfiguration;
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(recur_cols_kernel<R, D>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)cols_smem_bytes(D, kMaxWarps));
+        auto prep = [&](auto kernel) {
+            cudaFuncAttributes fa;
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+            if (e == cudaSuccess && fa.numRegs * kMaxWarps * kWarp > 65536)
+                e = cudaErrorInvalidConfiguration;
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cols_smem_bytes(D, kMaxWarps));
+        };
+        prep(recur_cols_kernel<R, D, false>);
+        prep(recur_cols_kernel<R, D, true>);
     });
     return ok ? e : cudaErrorInvalidValue;
 }
@@ -368,8 +374,13 @@ cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, con
         }
         const int warps = recur_cols_warps(D, bt.B);
         const unsigned blocks = (unsigned)((warps + warps_per_cta - 1) / warps_per_cta);
-        recur_cols_kernel<R, D><<<blocks, warps_per_cta * kWarp, cols_smem_bytes(D, warps_per_cta),
-                                  st>>>(bt, WB, WA, WD, k, c, G, X);
+        const size_t smem = cols_smem_bytes(D, warps_per_cta);
+        if (bt.y1)
+            recur_cols_kernel<R, D, true><<<blocks, warps_per_cta * kWarp, smem, st>>>(
+                bt, WB, WA, WD, k, c, G, X);
+        else
+            recur_cols_kernel<R, D, false><<<blocks, warps_per_cta * kWarp, smem, st>>>(
+                bt, WB, WA, WD, k, c, G, X);
     });
     return ok && !(need_x && !X) ? cudaGetLastError() : cudaErrorInvalidValue;
 }

@@ -55,17 +55,20 @@ def test_oscillator_vs_oracle(gpu_lib, parity, precision, hist):
     parity(rel_err(got, ref), 1e-12 if precision == "fp64" else 1e-6, hist or "fp64")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "split"])
-def test_forced_oscillator_batch_above_one(gpu_lib, parity, precision):
+@pytest.mark.parametrize("precision,rec", [("fp64", None), ("split", "columns"),
+                                            ("split", "targets")])
+def test_forced_oscillator_batch_above_one(gpu_lib, parity, precision, rec):
     """A sweep of 300 forced oscillators at alpha = 1.3 with their own y'(0)
-    and uneven lengths (600 columns: tensor history in split precision)."""
+    and uneven lengths (600 columns: tensor history in split precision, both
+    recurrence layouts)."""
     w = duffing_sweep(B=300, N=1500)
     alpha = 1.3
     y0 = uniform(SEED_BASE + 71, 2 * w.B, -0.5, 0.5).reshape(w.B, 2)
     y1 = uniform(SEED_BASE + 72, 2 * w.B, -0.5, 0.5).reshape(w.B, 2)
     ne = np.full(w.B, w.N, dtype=np.int64)
     ne[::5] = 999
-    with gpu_lib.Solver(w.rhs, w.dim, alpha, w.h, w.N, w.params, precision=precision) as s:
+    with gpu_lib.Solver(w.rhs, w.dim, alpha, w.h, w.N, w.params, precision=precision,
+                        recurrence=rec) as s:
         got = s.solve_batch(y0, traj_params=w.traj_params, N_each=ne, y1=y1)
     idx = np.r_[0:6, 147:151, 294:300]
     ref = oracle.solve_batch(w.rhs, alpha, w.h, w.N, y0[idx], params=w.params,
