@@ -31,6 +31,7 @@
 
 #include "fabm_internal.cuh"
 #include "rhs.cuh"
+#include "trace.h"
 
 using namespace fabm;
 
@@ -894,6 +895,7 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
 fabm_status fabm_create(int dim, double alpha, double h, int64_t N, int rhs_id,
                         const double *params, int n_params, int precision, fabm_solver **out)
 {
+    TraceRange tr("fabm_create");
     double a[FABM_MAX_DIM] = {alpha, alpha, alpha, alpha};
     return create_solver(dim, a, h, N, rhs_id, params, n_params, precision, out);
 }
@@ -902,6 +904,7 @@ fabm_status fabm_create_multi(int dim, const double *alpha, double h, int64_t N,
                               const double *params, int n_params, int precision,
                               fabm_solver **out)
 {
+    TraceRange tr("fabm_create_multi");
     return create_solver(dim, alpha, h, N, rhs_id, params, n_params, precision, out);
 }
 
@@ -929,6 +932,7 @@ fabm_status fabm_solve_batch_ic(fabm_solver *s, int64_t B, const double *y0, con
             if (!std::isfinite(traj_params[i]))
                 return fail(FABM_EINVAL, "traj_params[%lld] is not finite", (long long)i);
     DeviceGuard g(s->device);
+    TraceRange tr("fabm_solve_batch");
     return run_batch(s, B, y0, y1, traj_params, N_each, out, out_on_device);
 }
 
@@ -1028,6 +1032,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
                           int *ctas_report, int *n_report)
 {
     g_last_error.clear();
+    TraceRange tr("fabm_autotune");
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     if (B < 1 || !y0) return fail(FABM_EINVAL, "autotune needs B >= 1 and y0");
     if (n_probe < 1) return fail(FABM_EINVAL, "n_probe %lld < 1", (long long)n_probe);

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "history_blocks.cuh"
+#include "trace.h"
 #include "recurrence.cuh"
 #include "weights.cuh"
 
@@ -736,6 +737,7 @@ fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *t
 fabm_status fabm_server_step(fabm_server *S, int *n_active, int *n_waiting)
 {
     set_last_error("");
+    TraceRange tr("fabm_server_step");
     if (!S) return srv_fail(FABM_EINVAL, "server is NULL");
     int a = 0, w = 0;
     std::lock_guard<std::mutex> lk(S->mu);
