@@ -1,7 +1,8 @@
 /*
  * fabm.h -- C ABI of the GB300 fractional Adams-Bashforth-Moulton engine.
  *
- * The engine solves Caputo systems  D^alpha y = f(t, y),  y(0) = y0,  0 < alpha < 1,
+ * The engine solves Caputo systems  D^alpha y = f(t, y),  y(0) = y0,  0 < alpha < 2
+ * (y'(0) also given for 1 < alpha < 2; one order per component allowed),
  * on the uniform grid t_n = n h, n = 0..N, with the predictor-corrector of
  * Section 2 of Bonchis, Kaslik, Rosu, arXiv:1710.01133 (Eq. abm for the
  * predictor, the corrector and its weights a_n, c_n right after it).  For each
@@ -10,7 +11,8 @@
  *     S^P_{n+1} = sum_{k=0}^{n} b_{n-k} f_k
  *     S^C_{n+1} = c_n f_0 + sum_{k=1}^{n} a_{n-k} f_k,
  * then y^P_{n+1} = y0 + h^alpha S^P_{n+1},
- *      y_{n+1}   = y0 + h^alpha (S^C_{n+1} + f(t_{n+1}, y^P_{n+1}) / Gamma(alpha+2)).
+ *      y_{n+1}   = y0 + h^alpha (S^C_{n+1} + f(t_{n+1}, y^P_{n+1}) / Gamma(alpha+2))
+ * (for 1 < alpha < 2 the Taylor part y0 + t_{n+1} y'(0) takes the place of y0).
  * b_n is taken with a minus sign, ((n+1)^alpha - n^alpha)/Gamma(alpha+1): the
  * paper prints "+", which does not reproduce constant right-hand sides.
  * A system is solved componentwise (Sec. 2, last paragraph).
@@ -59,7 +61,7 @@ enum {
                        each y formed in double once.  Within 1e-6 of the solution
                        scale of an FP64 solve on every tested workload */
     FABM_FP64X2 = 2 /* the extended-precision mode the paper runs in long double
-                       (Sec. 4, "memory saving"): weights in double-double from
+                       (Sec. 3.4, "memory saving"): weights in double-double from
                        binary128 (fabm_weights_x2), far-history sums in
                        double-double (exact products, compensated sums, combined
                        across chunks in double-double) and rounded once; the
