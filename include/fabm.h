@@ -192,14 +192,14 @@ int fabm_get_recurrence_layout(const fabm_solver *s);
 
 /* Autotuner: times a solve of the caller's batch (B, y0, traj_params as for
  * fabm_solve_batch) truncated to n_probe steps for each candidate setting and
- * keeps the fastest on the solver.  Candidates: for FABM_FP64 (FABM_FP64X2: its
- * double-double kernel), the split-k CTA
- * target of the history kernel (304, 608, 1216 CTAs); for FABM_SPLIT, the
- * tensor-core kernel with 0, 16 or 32 SMs (or an automatic number) kept free
- * for the recurrence running beside it, and the compensated-fp32 kernel at the
- * three CTA targets.  Up to max_report candidates are reported (milliseconds
- * per truncated solve, history kernel FABM_HIST_*, CTA target or SM reserve);
- * *n_report receives the number tried.  Any report pointer may be NULL.  Allocates a device output buffer of
+ * keeps the fastest on the solver.  Candidates: for FABM_FP64 and FABM_FP64X2
+ * (with its double-double kernel), the split-k CTA target of the history kernel
+ * (304, 608, 1216 CTAs); for FABM_SPLIT, the tensor-core kernel with 0, 16 or 32
+ * SMs (or an automatic number) kept free for the recurrence running beside it,
+ * and the compensated-fp32 kernel at the three CTA targets.  Up to max_report
+ * candidates are reported (milliseconds per truncated solve, history kernel
+ * FABM_HIST_*, CTA target or SM reserve); *n_report receives the number tried.
+ * Any report pointer may be NULL.  Allocates a device output buffer of
  * B x (N+1) x dim doubles for the duration of the call. */
 fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
                           int64_t n_probe, int max_report, double *ms_report, int *kernel_report,
