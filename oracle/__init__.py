@@ -62,6 +62,7 @@ def _load():
         lib.fabm_oracle_rhs.argtypes = [i, i, d, P(d), P(d), i, P(d)]
         lib.fabm_oracle_solve.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), P(d), i]
         lib.fabm_oracle_solve_threaded.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), i]
+        lib.fabm_oracle_solve_q.argtypes = [i, d, d, i64, i, P(d), i, P(d), P(d), P(d)]
         lib.fabm_oracle_solve_w.argtypes = [i, d, i64, i, P(d), i, P(d), P(d), P(d), d, d,
                                             P(d), P(d), P(d), i]
         lib.fabm_oracle_solve_batch.argtypes = [i, d, d, i64, i, P(d), i, i64, P(d), P(d), P(d),
@@ -70,7 +71,8 @@ def _load():
                                                       P(d), P(d), P(ctypes.c_int64), P(d), i]
         for f in ("fabm_oracle_weights", "fabm_oracle_constants", "fabm_oracle_rhs",
                   "fabm_oracle_solve", "fabm_oracle_solve_w", "fabm_oracle_solve_batch",
-                  "fabm_oracle_solve_batch_multi"):
+                  "fabm_oracle_solve_batch_multi", "fabm_oracle_solve_threaded",
+                  "fabm_oracle_solve_q"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -149,6 +151,19 @@ def solve(name: str, alpha, h: float, N: int, y0, params=None,
     out = np.empty((N + 1, y0.size))
     _check(_load().fabm_oracle_solve(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
                                      _dp(y1), _dp(out), int(compensated)), "solve")
+    return out
+
+
+def solve_q(name: str, alpha: float, h: float, N: int, y0, params=None, y1=None):
+    """One trajectory with every quantity in binary128 (weights, sums, t, f),
+    y rounded to double once: the self-check of the double-precision oracle and
+    the reference of the double-double mode.  O(N^2) binary128 operations."""
+    y0 = _f64(y0).reshape(-1)
+    rid, p = _rhs(name, y0.size, params)
+    y1a = None if y1 is None else _f64(y1).reshape(-1)
+    out = np.empty((N + 1, y0.size))
+    _check(_load().fabm_oracle_solve_q(y0.size, alpha, h, N, rid, _dp(p), p.size, _dp(y0),
+                                       _dp(y1a), _dp(out)), "solve_q")
     return out
 
 

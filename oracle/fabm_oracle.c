@@ -427,6 +427,105 @@ int fabm_oracle_solve_threaded(int dim, double alpha, double h, int64_t N, int r
     return st;
 }
 
+/* ------------------------------------------------ binary128 self-check --- */
+
+/* f(t, y) in binary128, the formulas of orc_rhs. */
+static void orc_rhs_q(int rhs, int dim, q128 t, const q128 *y, const q128 *p, q128 *out)
+{
+    switch (rhs) {
+    case ORC_CONST:
+        for (int i = 0; i < dim; ++i) out[i] = p[0];
+        break;
+    case ORC_TIME:
+        for (int i = 0; i < dim; ++i) out[i] = t;
+        break;
+    case ORC_LINEAR:
+        for (int i = 0; i < dim; ++i) out[i] = -p[0] * y[i];
+        break;
+    case ORC_LORENZ:
+        out[0] = p[0] * (y[1] - y[0]);
+        out[1] = y[0] * (p[1] - y[2]) - y[1];
+        out[2] = y[0] * y[1] - p[2] * y[2];
+        break;
+    case ORC_DUFFING:
+        out[0] = y[1];
+        out[1] = -p[0] * y[1] - y[0] - y[0] * y[0] * y[0] + p[2] * cosf128(p[1] * t);
+        break;
+    case ORC_MANUFACTURED:
+        out[0] = p[0] * orc_powq(t, p[1]) + orc_powq(t, p[2]) - y[0];
+        break;
+    case ORC_LCR: {
+        const q128 x = y[0], a = p[2], b = p[3];
+        const q128 g = x <= -1 ? b * x - a + b : (x >= 1 ? b * x + a - b : a * x);
+        out[0] = y[1] - g;
+        out[1] = -p[0] * y[1] - y[0] + p[4] * sinf128(p[1] * t);
+        break;
+    }
+    default:
+        for (int i = 0; i < dim; ++i) out[i] = NAN;
+    }
+}
+
+/* The scheme of orc_solve_one with every quantity in binary128: the weights
+ * from the printed formulas without rounding them to double, the sums in plain
+ * binary128 (113-bit significands, ~90 bits left after 2^20 additions), t_n =
+ * n h and the right-hand side in binary128, y rounded to double once for out.
+ * It estimates the rounding of the double-precision oracle and is the
+ * reference of the double-double mode.  One order, 0 < alpha < 2 (y1 = y'(0)
+ * for alpha > 1, NULL: zero), one trajectory; cost O(N^2) binary128
+ * operations, meant for N of a few thousand. */
+int fabm_oracle_solve_q(int dim, double alpha, double h, int64_t N, int rhs, const double *params,
+                        int n_params, const double *y0, const double *y1, double *out)
+{
+    if (dim < 1 || dim > 8 || N < 1 || !(h > 0.0) || !(alpha > 0.0 && alpha < 2.0) ||
+        (y1 && alpha <= 1.0) || !orc_rhs_dim_ok(rhs, dim, n_params) || n_params > 16)
+        return ORC_EINVAL;
+    q128 *w = (q128 *)malloc((size_t)3 * N * sizeof(q128));
+    q128 *P = (q128 *)malloc((size_t)(N + 2) * sizeof(q128));
+    q128 *F = (q128 *)malloc((size_t)(N + 1) * dim * sizeof(q128));
+    if (!w || !P || !F) {
+        free(w), free(P), free(F);
+        return ORC_ENOMEM;
+    }
+    const q128 al = (q128)alpha, hq = (q128)h;
+    for (int64_t j = 0; j < N + 2; ++j) P[j] = orc_powq((q128)j, al);
+    const q128 g1 = tgammaf128(al + 1), g2 = tgammaf128(al + 2);
+    q128 *b = w, *a = w + N, *c = w + 2 * N;
+    for (int64_t j = 0; j < N; ++j) {
+        const q128 j0 = (q128)j, j1 = (q128)(j + 1), j2 = (q128)(j + 2);
+        b[j] = (P[j + 1] - P[j]) / g1;
+        a[j] = (j2 * P[j + 2] - 2 * (j1 * P[j + 1]) + j0 * P[j]) / g2;
+        c[j] = (j0 * P[j] - (j0 - al) * P[j + 1]) / g2;
+    }
+    const q128 ha = powf128(hq, al), ig2 = 1 / g2;
+    q128 p[16], yq0[8], yq1[8], yp[8], fp[8], yc[8];
+    for (int i = 0; i < n_params; ++i) p[i] = (q128)params[i];
+    for (int i = 0; i < dim; ++i) {
+        yq0[i] = (q128)y0[i];
+        yq1[i] = y1 ? (q128)y1[i] : 0;
+        out[i] = y0[i];
+    }
+    orc_rhs_q(rhs, dim, 0, yq0, p, F);
+    for (int64_t n = 0; n < N; ++n) {
+        const q128 t1 = (q128)(n + 1) * hq;
+        for (int i = 0; i < dim; ++i) {
+            q128 sp = 0;
+            for (int64_t k = 0; k <= n; ++k) sp += b[n - k] * F[k * dim + i];
+            yp[i] = yq0[i] + t1 * yq1[i] + ha * sp;
+        }
+        orc_rhs_q(rhs, dim, t1, yp, p, fp);
+        for (int i = 0; i < dim; ++i) {
+            q128 sc = c[n] * F[i];
+            for (int64_t k = 1; k <= n; ++k) sc += a[n - k] * F[k * dim + i];
+            yc[i] = yq0[i] + t1 * yq1[i] + ha * (sc + fp[i] * ig2);
+            out[(n + 1) * dim + i] = (double)yc[i];
+        }
+        orc_rhs_q(rhs, dim, t1, yc, p, F + (n + 1) * dim);
+    }
+    free(w), free(P), free(F);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------- batches --- */
 
 typedef struct {

@@ -97,3 +97,14 @@ def test_x2_history_kernel_and_autotune(gpu_lib, parity):
     parity(rel_err(got, ref), TOL, "")
     with pytest.raises(gpu_lib.FabmError):
         gpu_lib.Server(1 << 30, precision="fp64x2")
+
+
+@pytest.mark.parametrize("case", ["ml", "lorenz"])
+def test_x2_against_the_binary128_oracle(gpu_lib, parity, case):
+    """The double-double mode against the oracle run entirely in binary128 (its
+    weights, sums and steps), which pins the oracle's own rounding too."""
+    w = ml_scalar(N=2000) if case == "ml" else lorenz_single(N=2000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64x2") as s:
+        got = s.solve(w.y0[0])
+    ref = oracle.solve_q(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    parity(rel_err(got, ref), TOL, case)

@@ -480,3 +480,64 @@ def test_threaded_k_reduction_equals_the_sequential_oracle(threads):
         assert np.array_equal(got, ref)
     scale = np.max(np.abs(ref), axis=0)
     assert np.max(np.abs(got - ref) / scale) < 1e-13
+
+
+# ---- binary128 self-check of the oracle ----
+
+def _exact_power_law(y0, y1, c, alpha, h, N):
+    """y0 + y1 t + c t^alpha / Gamma(alpha+1) at t_n = n h, 40 digits."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    a = mpmath.mpf(alpha)
+    g = mpmath.gamma(a + 1)
+    out = []
+    for n in range(N + 1):
+        t = mpmath.mpf(n) * mpmath.mpf(h)
+        out.append(float(mpmath.mpf(y0) + mpmath.mpf(y1) * t + mpmath.mpf(c) * t ** a / g))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("alpha,y1", [(0.7, None), (0.3, None), (1.5, 0.4)])
+def test_binary128_oracle_is_correctly_rounded_on_the_power_law(alpha, y1):
+    """f = c: the scheme reproduces y0 (+ y1 t) + c t^a / Gamma(a+1) exactly, so
+    the binary128 run, rounded once, must give the nearest doubles."""
+    h, N, c = 0.01, 600, 1.5
+    got = oracle.solve_q("const", alpha, h, N, [0.25], params=[c],
+                         y1=None if y1 is None else [y1])[:, 0]
+    ex = _exact_power_law(0.25, y1 or 0.0, c, alpha, h, N)
+    ulps = np.abs(got - ex) / np.spacing(np.abs(ex))
+    assert np.max(ulps) <= 1.0
+
+
+def test_binary128_oracle_time_rhs_corrector_is_exact():
+    """f = t: the corrector integrates the linear interpolant of f exactly, so
+    y_n = y0 + t_n^(a+1) / Gamma(a+2) to binary128 precision."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    alpha, h, N = 0.6, 0.02, 400
+    got = oracle.solve_q("time", alpha, h, N, [0.5])[:, 0]
+    a = mpmath.mpf(alpha)
+    ex = np.array([float(mpmath.mpf(0.5) + (mpmath.mpf(n) * mpmath.mpf(h)) ** (a + 1)
+                         / mpmath.gamma(a + 2)) for n in range(N + 1)])
+    assert np.max(np.abs(got - ex) / np.spacing(np.abs(ex))) <= 1.0
+
+
+@pytest.mark.parametrize("case", ["ml", "lorenz", "duffing", "lcr"])
+def test_double_oracle_rounding_against_binary128(case):
+    """The double-precision oracle (compensated sums, weights rounded once)
+    stays within a few units in the last place of the binary128 run: its own
+    rounding is far below the GPU bars it is used for."""
+    from fabm_workloads import duffing_sweep, lcr_sweep
+    if case == "ml":
+        w = ml_scalar(N=1500)
+    elif case == "lorenz":
+        w = lorenz_single(N=1500)
+    elif case == "duffing":
+        w = duffing_sweep(B=8, N=1500).subset([5])
+    else:
+        w = lcr_sweep(B=8, N=1500).subset([6])
+    p = w.params if w.traj_params is None else w.traj_params[0]
+    q = oracle.solve_q(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=p)
+    d = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=p)
+    scale = np.max(np.abs(q), axis=0)
+    assert np.max(np.abs(d - q) / scale) < 1e-14
