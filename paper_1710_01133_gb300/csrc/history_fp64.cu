@@ -11,8 +11,8 @@
 // 1.19 TFLOP/s at 1.96 GHz), and a warp FP64 instruction costs the same pipe
 // time however many of its lanes are active, so this kernel keeps all 32
 // lanes of every DFMA busy (lane = target, warp = column).  The chunks are
-// summed afterwards in a fixed order (a3), so results do not depend on
-// scheduling.  In isolation it reaches ~0.8 of the FP64 peak at one wave of
+// summed afterwards in a fixed order with compensation (a3), so results do
+// not depend on scheduling.  In isolation it reaches ~0.8 of the FP64 peak at one wave of
 // ~600 CTAs; staging each tile before computing it costs most of the rest.
 #include "history_blocks.cuh"
 
@@ -32,9 +32,29 @@ __global__ void __launch_bounds__(kWarp *hist::kColsPerCta)
                                       blockIdx.y * hist::kColsPerCta, wstride, dim);
 }
 
+// Error-free sum of two doubles (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// (s, c) += v with compensation: the rounding error of every addition is
+// collected in c (Neumaier's compensated summation, written with TwoSum so
+// that it needs no branch on the magnitudes).
+__device__ __forceinline__ void comp_add(double &s, double &c, double v)
+{
+    double e;
+    two_sum(s, v, s, e);
+    c += e;
+}
+
 // a3: G[pc][a][col] = sum_{chunk} part[chunk][pc][a][col], chunk ascending
 // within each lane's strided subset, then a fixed xor tree over the R lanes of
-// a group.  grid-stride over the 2*L*cols outputs.
+// a group; every addition compensated (running sum s and error term c, added
+// once at the end), so the combined history carries the rounding of one
+// addition rather than of n_chunks.  grid-stride over the 2*L*cols outputs.
 template <int R>
 __global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks, int64_t n_out,
                                    double *__restrict__ G)
@@ -46,7 +66,7 @@ __global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks
     // always see full warps
     for (int64_t base = 0; base < n_out; base += groups) {
         const int64_t o = base + gtid / R;
-        double s = 0.0;
+        double s = 0.0, c = 0.0;
         if (o < n_out) {
             // independent loads in flight, summed in chunk order
             int ch = r;
@@ -55,16 +75,21 @@ __global__ void hist_reduce_kernel(const double *__restrict__ part, int n_chunks
                 const double v1 = part[(int64_t)(ch + R) * n_out + o];
                 const double v2 = part[(int64_t)(ch + 2 * R) * n_out + o];
                 const double v3 = part[(int64_t)(ch + 3 * R) * n_out + o];
-                s += v0;
-                s += v1;
-                s += v2;
-                s += v3;
+                comp_add(s, c, v0);
+                comp_add(s, c, v1);
+                comp_add(s, c, v2);
+                comp_add(s, c, v3);
             }
-            for (; ch < n_chunks; ch += R) s += part[(int64_t)ch * n_out + o];
+            for (; ch < n_chunks; ch += R) comp_add(s, c, part[(int64_t)ch * n_out + o]);
         }
 #pragma unroll
-        for (int off = R / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (r == 0 && o < n_out) G[o] = s;
+        for (int off = R / 2; off > 0; off >>= 1) {
+            const double os = __shfl_xor_sync(0xffffffffu, s, off);
+            const double oc = __shfl_xor_sync(0xffffffffu, c, off);
+            comp_add(s, c, os);
+            c += oc;
+        }
+        if (r == 0 && o < n_out) G[o] = s + c;
     }
 }
 

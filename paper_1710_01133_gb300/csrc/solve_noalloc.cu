@@ -20,9 +20,15 @@
 // second process-level instance of this code driving the same context from
 // outside the mutex) would race.  The array keeps the contents of the last
 // call; the only value that must start from a fixed state (the non-finite
-// status word) is reset at the start of every call.  On the first call on a
-// device the array's device address is looked up (cudaGetSymbolAddress) with
-// that device current; make that first call before any stream capture.
+// status word) is reset at the start of every call.
+//
+// The array belongs to the CUDA context that loaded the library's device
+// code, not to the device number: after cudaDeviceReset, or with another
+// context current, it lives at a different address.  So every call looks the
+// address up again (cudaGetSymbolAddress, with the calling thread's current
+// device and context, under the mutex) instead of keeping one from an earlier
+// call.  The first call in a context may load the library's device code into
+// that context; make it before any stream capture.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -61,9 +67,7 @@ constexpr int64_t kScratchDoubles = kOffSt + kRound;
 // The scratch array (about 7 MB).
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-double *g_noalloc_ptr[kMaxDevices] = {};
 
 fabm_status na_fail(fabm_status st, const char *fmt, ...)
 {
@@ -113,15 +117,10 @@ extern "C" fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64
         if (!std::isfinite(y0[i])) return na_fail(FABM_EINVAL, "fabm_solve_noalloc: y0 not finite");
 
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    int dev = 0;
-    NA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return na_fail(FABM_EINVAL, "fabm_solve_noalloc: device %d", dev);
-    if (!g_noalloc_ptr[dev]) {  // once per device, with that device current
-        void *p = nullptr;
-        NA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = static_cast<double *>(p);
-    }
-    double *S = g_noalloc_ptr[dev];
+    // the address in the context current now (see the header comment)
+    void *sym = nullptr;
+    NA_TRY(cudaGetSymbolAddress(&sym, g_noalloc_scratch));
+    double *S = static_cast<double *>(sym);
     cudaStream_t st = cudaStreamPerThread;
 
     // host-side constants and inputs
