@@ -3,8 +3,8 @@
 Requests with different right-hand sides, dims, alphas and lengths are
 admitted by an HBM budget, advanced together block by block, and must give the
 same result alone and in the mix (bit for bit: a request's chunking depends
-only on its own block index) and match standalone solves (FP64: 1e-12) or the
-oracle (split: 1e-6) on the solution scale.
+only on its own block index) and match the oracle on the solution scale (FP64:
+1e-12, split: 1e-6); FP64 requests also match the standalone solver.
 """
 import numpy as np
 import pytest
@@ -46,12 +46,12 @@ def test_server_matches_standalone(gpu_lib, parity, precision):
         results = [srv.result(t) for t in tickets]
     for (rhs, dim, a, h, N, y0, p), got in zip(MIX, results):
         assert got.shape == (N + 1, dim)
+        ref = oracle.solve(rhs, a, h, N, y0, params=p)
         if precision == "fp64":
-            with gpu_lib.Solver(rhs, dim, a, h, N, p) as s:
-                ref = s.solve(y0)
             parity(rel_err(got, ref), 1e-12, rhs)
+            with gpu_lib.Solver(rhs, dim, a, h, N, p) as s:
+                parity(rel_err(got, s.solve(y0)), 1e-12, f"{rhs}-vs-solver")
         else:
-            ref = oracle.solve(rhs, a, h, N, y0, params=p)
             parity(rel_err(got, ref), 1e-6, rhs)
 
 
@@ -89,9 +89,10 @@ def test_budget_admission_and_release(gpu_lib, parity):
         assert srv.stats()["bytes_in_use"] == 2 * per_req
         run_to_completion(srv, tickets)
         res = [srv.result(t) for t in tickets]
-    with gpu_lib.Solver(*req[:5], req[6]) as s:
-        for i, got in enumerate(res):
-            parity(rel_err(got, s.solve(np.asarray(req[5]) + 0.01 * i)), 1e-12, "")
+    y0s = np.stack([np.asarray(req[5]) + 0.01 * i for i in range(4)])
+    refs = oracle.solve_batch(req[0], req[2], req[3], req[4], y0s, params=req[6])
+    for i, got in enumerate(res):
+        parity(rel_err(got, refs[i]), 1e-12, f"req{i}")
 
 
 def test_failures_are_isolated(gpu_lib, parity):
