@@ -160,14 +160,21 @@ enum {
                               FP64X2 precision: FABM_HIST_X2                         */
     FABM_HIST_FP64 = 1,    /* double on CUDA cores (FP64 precision only)             */
     FABM_HIST_TENSOR = 2,  /* three-term bf16 split on tcgen05 tensor cores, exact
-                              per 64-point segment (split precision)                  */
+                              per 64-point segment, far history of each 64-step block
+                              with 64 targets per MMA (split precision)              */
     FABM_HIST_FP32C = 3,   /* compensated fp32 on CUDA cores (split precision)       */
-    FABM_HIST_X2 = 4       /* double-double on CUDA cores (FP64X2 precision only)    */
+    FABM_HIST_X2 = 4,      /* double-double on CUDA cores (FP64X2 precision only)    */
+    FABM_HIST_TENSOR_WIDE = 5 /* as FABM_HIST_TENSOR, but the far history of each pair
+                              of blocks with 128 targets per MMA (one weight kind per
+                              CTA, exact per 128-point group), the latest two or three
+                              64-point segments per block with 64; automatic choice
+                              on the tensor path from N >= 384 on                     */
 };
 
 /* Choose the history kernel (one of FABM_HIST_*; must fit the precision).
- * The block length follows from it: 64 targets for FABM_HIST_TENSOR, 32
- * otherwise.  fabm_autotune measures the candidates and sets the fastest. */
+ * The block length follows from it: 64 targets for FABM_HIST_TENSOR and
+ * FABM_HIST_TENSOR_WIDE, 32 otherwise.  fabm_autotune measures the candidates
+ * and sets the fastest. */
 fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel);
 int fabm_get_history_kernel(const fabm_solver *s);
 
@@ -194,9 +201,11 @@ int fabm_get_recurrence_layout(const fabm_solver *s);
  * fabm_solve_batch) truncated to n_probe steps for each candidate setting and
  * keeps the fastest on the solver.  Candidates: for FABM_FP64 and FABM_FP64X2
  * (with its double-double kernel), the split-k CTA target of the history kernel
- * (304, 608, 1216 CTAs); for FABM_SPLIT, the tensor-core kernel with 0, 16 or 32
- * SMs (or an automatic number) kept free for the recurrence running beside it,
- * and the compensated-fp32 kernel at the three CTA targets.  Up to max_report
+ * (304, 608, 1216 CTAs); for FABM_SPLIT, the two tensor-core far-history
+ * tilings (FABM_HIST_TENSOR_WIDE: 128 targets per MMA and per far launch;
+ * FABM_HIST_TENSOR: 64) each with 0 or 16 SMs (or an automatic number) kept
+ * free for the recurrence running beside it, and the compensated-fp32 kernel
+ * at 304 and 608 CTAs.  Up to max_report
  * candidates are reported (milliseconds per truncated solve, history kernel
  * FABM_HIST_*, CTA target or SM reserve); *n_report receives the number tried.
  * Any report pointer may be NULL.  Allocates a device output buffer of
@@ -218,6 +227,26 @@ int fabm_get_block(const fabm_solver *s);
  * parameters, per-trajectory lengths) are read from device memory by the
  * kernels, so a cached graph serves any inputs of the same shape. */
 fabm_status fabm_set_graphs(fabm_solver *s, int enable);
+
+/* Failure handling (Sec. 5 of the design has no counterpart in the paper; these
+ * make the library's error paths testable without faulting a GPU).
+ *
+ * fabm_set_wait_limit: the tensor-core history kernel waits on barriers that
+ * other warps of its CTA complete; each such wait gives up after `cycles` SM
+ * clock cycles (0: the default, about 2 s at 2 GHz).  A CTA that gives up sets
+ * the solver's status word, waits for its own copies and MMAs in flight, frees
+ * its tensor memory and returns, and the solve returns FABM_ETIMEOUT; the
+ * solver stays usable.  A tiny limit forces that path.  FABM_EINVAL for
+ * cycles < 0.
+ *
+ * fabm_inject_alloc_failures: the next n device allocations the library makes
+ * (solver work space, server admissions; process-wide) fail as if the device
+ * were out of memory, without calling the allocator: the call that needed the
+ * memory returns FABM_ENOMEM (a server marks that request failed with
+ * FABM_ENOMEM), and later calls allocate normally.  n = 0 cancels what is left.
+ * FABM_EINVAL for n < 0. */
+fabm_status fabm_set_wait_limit(fabm_solver *s, int64_t cycles);
+fabm_status fabm_inject_alloc_failures(int n);
 
 /* Copy the first n device weights of the solver to host arrays (n <= N+1):
  *   B[d] = b_{d-1}, A[d] = a_{d-1} (d >= 1; index 0 holds 0),
@@ -383,9 +412,11 @@ fabm_status fabm_server_destroy(fabm_server *s);
  * device array of about 7 MB that every GPU loading the library holds until
  * the process exits.  Calls share that array and keep the last call's data;
  * calls are serialized by a host mutex, and work overlapping on the GPU with
- * another user of the array would race.  The first call on a device looks up
- * the array's device address with that device current: make it before any
- * stream capture.  Runs on the calling thread's default stream; synchronous.
+ * another user of the array would race.  Every call looks up the array's
+ * device address in the calling thread's current context (the address changes
+ * after cudaDeviceReset or in another context); the first call in a context may
+ * load the library's device code there: make it before any stream capture.
+ * Runs on the calling thread's per-thread default stream; synchronous.
  * Errors: FABM_EINVAL (incl. N or dim beyond the array's limits, with a
  * message saying so), FABM_ECUDA, FABM_ENONFINITE. */
 fabm_status fabm_solve_noalloc(int dim, double alpha, double h, int64_t N, int rhs_id,

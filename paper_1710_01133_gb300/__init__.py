@@ -17,7 +17,8 @@ from . import build as _build
 FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, FABM_EBUSY = range(7)
 FABM_FP64, FABM_SPLIT, FABM_FP64X2 = 0, 1, 2
 FABM_HIST_AUTO, FABM_HIST_FP64, FABM_HIST_TENSOR, FABM_HIST_FP32C = range(4)
-HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3, "x2": 4}
+FABM_HIST_X2, FABM_HIST_TENSOR_WIDE = 4, 5
+HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3, "x2": 4, "tensor-wide": 5}
 RECURRENCE = {"auto": 0, "columns": 1, "targets": 2}
 RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
        "lcr": 6}
@@ -32,7 +33,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
             "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
-            "fabm_server_wait")
+            "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -116,6 +117,10 @@ def load(build_if_missing: bool = True):
     lib.fabm_kernel_busy.restype = i
     lib.fabm_stroboscope.argtypes = [vp, i64, i64, i, vp, d, d, d, i64, i, vp]
     lib.fabm_stroboscope.restype = i
+    lib.fabm_set_wait_limit.argtypes = [vp, i64]
+    lib.fabm_set_wait_limit.restype = i
+    lib.fabm_inject_alloc_failures.argtypes = [i]
+    lib.fabm_inject_alloc_failures.restype = i
     for f in ("fabm_create", "fabm_create_multi", "fabm_solve", "fabm_solve_batch",
               "fabm_solve_batch_ic",
               "fabm_destroy", "fabm_set_block",
@@ -291,6 +296,14 @@ def fabm_kernel_busy(handle, kind):
     return ms.value
 
 
+def fabm_set_wait_limit(handle, cycles: int):
+    _check(load().fabm_set_wait_limit(handle, int(cycles)))
+
+
+def fabm_inject_alloc_failures(n: int):
+    _check(load().fabm_inject_alloc_failures(int(n)))
+
+
 # ---------------------------------------------------------- convenience ---
 
 class Solver:
@@ -359,6 +372,10 @@ class Solver:
 
     def set_graphs(self, enable: bool = True):
         fabm_set_graphs(self.handle, enable)
+
+    def set_wait_limit(self, cycles: int = 0):
+        """Clock cycles after which the tensor kernel's waits give up (0: default)."""
+        fabm_set_wait_limit(self.handle, cycles)
 
     def set_timing(self, period: int = 1):
         """period > 0: time the launches of every period-th block; 0: off."""

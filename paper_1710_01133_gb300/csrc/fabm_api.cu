@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -67,7 +68,8 @@ struct DevBuf {
     {
         if (want <= n) return cudaSuccess;
         release();
-        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+        cudaError_t e = take_injected_alloc_failure() ? cudaErrorMemoryAllocation
+                                                      : cudaMalloc(&p, want * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
             n = 0;
@@ -92,6 +94,18 @@ constexpr int kAuxRing = 4;  // forcing tables computed up to 3 blocks ahead
 
 void fabm::set_last_error(const char *msg) { g_last_error = msg; }
 
+namespace {
+std::atomic<int> g_alloc_failures{0};  // injected device-allocation failures left
+}  // namespace
+
+bool fabm::take_injected_alloc_failure()
+{
+    int n = g_alloc_failures.load(std::memory_order_relaxed);
+    while (n > 0)
+        if (g_alloc_failures.compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+    return false;
+}
+
 struct fabm_solver {
     int device = 0;
     int dim = 0;
@@ -106,6 +120,8 @@ struct fabm_solver {
     int hist_kernel = FABM_HIST_AUTO;  // requested
     int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
+    long long wait_cycles = 0;         // tensor kernel's wait limit (0: its default)
+    bool wide = false;                 // the solve being set up uses the 128-target far history
     int L = kRecurL;                   // block length of the last solve
     int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
     int cols_warps = 1;                // tensor path: warps per CTA of the column recurrence,
@@ -122,12 +138,19 @@ struct fabm_solver {
     DevBuf<__nv_bfloat16> wH;
     DevBuf<int> wHe;
     int64_t g_max = 0;
+    // wide far history: Hankel tiles per group lag (128-point groups) and exponents
+    DevBuf<__nv_bfloat16> wH2;
+    DevBuf<int> wHe2;
+    int64_t G_max = 0;
     // per-batch workspace
     DevBuf<double> F, Ystage, G, part, y0, par;
     DevBuf<float> Ff;          // compensated-fp32 history: f rounded to float
     DevBuf<__nv_bfloat16> Fs;  // split: f slices
     DevBuf<int> Fe;            // split: f exponents
     DevBuf<float2> spart;      // split: float-float partials
+    DevBuf<__nv_bfloat16> Fs2; // wide far history: f slices per 128-point group
+    DevBuf<int> Fe2;           // wide far history: exponents per group
+    DevBuf<float2> fpart;      // wide far history: partials of two target groups
     DevBuf<float2> auxb;       // tensor path: forcing tables of kAuxRing blocks
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
@@ -135,13 +158,15 @@ struct fabm_solver {
     // sR: recurrence; sG, sG2: far history (the CUDA-core history of odd blocks
     // runs on sG2, so that consecutive blocks' history launches overlap)
     // sC: device-to-host copies of finished rows while the solve goes on
-    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr, sC = nullptr;
+    // sG3: far history of odd target groups (wide tensor path)
+    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr, sC = nullptr, sG3 = nullptr;
     double *out_stream = nullptr;  // pinned host output of the solve being enqueued, or NULL
     int64_t out_group = 1;         // blocks per streamed copy
     // evN: the newest-segment history launch of the tensor path (on sR); evA:
     // the forcing tables (tensor path, on sG2)
     cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evN[3] = {}, evA[kAuxRing] = {};
-    cudaEvent_t evFork = nullptr, evJoin = nullptr, evJoinC = nullptr;
+    cudaEvent_t evF[2] = {};  // wide far history of target group C, slot C % 2
+    cudaEvent_t evFork = nullptr, evJoin = nullptr, evJoinC = nullptr, evJoin3 = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
@@ -169,6 +194,7 @@ struct fabm_solver {
     ~fabm_solver()
     {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
+        wH2.release(), wHe2.release(), Fs2.release(), Fe2.release(), fpart.release();
         wBl.release(), wAl.release(), wDl.release();
         wBf.release(), wAf.release(), wBff.release(), wAff.release(), wDff.release();
         F.release(), Ff.release(), Ystage.release(), G.release(), part.release();
@@ -182,6 +208,9 @@ struct fabm_solver {
             if (e) cudaEventDestroy(e);
         for (auto &e : evA)
             if (e) cudaEventDestroy(e);
+        for (auto &e : evF)
+            if (e) cudaEventDestroy(e);
+        if (evJoin3) cudaEventDestroy(evJoin3);
         if (evFork) cudaEventDestroy(evFork);
         if (evJoin) cudaEventDestroy(evJoin);
         if (evJoinC) cudaEventDestroy(evJoinC);
@@ -191,6 +220,7 @@ struct fabm_solver {
         if (sG) cudaStreamDestroy(sG);
         if (sG2) cudaStreamDestroy(sG2);
         if (sC) cudaStreamDestroy(sC);
+        if (sG3) cudaStreamDestroy(sG3);
     }
 };
 
@@ -305,8 +335,9 @@ int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
     // one order per component: every column tile would need its own weight
     // operand, so the tensor kernel (one weight operand per tile) is not used
     if (s->multi) return FABM_HIST_FP32C;
-    if (s->hist_kernel == FABM_HIST_TENSOR || s->hist_kernel == FABM_HIST_FP32C)
-        return s->hist_kernel;
+    if (s->hist_kernel == FABM_HIST_TENSOR || s->hist_kernel == FABM_HIST_TENSOR_WIDE)
+        return FABM_HIST_TENSOR;
+    if (s->hist_kernel == FABM_HIST_FP32C) return s->hist_kernel;
     return cols >= 64 ? FABM_HIST_TENSOR : FABM_HIST_FP32C;
 }
 
@@ -336,7 +367,8 @@ int history_lag(int hk, int64_t N, int64_t cols)
 // recurrence (and, tensor path, the newest segment's history and the slicing
 // of the finished segment) on sR.
 fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &w, int64_t nblk,
-                          int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks, int hk)
+                          int64_t Nmax, int64_t max_chunks, int n_ct, int split_chunks, int hk,
+                          int far_chunks)
 {
     const int L = s->L;
     const int64_t cols = bt.cols;
@@ -369,7 +401,52 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
         const int64_t ph = c % s->timing_period;
         s->sample_now = ph == 0 || (lag == 2 && ph < 8);
         const void *Gc = nullptr;
-        if (split && c >= 1) {
+        if (split && c >= 1 && s->wide) {
+            // pairs of blocks: the far history of target group C = c/2 over
+            // the point groups 0 .. C-2 (128 points each) on sG / sG3, started
+            // once R(2C-3) has finished group C-2 and due by R(2C), so it runs
+            // beside the recurrences of blocks 2C-2 and 2C-1; the segments of
+            // 64 points from 2C-2 up to c-1 as a near launch on sR; both
+            // combined on sR
+            float2 *Gbuf = reinterpret_cast<float2 *>(s->G.p) + (size_t)(c % n_gbuf) * 2 * L * cols;
+            const int64_t C = c / 2;
+            const int t = (int)(c % 2);
+            const size_t fstride = far_part_elems(far_chunks, (int)cols);
+            const float2 *fp = s->fpart.p + (size_t)(C & 1) * fstride;
+            int n_far = 0;
+            if (C >= 2) {
+                n_far = (int)std::min<int64_t>(far_chunks, C - 1);
+                if (t == 0) {
+                    cudaStream_t fs = (C & 1) ? s->sG3 : s->sG;
+                    float2 *fw = s->fpart.p + (size_t)(C & 1) * fstride;
+                    const double flops = 4.0 * 128.0 * (double)((C - 1) * 128) * (double)cols;
+                    FABM_CUDA_TRY(cudaStreamWaitEvent(fs, s->evR[(c - 3) % kEvRing], 0));
+                    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, fs, 0.0, [&] {
+                        return launch_slice_group(bt, n_ct, C - 2, s->Fs2.p, s->Fe2.p, fs);
+                    }));
+                    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, fs, flops, [&] {
+                        return launch_hist_far(s->Fs2.p, s->Fe2.p, s->wH2.p, s->wHe2.p, C,
+                                               (int)(C - 1), n_far, n_ct, (int)cols, fw, s->err.p,
+                                               s->wait_cycles, fs);
+                    }));
+                    FABM_CUDA_TRY(cudaEventRecord(s->evF[C & 1], fs));
+                }
+            }
+            const int64_t lo = std::max<int64_t>(0, 2 * C - 2);
+            const int n_near = (int)(c - lo);
+            const double nflops = 4.0 * L * (double)(n_near * L) * (double)cols;
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, nflops, [&] {
+                return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, (int)lo, n_near,
+                                         0, n_near, n_ct, (int)cols, s->spart.p, s->err.p,
+                                         s->wait_cycles, s->sR);
+            }));
+            if (n_far > 0) FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evF[C & 1], 0));
+            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sR, 0.0, [&] {
+                return launch_combine_far(fp, n_far, 64 * t, s->spart.p, n_near, (int)cols, Gbuf,
+                                          s->sR);
+            }));
+            Gc = Gbuf;
+        } else if (split && c >= 1) {
             // far part (segments 0 .. c-2) on sG beside the recurrence of block
             // c-1; the newest segment c-1 on sR once it is sliced; the combine
             // on sG after both
@@ -380,13 +457,15 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                 FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evR[(c - 2) % kEvRing], 0));
                 FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sG, flops, [&] {
                     return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, 0, (int)(c - 1),
-                                             0, n_far, n_ct, (int)cols, s->spart.p, s->err.p, s->sG);
+                                             0, n_far, n_ct, (int)cols, s->spart.p, s->err.p,
+                                             s->wait_cycles, s->sG);
                 }));
             }
             const double nflops = 4.0 * L * (double)L * (double)cols;
             FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, nflops, [&] {
                 return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, (int)(c - 1), 1,
-                                         n_far, 1, n_ct, (int)cols, s->spart.p, s->err.p, s->sR);
+                                         n_far, 1, n_ct, (int)cols, s->spart.p, s->err.p,
+                                         s->wait_cycles, s->sR);
             }));
             FABM_CUDA_TRY(cudaEventRecord(s->evN[c % 3], s->sR));
             FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evN[c % 3], 0));
@@ -541,7 +620,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     FABM_CUDA_TRY(s->nEach.ensure((size_t)B));
     FABM_CUDA_TRY(s->status.ensure(1));
     const int n_ct = (int)((cols + 127) / 128);
-    int split_chunks = 1;
+    int split_chunks = 1, far_chunks = 1;
+    s->wide = false;
     if (split) {
         // recurrence layout: one lane per column for wide batches, and where
         // the history dominates (its SMs matter more than the recurrence's
@@ -562,13 +642,25 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             reserve = n_ct <= 16 ? (int)want : 0;
         }
         split_chunks = std::max(1, (148 - reserve) / n_ct);
+        // far history with 128 targets per MMA (pairs of blocks): requested,
+        // or automatic once there are groups to sum
+        s->wide = s->G_max >= 2 && (s->hist_kernel == FABM_HIST_TENSOR_WIDE ||
+                                    s->hist_kernel == FABM_HIST_AUTO);
+        far_chunks = std::max(1, (148 - reserve) / (2 * n_ct));
         // column layout: CTAs sized to fill the SMs the tensor CTAs leave free
         const int free_sms = std::max(4, 152 - n_ct * split_chunks);
         s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 12) : 0;
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
-        // far chunks and one chunk for the newest segment
-        FABM_CUDA_TRY(s->spart.ensure(split_part_elems(split_chunks + 1, (int)cols)));
+        // far chunks and one chunk for the newest segment; with the wide far
+        // history, up to three near segments
+        FABM_CUDA_TRY(s->spart.ensure(split_part_elems(std::max(split_chunks + 1, 3), (int)cols)));
+        if (s->wide) {
+            const int64_t n_grp = (N + 127) / 128;
+            FABM_CUDA_TRY(s->Fs2.ensure((size_t)n_grp * n_ct * far_group_slice_elems()));
+            FABM_CUDA_TRY(s->Fe2.ensure((size_t)n_grp * n_ct * 128));
+            FABM_CUDA_TRY(s->fpart.ensure(2 * far_part_elems(far_chunks, (int)cols)));
+        }
         if (rhs_has_forcing(s->rhs, dim))
             FABM_CUDA_TRY(s->auxb.ensure((size_t)kAuxRing * kSplitSeg * B));
         FABM_CUDA_TRY(s->err.ensure(1));
@@ -637,9 +729,11 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)s->F.p, (uintptr_t)s->Ff.p, (uintptr_t)s->G.p, (uintptr_t)s->part.p, (uintptr_t)s->Fs.p,
         (uintptr_t)s->Fe.p, (uintptr_t)s->spart.p, (uintptr_t)s->y0.p, (uintptr_t)s->par.p,
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
-        (uintptr_t)s->out_stream, (uintptr_t)s->out_group};
+        (uintptr_t)s->out_stream, (uintptr_t)s->out_group, (uintptr_t)s->wait_cycles,
+        (uintptr_t)s->wide, (uintptr_t)far_chunks, (uintptr_t)s->Fs2.p, (uintptr_t)s->Fe2.p,
+        (uintptr_t)s->fpart.p};
     auto enqueue = [&]() -> fabm_status {
-        return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk);
+        return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk, far_chunks);
     };
     if (!s->use_graphs) {
         s->recs.clear();
@@ -648,8 +742,10 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG, s->evFork, 0));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG2, s->evFork, 0));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sC, s->evFork, 0));
+        FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG3, s->evFork, 0));
         fabm_status est = enqueue();
         if (est != FABM_OK) return est;
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sG3));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG2));
@@ -667,6 +763,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG, s->evFork, 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG2, s->evFork, 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sC, s->evFork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG3, s->evFork, 0);
             fabm_status est = e == cudaSuccess ? enqueue() : FABM_ECUDA;
             if (est == FABM_OK) {
                 e = cudaEventRecord(s->evFork, s->sG);
@@ -675,6 +772,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoin, 0);
                 if (e == cudaSuccess) e = cudaEventRecord(s->evJoinC, s->sC);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoinC, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(s->evJoin3, s->sG3);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoin3, 0);
             }
             cudaError_t e2 = cudaStreamEndCapture(s->sR, &graph);
             s->capturing = false;
@@ -810,6 +909,10 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sC, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG3, cudaStreamNonBlocking);
+    for (auto &ev : s->evF)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin3, cudaEventDisableTiming);
     for (auto &ev : s->evR)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto &ev : s->evG)
@@ -868,6 +971,15 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
             if (e == cudaSuccess) e = s->wHe.ensure((size_t)(s->g_max + 1) * 2);
             if (e == cudaSuccess)
                 e = launch_hankel_weights(s->wB.p, s->wA.p, s->g_max, s->wH.p, s->wHe.p, s->sR);
+        }
+        // wide far history: 128-point groups, lags 2 .. G_max
+        s->G_max = multi ? 0 : (N + 127) / 128 - 1;
+        if (e == cudaSuccess && s->G_max >= 2) {
+            e = prepare_hist_far();
+            if (e == cudaSuccess) e = s->wH2.ensure((size_t)(s->G_max + 1) * far_group_tile_elems());
+            if (e == cudaSuccess) e = s->wHe2.ensure((size_t)(s->G_max + 1) * 2);
+            if (e == cudaSuccess)
+                e = launch_hankel_group(s->wB.p, s->wA.p, s->G_max, s->wH2.p, s->wHe2.p, s->sR);
         }
         if (e == cudaSuccess && !multi) {
             const double ha = s->k.h_alpha[0];
@@ -984,12 +1096,16 @@ fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
                     (s->precision == FABM_FP64 && kernel == FABM_HIST_FP64) ||
                     (s->precision == FABM_FP64X2 && kernel == FABM_HIST_X2) ||
                     (s->precision == FABM_SPLIT &&
-                     (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_FP32C));
+                     (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_TENSOR_WIDE ||
+                      kernel == FABM_HIST_FP32C));
     if (!ok) return fail(FABM_EINVAL, "history kernel %d does not fit precision %d", kernel, s->precision);
     std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
     s->hist_kernel = kernel;
-    s->L = kernel == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    s->L = (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_TENSOR_WIDE ||
+            (kernel == FABM_HIST_AUTO && s->precision == FABM_SPLIT))
+               ? kSplitSeg
+               : kRecurL;
     return FABM_OK;
 }
 
@@ -1047,9 +1163,12 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         const int k = s->precision == FABM_FP64 ? FABM_HIST_FP64 : FABM_HIST_X2;
         for (int c : ctas_opts) cands.push_back({k, c});
     } else {
-        // tensor kernel: "ctas" carries the SM reserve (-1 automatic, 0, 16, 32)
-        for (int r : {-1, 0, 16, 32}) cands.push_back({FABM_HIST_TENSOR, r});
-        for (int c : ctas_opts) cands.push_back({FABM_HIST_FP32C, c});
+        // tensor kernels (far history of pairs of blocks with 128 targets per
+        // MMA, or of single blocks with 64): "ctas" carries the SM reserve
+        // (-1 automatic, 0, 16); the compensated-fp32 kernel at two CTA targets
+        for (int k : {FABM_HIST_TENSOR_WIDE, FABM_HIST_TENSOR})
+            for (int r : {-1, 0, 16}) cands.push_back({k, r});
+        for (int c : {152 * 2, 152 * 4}) cands.push_back({FABM_HIST_FP32C, c});
     }
     std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
@@ -1069,7 +1188,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     fabm_status st = FABM_OK;
     for (const Cand &cd : cands) {
         s->hist_kernel = cd.kernel;
-        if (cd.kernel == FABM_HIST_TENSOR)
+        if (cd.kernel == FABM_HIST_TENSOR || cd.kernel == FABM_HIST_TENSOR_WIDE)
             s->sm_reserve = cd.ctas, s->chunk_ctas = keep_ctas;
         else
             s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
@@ -1096,12 +1215,32 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         return st;
     }
     s->hist_kernel = pick.kernel;
-    if (pick.kernel == FABM_HIST_TENSOR)
+    const bool tensor = pick.kernel == FABM_HIST_TENSOR || pick.kernel == FABM_HIST_TENSOR_WIDE;
+    if (tensor)
         s->sm_reserve = pick.ctas, s->chunk_ctas = keep_ctas;
     else
         s->chunk_ctas = pick.ctas, s->sm_reserve = keep_res;
-    s->L = pick.kernel == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    s->L = tensor ? kSplitSeg : kRecurL;
     if (n_report) *n_report = nr;
+    return FABM_OK;
+}
+
+fabm_status fabm_set_wait_limit(fabm_solver *s, int64_t cycles)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (cycles < 0) return fail(FABM_EINVAL, "wait limit %lld < 0", (long long)cycles);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->wait_cycles = (long long)cycles;
+    return FABM_OK;
+}
+
+fabm_status fabm_inject_alloc_failures(int n)
+{
+    g_last_error.clear();
+    if (n < 0) return fail(FABM_EINVAL, "n %d < 0", n);
+    g_alloc_failures.store(n, std::memory_order_relaxed);
     return FABM_OK;
 }
 

@@ -100,6 +100,11 @@ cudaError_t launch_recur(int rhs, const DevBatch &bt, const DevWeights &w, const
 // Message returned by fabm_last_error() on the calling thread.
 void set_last_error(const char *msg);
 
+// Host-side fault injection (fabm_inject_alloc_failures): true when the
+// device allocation about to be made must fail as if the device were out of
+// memory (the allocator is then not called).  Consumes one injected failure.
+bool take_injected_alloc_failure();
+
 // ---- split path (history on tensor cores) ----
 
 // f of segment seg (64 points) -> bf16 slices Fs and per-column exponents Ef.
@@ -125,7 +130,7 @@ size_t split_part_elems(int n_chunks, int cols);
 cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
                               const int *Ew, int64_t c, int seg0, int n_seg, int chunk0,
                               int n_chunks, int n_ct, int cols, float2 *part, unsigned int *err,
-                              cudaStream_t st);
+                              long long wait_cycles, cudaStream_t st);
 
 // G[kind][t][col] = sum of the float-float partials over chunks, for blocks
 // of L targets: rounded to double, or (_ff) kept as float-float pairs.
@@ -137,6 +142,38 @@ cudaError_t launch_combine_split_ff(const float2 *part, int n_chunks, int cols, 
 // out[i] = scale * W[i] as a float-float pair, i < n.
 cudaError_t launch_ff_weights(const double *W, double scale, int64_t n, float2 *out,
                               cudaStream_t st);
+
+// ---- tensor path, wide far history (history_far.cu) ----
+// Point groups of 128 (two blocks of 64); the far history of a pair of blocks
+// (target group C: m = 128C+1 .. 128C+128) over the groups 0 .. C-2 on tensor
+// cores with 128 targets per MMA, one weight kind per CTA.
+
+// f of group S -> bf16 slices Fs (far_group_slice_elems() per group and
+// column tile) and per-column exponents Ef (128 per group and column tile).
+cudaError_t launch_slice_group(const DevBatch &bt, int n_ct, int64_t S, __nv_bfloat16 *Fs, int *Ef,
+                               cudaStream_t st);
+// Hankel weight tiles (far_group_tile_elems() per group lag) and exponents
+// (2 per lag) for the group lags 2 .. G_max.
+cudaError_t launch_hankel_group(const double *WB, const double *WA, int64_t G_max,
+                                __nv_bfloat16 *WH, int *Ew, cudaStream_t st);
+size_t far_group_tile_elems();
+size_t far_group_slice_elems();
+// Kernel attributes of the wide far kernel; call once per device, outside any
+// graph capture.
+cudaError_t prepare_hist_far();
+// float2 elements of the wide far kernel's partials for n_chunks chunks.
+size_t far_part_elems(int n_chunks, int cols);
+// Far history of target group C over the point groups 0 .. n_grp-1 (n_grp <=
+// C-1), n_chunks chunks of groups per column tile and kind:
+// part[chunk][kind][128][cols] float-float pairs.
+cudaError_t launch_hist_far(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
+                            const int *Ew, int64_t C, int n_grp, int n_chunks, int n_ct, int cols,
+                            float2 *part, unsigned int *err, long long wait_cycles,
+                            cudaStream_t st);
+// G[kind][t][col] (64 targets) = far[.][kind][off + t][col] over n_far chunks
+// (off 0 or 64) + near[.][kind][t][col] over n_near chunks, float-float.
+cudaError_t launch_combine_far(const float2 *far, int n_far, int off, const float2 *nearp,
+                               int n_near, int cols, float2 *G, cudaStream_t st);
 
 // a4 + a5 on the tensor-history path, one lane per column (recurrence_cols.cu):
 // the 64 steps of block c given G, the history of every point k < 64c as

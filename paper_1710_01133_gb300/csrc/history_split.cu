@@ -36,8 +36,8 @@
 //
 // CTA layout (1 CTA per SM, 384 threads): warp 0 streams segments into a
 // 3-stage shared-memory ring with bulk copies; warp 1 issues the MMAs into one
-// of two TMEM accumulator sets (512 columns), one weight kind at a time with
-// per-kind barriers; warps 2..9 drain the other set, each warp one TMEM lane
+// of two TMEM accumulator sets (512 columns), both weight kinds at once with
+// their MMAs interleaved; warps 2..9 drain the other set, each warp one TMEM lane
 // quadrant (its columns) and the 64 targets of one kind, with
 // Kahan-compensated fp32 sums held in registers.  A warp can only read the
 // TMEM lanes of its own sub-partition, so quadrant 1 is drained on the MMA
@@ -46,7 +46,11 @@
 // that the MMA thread keeps its issue slots.  Measured in isolation: the copy
 // ring alone streams at the HBM peak, the MMAs alone reach ~0.6 of the bf16
 // peak (N = 64 per MMA), the full kernel 0.47-0.53 (0.43-0.49 with the whole
-// drain on the MMA warp's sub-partition).
+// drain on the MMA warp's sub-partition).  An M = 128, N = 64, K = 16 MMA
+// reads 6 KB of operands from shared memory, which at the 128 B per clock an
+// SM delivers takes 48 clocks against 32 of compute (measured: N = 128 takes
+// its 64 compute clocks), so this shape caps at ~0.67 of the tensor pipe; the
+// 128-target kernel (history_far.cu) is the fast path for long histories.
 // Every wait is bounded; on timeout the CTA sets an error flag, waits for its
 // own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -76,7 +80,10 @@ constexpr int kEpiWarps = 8;
 constexpr int kEpiT = 64;         // targets per drain thread
 constexpr int kStashBytes = 2 * 2 * kEpiT * 32 * 4;  // [buffer][kind][target][column]
 constexpr size_t kSmemBytes = (size_t)kStages * kStageStride + 1024 + kStashBytes;
-constexpr long long kWaitCycles = 4000000000LL;      // ~2 s at 2 GHz
+// limit of the waits that wait for the rest of the CTA (launch parameter,
+// default ~2 s at 2 GHz); waits for the CTA's own copies and MMAs to land,
+// which always complete, keep the default
+constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ int exp_clamp(int e) { return e < -126 ? -126 : (e > 127 ? 127 : e); }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((exp_clamp(e) + 127) << 23); }
@@ -214,6 +221,7 @@ struct SplitArgs {
     int n_chunks;             // gridDim.y
     float2 *part;             // [chunk][2][64][cols] (sum, -compensation)
     unsigned int *err;
+    long long wait;           // clock cycles a wait on another warp may take
 };
 
 __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs a)
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
             for (int i = 0; i < nseg && ok; ++i) {
                 const int st = i % kStages;
                 const uint32_t ph = (i / kStages) & 1;
-                if (!mbar_wait(&empty[st], ph ^ 1, kWaitCycles)) {
+                if (!mbar_wait(&empty[st], ph ^ 1, a.wait)) {
                     ok = false;
                     break;
                 }
@@ -279,41 +287,43 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 const uint32_t ph = (i / kStages) & 1;
                 const int b = i & 1;
                 const uint32_t bph = (i >> 1) & 1;
-                if (!mbar_wait(&full[st], ph, kWaitCycles)) {
+                if (!mbar_wait(&full[st], ph, a.wait)) {
                     ok = false;
                     break;
                 }
                 const uint32_t sF = smem_u32(smem + st * kStageStride);
                 const uint32_t sW = sF + kFBytes;
-                // one kind at a time, each with its own accumulator barriers, so
-                // the drain of kind 0 starts while the MMAs of kind 1 run
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (!mbar_wait(&acc_empty[b * 2 + k], bph ^ 1, kWaitCycles)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d0 = tmem + b * 256 + k * 64;  // level 0
-                    const uint32_t d12 = d0 + 128;                // levels 1 and 2
-                    // descriptors as base word + offset/16: few instructions per
-                    // MMA, since this thread shares its issue slots with two
-                    // drain warps
-                    const uint32_t a_lo = smem_desc_lo(sF, 2048);
-                    const uint32_t b_lo = smem_desc_lo(sW + k * 3 * (kHk * 128), 128);
-                    constexpr uint32_t a_hi = smem_desc_hi(128), b_hi = smem_desc_hi(128);
-#pragma unroll
-                    for (int s = 0; s < kSeg / 16; ++s) {
-                        constexpr uint32_t fq = (kFBytes / 3) >> 4, wq = (kHk * 128) >> 4;
-                        const uint32_t ao = a_lo + s * (4096 >> 4), bo = b_lo + s * (256 >> 4);
-                        mma_bf16_split6(d0, d12, desc_join(ao, a_hi), desc_join(ao + fq, a_hi),
-                                        desc_join(ao + 2 * fq, a_hi), desc_join(bo, b_hi),
-                                        desc_join(bo + wq, b_hi), desc_join(bo + 2 * wq, b_hi),
-                                        idesc, s == 0);
-                    }
-                    mma_commit(&acc_full[b * 2 + k]);
+                // both kinds at once, their dependent MMAs interleaved (see
+                // mma_bf16_split6x2); the drain of this buffer runs during the
+                // next segment's MMAs, which use the other buffer
+                if (!mbar_wait(&acc_empty[b * 2], bph ^ 1, a.wait) ||
+                    !mbar_wait(&acc_empty[b * 2 + 1], bph ^ 1, a.wait)) {
+                    ok = false;
+                    break;
                 }
-                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d0 = tmem + b * 256;  // level 0, kind 0 (kind 1: +64)
+                const uint32_t d12 = d0 + 128;       // levels 1 and 2
+                // descriptors as base word + offset/16: few instructions per
+                // MMA, since this thread shares its issue slots with two drain
+                // warps
+                const uint32_t a_lo = smem_desc_lo(sF, 2048);
+                const uint32_t b_lo = smem_desc_lo(sW, 128);
+                constexpr uint32_t a_hi = smem_desc_hi(128), b_hi = smem_desc_hi(128);
+                constexpr uint32_t fq = (kFBytes / 3) >> 4, wq = (kHk * 128) >> 4;
+                constexpr uint32_t kq = (3 * kHk * 128) >> 4;  // kind 1's weight tiles
+#pragma unroll
+                for (int s = 0; s < kSeg / 16; ++s) {
+                    const uint32_t ao = a_lo + s * (4096 >> 4), bo = b_lo + s * (256 >> 4);
+                    mma_bf16_split6x2(d0, d12, d0 + 64, d12 + 64, desc_join(ao, a_hi),
+                                      desc_join(ao + fq, a_hi), desc_join(ao + 2 * fq, a_hi),
+                                      desc_join(bo, b_hi), desc_join(bo + wq, b_hi),
+                                      desc_join(bo + 2 * wq, b_hi), desc_join(bo + kq, b_hi),
+                                      desc_join(bo + kq + wq, b_hi),
+                                      desc_join(bo + kq + 2 * wq, b_hi), idesc, s == 0);
+                }
+                mma_commit(&acc_full[b * 2]);
+                mma_commit(&acc_full[b * 2 + 1]);
                 mma_commit(&empty[st]);
             }
             mma_commit(done);
@@ -335,8 +345,8 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                 ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
                 ew_next = a.Ew[(a.c - sn) * 2 + kind];
             }
-            if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles) ||
-                !mbar_wait(&stash_empty[b * 2 + kind], bph ^ 1, kWaitCycles)) {
+            if (!mbar_wait(&acc_full[b * 2 + kind], bph, a.wait) ||
+                !mbar_wait(&stash_empty[b * 2 + kind], bph ^ 1, a.wait)) {
                 ok = false;
                 break;
             }
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
             for (int i = 0; i < nseg; ++i) {
                 const int b = i & 1;
                 const uint32_t bph = (i >> 1) & 1;
-                if (!mbar_wait(&stash_full[b * 2 + kind], bph, kWaitCycles)) {
+                if (!mbar_wait(&stash_full[b * 2 + kind], bph, a.wait)) {
                     ok = false;
                     break;
                 }
@@ -421,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
                     ef_next = a.Ef[(sn * a.n_ct + ct) * kMC + cloc];
                     ew_next = a.Ew[(a.c - sn) * 2 + kind];
                 }
-                if (!mbar_wait(&acc_full[b * 2 + kind], bph, kWaitCycles)) {
+                if (!mbar_wait(&acc_full[b * 2 + kind], bph, a.wait)) {
                     ok = false;
                     break;
                 }
@@ -564,13 +574,14 @@ size_t split_part_elems(int n_chunks, int cols) { return (size_t)n_chunks * 2 * 
 cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv_bfloat16 *WH,
                               const int *Ew, int64_t c, int seg0, int n_seg, int chunk0,
                               int n_chunks, int n_ct, int cols, float2 *part, unsigned int *err,
-                              cudaStream_t st)
+                              long long wait_cycles, cudaStream_t st)
 {
     if (n_seg < 1) return cudaSuccess;
+    if (wait_cycles <= 0) wait_cycles = kWaitCycles;
     // segments lie before block c: lag g = c - seg >= 1
     if (seg0 < 0 || seg0 + n_seg > c || n_chunks < 1 || n_chunks > n_seg || chunk0 < 0)
         return cudaErrorInvalidValue;
-    SplitArgs a{Fs, Ef, WH, Ew, c, n_ct, cols, seg0, n_seg, chunk0, n_chunks, part, err};
+    SplitArgs a{Fs, Ef, WH, Ew, c, n_ct, cols, seg0, n_seg, chunk0, n_chunks, part, err, wait_cycles};
     hist_split_kernel<<<dim3((unsigned)n_ct, (unsigned)n_chunks), kThreads, kSmemBytes, st>>>(a);
     return cudaGetLastError();
 }

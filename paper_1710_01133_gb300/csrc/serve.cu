@@ -529,7 +529,8 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
         s.req = r;
         s.bytes = bytes;
         s.nblk = (r.N + kSL - 1) / kSL;
-        cudaError_t e = cudaMallocAsync(&s.mem, bytes, S->sR);
+        cudaError_t e = take_injected_alloc_failure() ? cudaErrorMemoryAllocation
+                                                      : cudaMallocAsync(&s.mem, bytes, S->sR);
         if (e != cudaSuccess) {
             if (S->slots.empty()) {
                 S->queue.pop_front();

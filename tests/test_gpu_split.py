@@ -3,7 +3,9 @@
 The history sums run as bf16 tcgen05 products of fixed-point slices; the bar
 is the mixed-precision one: max_n |y_gpu - y_oracle| / S_i <= 1e-6, S_i the
 largest |y_oracle| of component i of the trajectory.  Sizes span several
-64-point segments, several 128-column tiles and ragged tails.
+64-point segments, several 128-column tiles and ragged tails.  Both tensor
+tilings run: "tensor-wide" (far history of pairs of blocks, 128 targets per
+MMA, 128-point groups) and "tensor" (64 targets per MMA, 64-point segments).
 """
 import math
 
@@ -16,9 +18,10 @@ from fabm_workloads import (duffing_sweep, lcr_sweep, lorenz_long, lorenz_single
 
 pytestmark = pytest.mark.gpu
 TOL_SPLIT = 1e-6
-HISTS = ["tensor", "fp32c"]
+HISTS = ["tensor-wide", "tensor", "fp32c"]
 # history kernel and, on the tensor path, the recurrence layout
-PATHS = [("tensor", "columns"), ("tensor", "targets"), ("fp32c", None)]
+PATHS = [("tensor-wide", "columns"), ("tensor-wide", "targets"), ("tensor", "columns"),
+         ("tensor", "targets"), ("fp32c", None)]
 
 
 def rel_err(got, ref):
@@ -77,8 +80,9 @@ def test_split_duffing_batch_several_column_tiles(gpu_lib, parity, hist, rec):
         parity(rel_err(got[b, : n + 1], ref[j, : n + 1]), TOL_SPLIT, b)
 
 
+@pytest.mark.parametrize("hist", ["tensor-wide", "tensor"])
 @pytest.mark.parametrize("rec", ["columns", "targets"])
-def test_split_lorenz_batch_partial_warps(gpu_lib, parity, rec):
+def test_split_lorenz_batch_partial_warps(gpu_lib, parity, rec, hist):
     """23 Lorenz trajectories on the tensor path: the column recurrence puts 10
     trajectories (30 columns) in a warp, so the warps hold 10, 10 and 3 of them
     and two lanes of each warp idle; lengths differ inside a warp, including
@@ -88,7 +92,7 @@ def test_split_lorenz_batch_partial_warps(gpu_lib, parity, rec):
     ne[::6] = 777
     ne[[1, 13, 21]] = [5, 1280, 1999]
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
-                        history="tensor", recurrence=rec) as s:
+                        history=hist, recurrence=rec) as s:
         got = s.solve_batch(w.y0, N_each=ne)
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0, params=w.params, N_each=ne)
     for b in range(w.B):
@@ -170,10 +174,58 @@ def test_autotune_picks_a_candidate_and_stays_correct(gpu_lib, parity):
     w = duffing_sweep(B=96, N=2000)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
         rep = s.autotune(w.y0, traj_params=w.traj_params, n_probe=1024)
-        assert len(rep) == 7 and all(ms > 0 for ms, _, _ in rep)
+        assert len(rep) == 8 and all(ms > 0 for ms, _, _ in rep)
+        assert {k for _, k, _ in rep} == {gpu_lib.FABM_HIST_TENSOR_WIDE, gpu_lib.FABM_HIST_TENSOR,
+                                          gpu_lib.FABM_HIST_FP32C}
         best = min(rep)[1]
         assert gpu_lib.fabm_get_history_kernel(s.handle) == best
         got = s.solve_batch(w.y0[:4], traj_params=w.traj_params[:4])
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[:4], params=w.params,
                              traj_params=w.traj_params[:4])
     parity(rel_err(got, ref), TOL_SPLIT, "")
+
+
+@pytest.mark.parametrize("N", [255, 256, 257, 383, 384, 385, 511, 512, 513, 767, 769, 1025])
+def test_wide_far_history_group_edges_closed_form(gpu_lib, N):
+    """The 128-target far history starts at block 4 (target group 2, point group
+    0) and steps by pairs of blocks; lengths around group and pair edges, on the
+    constant right-hand side whose scheme is exact."""
+    alpha, h = 0.7, 0.01
+    B = 40  # 40 trajectories x 2 components = 80 columns: one column tile, ragged
+    with gpu_lib.Solver("const", 2, alpha, h, N, [1.5], precision="split",
+                        history="tensor-wide") as s:
+        y = s.solve_batch(np.full((B, 2), 0.25))
+        assert gpu_lib.fabm_get_history_kernel(s.handle) == gpu_lib.FABM_HIST_TENSOR_WIDE
+    t = np.arange(N + 1) * h
+    ex = 0.25 + 1.5 * t ** alpha / math.gamma(alpha + 1)
+    assert np.max(np.abs(y - ex[None, :, None])) / np.max(np.abs(ex)) < TOL_SPLIT
+
+
+def test_wide_and_narrow_tilings_agree_with_the_oracle(gpu_lib, parity):
+    """Duffing batch (160 trajectories, 320 columns: three column tiles, the
+    last ragged) with uneven lengths, order above one (weights growing with the
+    distance) on the linear right-hand side, both tilings against the oracle."""
+    w = duffing_sweep(B=160, N=2500)
+    ne = np.full(w.B, w.N, dtype=np.int64)
+    ne[::5] = 1300
+    ne[7] = 300
+    idx = np.array([0, 7, 64, 100, 159])
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
+                             traj_params=w.traj_params[idx], N_each=ne[idx])
+    for hist in ("tensor-wide", "tensor"):
+        with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
+                            history=hist) as s:
+            got = s.solve_batch(w.y0, traj_params=w.traj_params, N_each=ne)
+        for j, b in enumerate(idx):
+            n = ne[b]
+            parity(rel_err(got[b, : n + 1], ref[j, : n + 1]), TOL_SPLIT, f"{hist}-{b}")
+    alpha, N = 1.4, 1500
+    y0 = np.linspace(0.5, 1.5, 70).reshape(70, 1)
+    y1 = np.linspace(-1.0, 1.0, 70).reshape(70, 1)
+    refh = oracle.solve_batch("linear", alpha, 1e-3, N, y0[[0, 35, 69]], params=[1.0],
+                              y1=y1[[0, 35, 69]])
+    with gpu_lib.Solver("linear", 1, alpha, 1e-3, N, [1.0], precision="split",
+                        history="tensor-wide") as s:
+        goth = s.solve_batch(y0, y1=y1)
+    for j, b in enumerate([0, 35, 69]):
+        parity(rel_err(goth[b], refh[j]), TOL_SPLIT, f"alpha1.4-{b}")
