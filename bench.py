@@ -5,8 +5,11 @@
 
 One "step" is one whole solve of the workload (every block of the history
 sums, the recurrence, initial values) through the C ABI.  The default
-workload is the 3-dim Lorenz-type system, alpha = 0.98, h = 5e-4, N = 2^18
-steps, one trajectory, plain FP64.
+workload is the largest single-GPU configuration: 256 trajectories of the
+3-dim Lorenz-type system, alpha = 0.95, h = 1e-4, N = 2^20 steps, in split
+precision (history sums on tensor cores).  The same run times the plain FP64
+single-trajectory solve (Lorenz-type, alpha = 0.98, h = 5e-4, N = 2^18) as
+``vs_fp64_path``: the batched split path against the plain FP64 path.
 
 Timing: W untimed warm-up solves, then K timed solves, each bracketed by CUDA
 events, with a 256 MiB buffer written between them to flush L2.  The library
@@ -43,9 +46,17 @@ WORKLOADS = {
     "lorenz-single": lambda: wl.lorenz_single(),
     "ml-scalar": lambda: wl.ml_scalar(),
     "duffing-sweep": lambda: wl.duffing_sweep(),
-    "lorenz-long": lambda: wl.lorenz_long(),
+    "lorenz-long": lambda: _lorenz_long(),
     "lcr-sweep": lambda: _lcr_sweep(),
 }
+DEFAULT_WORKLOAD = "lorenz-long"
+
+
+def _lorenz_long():
+    """256 Lorenz-type trajectories x 2^20 steps, split precision by default."""
+    w = wl.lorenz_long()
+    w.precision = "split"
+    return w
 
 
 def _lcr_sweep():
@@ -212,10 +223,17 @@ def _measured_peaks():
         return 6800.0, 1900.0, "of fallback"
 
 
-def roofline(kind, ks, precision, clocks, workload):
-    """Roofline line for the dominant kernel class from the library's sampled
-    CUDA-event stats: achieved = algorithmic work of the timed launches /
-    their total duration."""
+def roofline(kind, ks, precision, clocks, workload, w=None, step_ms=None):
+    """Roofline line for the dominant kernel class.
+
+    For the history kernels the headline `achieved` is the algorithmic history
+    work of one whole solve (2 N^2 flops per column: the predictor and the
+    corrector sum, one multiply-add per past point each) divided by the
+    uninstrumented solve time `step_ms`: a lower bound on the kernel's rate,
+    since the solve also runs the recurrence and the launches between blocks.
+    `in_launch` gives the same work per timed launch divided by the time those
+    launches ran (CUDA events on the launching streams, overlaps counted once),
+    taken on separate instrumented solves."""
     n, flops = ks["launches"], ks["flops"]
     # time during which the timed launches ran, overlaps counted once (history
     # launches of consecutive blocks overlap on two streams in long FP64 solves)
@@ -223,40 +241,83 @@ def roofline(kind, ks, precision, clocks, workload):
     avg_us = ks["ms"] * 1e3 / max(n, 1)
     hbm, bf16, src = _measured_peaks()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    out = {"kernel": f"{kind} ({precision})", "launches_timed": n, "avg_launch_us": avg_us,
-           "busy_ms": ms, "achieved_over": "union of the timed launches' intervals"}
-    if kind == "history" and precision == "split":
+    out = {"kernel": f"{kind} ({precision})"}
+    tensor = kind == "history" and precision == "split"
+    if tensor:
         # 6 bf16 products per algorithmic multiply-add (three-term split, order <= 2)
-        achieved = 6.0 * flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-        out.update({"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
-                    "frac": achieved / bf16 if bf16 else None,
+        mult, unit, scale, peak = 6.0, "TFLOP/s", 1e12, bf16
+        out.update({"bound": "tensor",
                     "peak_note": f"dense bf16 burst {src} (MEASURED_PEAKS.json); achieved counts "
                                  "the 6 bf16 products per algorithmic multiply-add"})
     elif kind == "recurrence" and precision == "split":
         # float-float on the FP32 pipe: algorithmic near-field FLOP/s against FP32 FMA
+        mult, unit, scale = 1.0, "GFLOP/s", 1e9
         peak = FP32_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
-        achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": achieved / peak if peak else None,
+        out.update({"bound": "alu",
                     "peak_note": "FP32 FMA pipe: 128 FFMA/clk/SM x 152 SMs x max SM clock "
                                  "(probe: 74.7 TFLOP/s); a latency-bound serial chain, each "
                                  "algorithmic multiply-add costs ~15 float-float operations"})
     else:
+        mult, unit, scale = 1.0, "GFLOP/s", 1e9
         peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * sm_max * 1e6 / 1e9
-        achieved = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
         note = ("FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x max SM clock "
                 "(probe: 1.19 TFLOP/s at 1.96 GHz)")
         if precision == "fp64x2":
             note += ("; achieved counts algorithmic multiply-adds, each of which costs ten "
                      "FP64 operations in double-double")
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": achieved / peak if peak else None, "peak_note": note})
+        out.update({"bound": "alu", "peak_note": note})
+    in_launch = mult * flops / (ms * 1e-3) / scale if ms > 0 else 0.0
+    out["in_launch"] = {"launches_timed": n, "avg_launch_us": avg_us, "busy_ms": ms,
+                        "achieved": in_launch, "frac": in_launch / peak if peak else None,
+                        "over": "union of the timed launches' intervals (instrumented solves)"}
+    if kind == "history" and w is not None and step_ms:
+        solve_flops = 2.0 * w.history_macs()
+        achieved = mult * solve_flops / (step_ms * 1e-3) / scale
+        out.update({"achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak if peak else None,
+                    "work_per_step": mult * solve_flops,
+                    "achieved_over": "whole uninstrumented solve: algorithmic history work "
+                                     "(2 N^2 flops per column) / ms_per_step"})
+    else:
+        out.update({"achieved": in_launch, "peak": peak, "unit": unit,
+                    "frac": in_launch / peak if peak else None,
+                    "achieved_over": out["in_launch"]["over"]})
     key = {"history": f"history_{'split' if precision == 'split' else 'fp64'}",
            "recurrence": "recurrence"}.get(kind)
     # profiles/<kernel class>_<precision>_<workload>.md, e.g. history_fp64_lorenz-single.md
     traffic = _profile_traffic(key, f"{kind}_{precision}_{workload}") if key else None
     out["traffic"] = traffic
     return out
+
+
+def fp64_comparator(steps, warmup):
+    """The plain FP64 single-trajectory solve (Lorenz-type, alpha 0.98,
+    h 5e-4, N 2^18) timed the same way as the headline: the path the batched
+    split solve is compared with."""
+    import torch
+
+    import paper_1710_01133_gb300 as fabm
+    w = wl.lorenz_single()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out_dev = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, device="cuda")
+    with fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
+        for _ in range(warmup):
+            s.solve_batch(w.y0, out=out_dev)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve_batch(w.y0, out=out_dev)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    return {"workload": w.name, "precision": "fp64", "trajectories": w.B, "steps_N": w.N,
+            "value": w.steps_traj() / (ms * 1e-3), "unit": "steps*traj/s", "ms_per_step": ms,
+            "steps": steps, "warmup": warmup}
 
 
 def cpu_baseline(w, target_s=12.0):
@@ -408,7 +469,8 @@ def run_served(args):
 
 
 def _config(w, args):
-    return {"workload": w.name, "precision": args.precision, "rhs": w.rhs, "dim": w.dim,
+    return {"workload": w.name, "precision": args.precision,
+            "history_kernel": getattr(args, "history", "auto"), "rhs": w.rhs, "dim": w.dim,
             "alpha": w.alpha, "h": w.h, "steps_N": w.N, "trajectories": w.B,
             "l2": "flushed between timed solves (256 MiB write)"}
 
@@ -419,7 +481,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fabm", choices=["fabm", "reference"])
-    ap.add_argument("--workload", default="lorenz-single",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + ["served-mix"])
     ap.add_argument("--precision", default=None, choices=["fp64", "split", "fp64x2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -436,6 +498,13 @@ def main():
     ap.add_argument("--k-max", type=int, default=14, help="served-mix: N = 2^k, k <= k_max")
     ap.add_argument("--recurrence", default="auto", choices=["auto", "columns", "targets"],
                     help="split precision, tensor history: layout of the recurrence")
+    ap.add_argument("--history", default="auto",
+                    choices=["auto", "tensor", "tensor-wide", "fp32c", "fp64", "x2"],
+                    help="history kernel (auto: the library's choice)")
+    ap.add_argument("--no-fp64-comparator", action="store_true",
+                    help="skip timing the plain FP64 single-trajectory solve (vs_fp64_path)")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end solves timed (at most --steps)")
     args = ap.parse_args()
     if args.workload == "served-mix":
         if args.precision is None:
@@ -465,7 +534,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fabm.load()
     solver = fabm.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision=args.precision,
-                         recurrence=args.recurrence)
+                         recurrence=args.recurrence,
+                         history=None if args.history == "auto" else args.history)
     wstats = solver.kernel_stats()["weights"]
     tuned = None
     if args.autotune > 0:
@@ -523,8 +593,9 @@ def main():
     out_host = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, pin_memory=True)
     solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_host)
     e2e_times = []
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -535,6 +606,11 @@ def main():
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = dist_max(float(np.mean(e2e_times)), "cuda")
     finite = bool(torch.isfinite(out_dev).all().item())
+    del out_host
+    comparator = None
+    if not args.no_fp64_comparator and not (args.workload == "lorenz-single"
+                                            and args.precision == "fp64"):
+        comparator = fp64_comparator(max(3, min(args.steps, 5)), 3)
 
     if rank == 0:
         units = w.steps_traj() * ws  # replicas: every rank solves its own copy
@@ -542,7 +618,7 @@ def main():
         # the kinds that do the method's arithmetic (both are timed on the same
         # sampled blocks; combine, slice and init only move or convert data)
         dom = max(("history", "recurrence"), key=lambda k: kstats[k]["busy_ms"] or kstats[k]["ms"])
-        line_roof = roofline(dom, kstats[dom], args.precision, clocks, args.workload)
+        line_roof = roofline(dom, kstats[dom], args.precision, clocks, args.workload, w, step_ms)
         h2d = w.B * w.dim * 8 + w.B * 8 * 8 + w.B * 8
         d2h = w.B * (w.N + 1) * w.dim * 8 + 8
         line = {
@@ -551,7 +627,8 @@ def main():
             "unit": "steps*traj/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64x2" if args.precision == "fp64x2" else "f64",
+            "vs_baseline": None,
+            "dtype": {"fp64x2": "f64x2", "split": "bf16x3"}.get(args.precision, "f64"),
             "data": "synthetic",
             "config": _config(w, args),
             "history_gmac_s": w.history_macs() * ws / (step_ms * 1e-3) / 1e9,
@@ -566,7 +643,8 @@ def main():
                              f"(the timed solves carry no events)",
             "weights_ms": wstats["ms"],
             "e2e": {"value": replica_throughput(w.steps_traj(), ws, e2e_ms), "unit": "steps*traj/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
             "autotune": None if tuned is None else {
@@ -574,6 +652,9 @@ def main():
                 "candidates_ms_kernel_setting": [[round(m, 3), k, c] for m, k, c in tuned]},
             "output_finite": finite,
         }
+        if comparator is not None:
+            comparator["ratio"] = line["value"] / comparator["value"]
+            line["vs_fp64_path"] = comparator
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line))

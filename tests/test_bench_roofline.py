@@ -50,3 +50,22 @@ def test_committed_summaries_name_their_command_and_hash():
         txt = open(os.path.join(ROOT, "profiles", name)).read()
         assert "ncu " in txt and "--clock-control none" in txt, name
         assert "source_sha256:" in txt and "traffic_bytes_per_full_launch:" in txt, name
+
+
+def test_headline_is_the_solve_work_over_the_uninstrumented_step():
+    """With the workload and the uninstrumented step time given, `achieved` is
+    2 N^2 flops per column (x6 bf16 products on the tensor path) over
+    ms_per_step, and the instrumented per-launch rate moves to `in_launch`."""
+    import fabm_workloads as wl
+    w = wl.lorenz_long(B=4, N=1024)
+    macs = w.history_macs()
+    assert macs == pytest.approx(4 * 3 * 1024.0 ** 2)
+    line = bench.roofline("history", STATS, "split", {"sm_max_mhz": 2070.0}, "lorenz-long",
+                          w, 100.0)
+    assert line["achieved"] == pytest.approx(6 * 2 * macs / 0.1 / 1e12)
+    assert line["work_per_step"] == pytest.approx(6 * 2 * macs)
+    assert line["in_launch"]["achieved"] == pytest.approx(6 * 1.0e12 / 1.0 / 1e12)
+    assert line["frac"] == pytest.approx(line["achieved"] / line["peak"])
+    fp64 = bench.roofline("history", STATS, "fp64", {"sm_max_mhz": 2070.0}, "lorenz-single",
+                          w, 100.0)
+    assert fp64["achieved"] == pytest.approx(2 * macs / 0.1 / 1e9)
