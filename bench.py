@@ -159,7 +159,7 @@ class ClockSampler:
 # traffic only while the sha256 over these files (in this order) still matches.
 KERNEL_SOURCES = {
     "history_fp64": ["history_fp64.cu", "history_blocks.cuh", "fabm_internal.cuh"],
-    "history_split": ["history_split.cu", "sm100_ptx.cuh", "fabm_internal.cuh"],
+    "history_split": ["history_far.cu", "history_split.cu", "sm100_ptx.cuh", "fabm_internal.cuh"],
     "recurrence": ["recurrence.cu", "recurrence.cuh", "rhs.cuh", "fabm_internal.cuh"],
 }
 
@@ -504,7 +504,9 @@ def main():
     ap.add_argument("--no-fp64-comparator", action="store_true",
                     help="skip timing the plain FP64 single-trajectory solve (vs_fp64_path)")
     ap.add_argument("--e2e-steps", type=int, default=3,
-                    help="end-to-end solves timed (at most --steps)")
+                    help="end-to-end solves timed (at most --steps; 0: no end-to-end leg)")
+    ap.add_argument("--stat-solves", type=int, default=2,
+                    help="instrumented solves for the per-launch kernel statistics (0: none)")
     args = ap.parse_args()
     if args.workload == "served-mix":
         if args.precision is None:
@@ -577,23 +579,26 @@ def main():
     barrier()
     # per-kernel statistics for the roofline: the same solve with CUDA events
     # around the launches of the sampled blocks, run after the timed ones
-    stat_solves = min(args.steps, 2)
-    solver.set_timing(args.timing_period)
-    solve_dev()  # builds the instrumented graph
-    solver.set_timing(args.timing_period)  # resets the counters
-    for _ in range(stat_solves):
-        flush.fill_(1.0)
-        solve_dev()
+    stat_solves = min(args.steps, args.stat_solves)
+    if stat_solves > 0:
+        solver.set_timing(args.timing_period)
+        solve_dev()  # builds the instrumented graph
+        solver.set_timing(args.timing_period)  # resets the counters
+        for _ in range(stat_solves):
+            flush.fill_(1.0)
+            solve_dev()
     barrier()
     kstats = solver.kernel_stats()
     solver.set_timing(0)
     step_ms = dist_max(float(np.mean(times)), "cuda")
 
     # end to end: host y0 in, host trajectory out (pinned), copies timed
-    out_host = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, pin_memory=True)
-    solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_host)
     e2e_times = []
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_steps = min(args.steps, args.e2e_steps)
+    out_host = None
+    if e2e_steps > 0:
+        out_host = torch.empty((w.B, w.N + 1, w.dim), dtype=torch.float64, pin_memory=True)
+        solver.solve_batch(w.y0, traj_params=w.traj_params, N_each=w.N_each, out=out_host)
     barrier()
     for _ in range(e2e_steps):
         flush.fill_(1.0)
@@ -604,7 +609,7 @@ def main():
         e1.record()
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = dist_max(float(np.mean(e2e_times)), "cuda")
+    e2e_ms = dist_max(float(np.mean(e2e_times)), "cuda") if e2e_times else None
     finite = bool(torch.isfinite(out_dev).all().item())
     del out_host
     comparator = None
@@ -642,9 +647,10 @@ def main():
                              f"{min(args.steps, 2)} instrumented solves after the timed ones "
                              f"(the timed solves carry no events)",
             "weights_ms": wstats["ms"],
-            "e2e": {"value": replica_throughput(w.steps_traj(), ws, e2e_ms), "unit": "steps*traj/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "steps": e2e_steps},
+            "e2e": None if e2e_ms is None else {
+                "value": replica_throughput(w.steps_traj(), ws, e2e_ms), "unit": "steps*traj/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
             "autotune": None if tuned is None else {

@@ -164,11 +164,18 @@ enum {
                               with 64 targets per MMA (split precision)              */
     FABM_HIST_FP32C = 3,   /* compensated fp32 on CUDA cores (split precision)       */
     FABM_HIST_X2 = 4,      /* double-double on CUDA cores (FP64X2 precision only)    */
-    FABM_HIST_TENSOR_WIDE = 5 /* as FABM_HIST_TENSOR, but the far history of each pair
+    FABM_HIST_TENSOR_WIDE = 5, /* as FABM_HIST_TENSOR, but the far history of each pair
                               of blocks with 128 targets per MMA (one weight kind per
                               CTA, exact per 128-point group), the latest two or three
                               64-point segments per block with 64; automatic choice
                               on the tensor path from N >= 384 on                     */
+    FABM_HIST_FP64_PERSIST = 6 /* FP64 precision, the whole solve as one persistent
+                              cooperative launch: one CTA per trajectory runs its
+                              recurrence with weights and the recent window of f in
+                              shared memory, the other CTAs sum the far history
+                              (as FABM_HIST_FP64) and hand it over through device
+                              flags; automatic choice for FP64 batches of at most 16
+                              single-order trajectories                              */
 };
 
 /* Choose the history kernel (one of FABM_HIST_*; must fit the precision).
@@ -254,6 +261,11 @@ fabm_status fabm_inject_alloc_failures(int n);
  * the predictor weights of Eq. abm and the corrector weights of Sec. 2 in the
  * distance form d = (n+1) - k used by the kernels.  Any of B, A, D may be NULL. */
 fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D);
+/* FABM_FP64X2 solvers: the low parts of the double-double weights whose high
+ * parts fabm_copy_weights returns (value = high + low), computed on the device
+ * in double-double arithmetic.  FABM_EINVAL for other precisions or n outside
+ * 0..N+1. */
+fabm_status fabm_copy_weights_lo(fabm_solver *s, int64_t n, double *Bl, double *Al, double *Dl);
 
 /* The weights B(d), A(d), D(m) of fabm_copy_weights for d, m = 0..n in
  * double-double: hi is the double nearest the value, lo the rounded rest

@@ -17,8 +17,9 @@ from . import build as _build
 FABM_OK, FABM_EINVAL, FABM_ENOMEM, FABM_ECUDA, FABM_ENONFINITE, FABM_ETIMEOUT, FABM_EBUSY = range(7)
 FABM_FP64, FABM_SPLIT, FABM_FP64X2 = 0, 1, 2
 FABM_HIST_AUTO, FABM_HIST_FP64, FABM_HIST_TENSOR, FABM_HIST_FP32C = range(4)
-FABM_HIST_X2, FABM_HIST_TENSOR_WIDE = 4, 5
-HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3, "x2": 4, "tensor-wide": 5}
+FABM_HIST_X2, FABM_HIST_TENSOR_WIDE, FABM_HIST_FP64_PERSIST = 4, 5, 6
+HIST = {"auto": 0, "fp64": 1, "tensor": 2, "fp32c": 3, "x2": 4, "tensor-wide": 5,
+        "fp64-persist": 6}
 RECURRENCE = {"auto": 0, "columns": 1, "targets": 2}
 RHS = {"const": 0, "time": 1, "linear": 2, "lorenz": 3, "duffing": 4, "manufactured": 5,
        "lcr": 6}
@@ -33,7 +34,8 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_server_cancel", "fabm_server_shape", "fabm_solve_batch_ic",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
             "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
-            "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures")
+            "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures",
+            "fabm_copy_weights_lo")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -83,6 +85,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_last_launch_count.argtypes = [vp]
     lib.fabm_last_launch_count.restype = i64
     lib.fabm_copy_weights.argtypes = [vp, i64, P(d), P(d), P(d)]
+    lib.fabm_copy_weights_lo.argtypes = [vp, i64, P(d), P(d), P(d)]
+    lib.fabm_copy_weights_lo.restype = i
     lib.fabm_set_timing.argtypes = [vp, i]
     lib.fabm_set_graphs.argtypes = [vp, i]
     lib.fabm_server_create.argtypes = [ctypes.c_size_t, i, i, P(vp)]
@@ -228,6 +232,13 @@ def fabm_copy_weights(handle, n):
     B, A, D = np.empty(n), np.empty(n), np.empty(n)
     _check(load().fabm_copy_weights(handle, int(n), _dp(B), _dp(A), _dp(D)))
     return B, A, D
+
+
+def fabm_copy_weights_lo(handle, n):
+    """Low parts (Bl, Al, Dl) of an FP64X2 solver's double-double weights, d < n."""
+    Bl, Al, Dl = np.empty(n), np.empty(n), np.empty(n)
+    _check(load().fabm_copy_weights_lo(handle, int(n), _dp(Bl), _dp(Al), _dp(Dl)))
+    return Bl, Al, Dl
 
 
 def fabm_weights_x2(alpha: float, n: int):

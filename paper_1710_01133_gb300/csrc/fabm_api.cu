@@ -122,6 +122,7 @@ struct fabm_solver {
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     long long wait_cycles = 0;         // tensor kernel's wait limit (0: its default)
     bool wide = false;                 // the solve being set up uses the 128-target far history
+    int persist_ctas = 0;              // FP64: CTAs of the persistent kernel resident at once
     int L = kRecurL;                   // block length of the last solve
     int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
     int cols_warps = 1;                // tensor path: warps per CTA of the column recurrence,
@@ -151,6 +152,9 @@ struct fabm_solver {
     DevBuf<__nv_bfloat16> Fs2; // wide far history: f slices per 128-point group
     DevBuf<int> Fe2;           // wide far history: exponents per group
     DevBuf<float2> fpart;      // wide far history: partials of two target groups
+    DevBuf<float2> fsum;       // wide far history: their chunk sums, [C % 2][2][128][cols]
+    DevBuf<double> ppart;      // persistent FP64 solve: partial-sum slots
+    DevBuf<int> pdone, prdone; // persistent FP64 solve: chunks done per block, blocks done per trajectory
     DevBuf<float2> auxb;       // tensor path: forcing tables of kAuxRing blocks
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
@@ -194,7 +198,8 @@ struct fabm_solver {
     ~fabm_solver()
     {
         wB.release(), wA.release(), wD.release(), wH.release(), wHe.release();
-        wH2.release(), wHe2.release(), Fs2.release(), Fe2.release(), fpart.release();
+        wH2.release(), wHe2.release(), Fs2.release(), Fe2.release(), fpart.release(), fsum.release();
+        ppart.release(), pdone.release(), prdone.release();
         wBl.release(), wAl.release(), wDl.release();
         wBf.release(), wAf.release(), wBff.release(), wAff.release(), wDff.release();
         F.release(), Ff.release(), Ystage.release(), G.release(), part.release();
@@ -330,7 +335,15 @@ cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &
 // History kernel for a batch of `cols` columns.
 int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 {
-    if (s->precision == FABM_FP64) return FABM_HIST_FP64;
+    if (s->precision == FABM_FP64) {
+        // one persistent launch per solve for narrow single-order batches: the
+        // recurrence CTAs take B SMs, the rest sum the history
+        const int64_t B = cols / s->dim;
+        const bool fits = !s->multi && s->persist_ctas >= B + 8 && B <= 64;
+        if (s->hist_kernel == FABM_HIST_FP64_PERSIST) return fits ? FABM_HIST_FP64_PERSIST : FABM_HIST_FP64;
+        if (s->hist_kernel == FABM_HIST_AUTO && fits && B <= 16) return FABM_HIST_FP64_PERSIST;
+        return FABM_HIST_FP64;
+    }
     if (s->precision == FABM_FP64X2) return FABM_HIST_X2;
     // one order per component: every column tile would need its own weight
     // operand, so the tensor kernel (one weight operand per tile) is not used
@@ -401,36 +414,37 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
         const int64_t ph = c % s->timing_period;
         s->sample_now = ph == 0 || (lag == 2 && ph < 8);
         const void *Gc = nullptr;
+        HistIn hin;  // tensor path: the history the recurrence starts from
         if (split && c >= 1 && s->wide) {
             // pairs of blocks: the far history of target group C = c/2 over
             // the point groups 0 .. C-2 (128 points each) on sG / sG3, started
             // once R(2C-3) has finished group C-2 and due by R(2C), so it runs
-            // beside the recurrences of blocks 2C-2 and 2C-1; the segments of
-            // 64 points from 2C-2 up to c-1 as a near launch on sR; both
-            // combined on sR
-            float2 *Gbuf = reinterpret_cast<float2 *>(s->G.p) + (size_t)(c % n_gbuf) * 2 * L * cols;
+            // beside the recurrences of blocks 2C-2 and 2C-1, its chunks summed
+            // on the same stream; the segments of 64 points from 2C-2 up to c-1
+            // as a near launch on sR; the recurrence adds the two
             const int64_t C = c / 2;
             const int t = (int)(c % 2);
             const size_t fstride = far_part_elems(far_chunks, (int)cols);
-            const float2 *fp = s->fpart.p + (size_t)(C & 1) * fstride;
-            int n_far = 0;
-            if (C >= 2) {
-                n_far = (int)std::min<int64_t>(far_chunks, C - 1);
-                if (t == 0) {
-                    cudaStream_t fs = (C & 1) ? s->sG3 : s->sG;
-                    float2 *fw = s->fpart.p + (size_t)(C & 1) * fstride;
-                    const double flops = 4.0 * 128.0 * (double)((C - 1) * 128) * (double)cols;
-                    FABM_CUDA_TRY(cudaStreamWaitEvent(fs, s->evR[(c - 3) % kEvRing], 0));
-                    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, fs, 0.0, [&] {
-                        return launch_slice_group(bt, n_ct, C - 2, s->Fs2.p, s->Fe2.p, fs);
-                    }));
-                    FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, fs, flops, [&] {
-                        return launch_hist_far(s->Fs2.p, s->Fe2.p, s->wH2.p, s->wHe2.p, C,
-                                               (int)(C - 1), n_far, n_ct, (int)cols, fw, s->err.p,
-                                               s->wait_cycles, fs);
-                    }));
-                    FABM_CUDA_TRY(cudaEventRecord(s->evF[C & 1], fs));
-                }
+            const size_t sstride = far_part_elems(1, (int)cols);
+            if (C >= 2 && t == 0) {
+                const int n_far = (int)std::min<int64_t>(far_chunks, C - 1);
+                cudaStream_t fs = (C & 1) ? s->sG3 : s->sG;
+                float2 *fw = s->fpart.p + (size_t)(C & 1) * fstride;
+                float2 *fsw = s->fsum.p + (size_t)(C & 1) * sstride;
+                const double flops = 4.0 * 128.0 * (double)((C - 1) * 128) * (double)cols;
+                FABM_CUDA_TRY(cudaStreamWaitEvent(fs, s->evR[(c - 3) % kEvRing], 0));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_SLICE, fs, 0.0, [&] {
+                    return launch_slice_group(bt, n_ct, C - 2, s->Fs2.p, s->Fe2.p, fs);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, fs, flops, [&] {
+                    return launch_hist_far(s->Fs2.p, s->Fe2.p, s->wH2.p, s->wHe2.p, C,
+                                           (int)(C - 1), n_far, n_ct, (int)cols, fw, s->err.p,
+                                           s->wait_cycles, fs);
+                }));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, fs, 0.0, [&] {
+                    return launch_sum_far(fw, n_far, (int)cols, fsw, fs);
+                }));
+                FABM_CUDA_TRY(cudaEventRecord(s->evF[C & 1], fs));
             }
             const int64_t lo = std::max<int64_t>(0, 2 * C - 2);
             const int n_near = (int)(c - lo);
@@ -440,12 +454,14 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                                          0, n_near, n_ct, (int)cols, s->spart.p, s->err.p,
                                          s->wait_cycles, s->sR);
             }));
-            if (n_far > 0) FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evF[C & 1], 0));
-            FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sR, 0.0, [&] {
-                return launch_combine_far(fp, n_far, 64 * t, s->spart.p, n_near, (int)cols, Gbuf,
-                                          s->sR);
-            }));
-            Gc = Gbuf;
+            if (C >= 2) {
+                FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evF[C & 1], 0));
+                hin.G = s->fsum.p + (size_t)(C & 1) * sstride;
+                hin.g_rows = 128;
+                hin.g_off = 64 * t;
+            }
+            hin.near = s->spart.p;
+            hin.n_near = n_near;
         } else if (split && c >= 1) {
             // far part (segments 0 .. c-2) on sG beside the recurrence of block
             // c-1; the newest segment c-1 on sR once it is sliced; the combine
@@ -474,7 +490,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             }));
             FABM_CUDA_TRY(cudaEventRecord(s->evG[c % 3], s->sG));
             FABM_CUDA_TRY(cudaStreamWaitEvent(s->sR, s->evG[c % 3], 0));
-            Gc = Gbuf;
+            hin.G = Gbuf;
         } else if (!split && (c - lag) * L > 0) {
             const int64_t k_end = (c - lag) * L;
             double *Gbuf = s->G.p + (size_t)(c % n_gbuf) * 2 * L * cols;
@@ -529,8 +545,8 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
         }
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_RECURRENCE, s->sR, rflops, [&] {
             if (split)
-                return launch_recur_cols(s->rhs, bt, s->wBff.p, s->wAff.p, s->wDff.p, s->k, c,
-                                         static_cast<const float2 *>(Gc), X, s->cols_warps, s->sR);
+                return launch_recur_cols(s->rhs, bt, s->wBff.p, s->wAff.p, s->wDff.p, s->k, c, hin,
+                                         X, s->cols_warps, s->sR);
             return launch_recur(s->rhs, bt, w, s->k, c, L, lag, s->precision == FABM_SPLIT,
                                 static_cast<const double *>(Gc), s->sR);
         }));
@@ -660,6 +676,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             FABM_CUDA_TRY(s->Fs2.ensure((size_t)n_grp * n_ct * far_group_slice_elems()));
             FABM_CUDA_TRY(s->Fe2.ensure((size_t)n_grp * n_ct * 128));
             FABM_CUDA_TRY(s->fpart.ensure(2 * far_part_elems(far_chunks, (int)cols)));
+            FABM_CUDA_TRY(s->fsum.ensure(2 * far_part_elems(1, (int)cols)));
         }
         if (rhs_has_forcing(s->rhs, dim))
             FABM_CUDA_TRY(s->auxb.ensure((size_t)kAuxRing * kSplitSeg * B));
@@ -676,7 +693,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     // least 8 MB), instead of once at the end
     s->out_stream = nullptr;
     const size_t out_bytes = sizeof(double) * (size_t)B * (N + 1) * dim;
-    if (!out_on_device && all_full && out_bytes >= (64u << 20)) {
+    if (!out_on_device && all_full && out_bytes >= (64u << 20) && hk != FABM_HIST_FP64_PERSIST) {
         cudaPointerAttributes pa{};
         if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost) {
             s->out_stream = out;
@@ -731,11 +748,38 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
         (uintptr_t)s->out_stream, (uintptr_t)s->out_group, (uintptr_t)s->wait_cycles,
         (uintptr_t)s->wide, (uintptr_t)far_chunks, (uintptr_t)s->Fs2.p, (uintptr_t)s->Fe2.p,
-        (uintptr_t)s->fpart.p};
+        (uintptr_t)s->fpart.p, (uintptr_t)s->fsum.p};
     auto enqueue = [&]() -> fabm_status {
         return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk, far_chunks);
     };
-    if (!s->use_graphs) {
+    if (hk == FABM_HIST_FP64_PERSIST) {
+        // one cooperative launch runs every block (after the initial values);
+        // its flags start at zero
+        const int grid = s->persist_ctas;
+        const int pchunks = grid - (int)B;
+        const int ncg = (int)((cols + 3) / 4);
+        FABM_CUDA_TRY(s->ppart.ensure(persist_part_elems(pchunks, (int)cols)));
+        FABM_CUDA_TRY(s->pdone.ensure((size_t)nblk * ncg));
+        FABM_CUDA_TRY(s->prdone.ensure((size_t)B));
+        FABM_CUDA_TRY(s->err.ensure(1));
+        s->recs.clear();
+        FABM_CUDA_TRY(cudaMemsetAsync(s->pdone.p, 0, sizeof(int) * nblk * ncg, s->sR));
+        FABM_CUDA_TRY(cudaMemsetAsync(s->prdone.p, 0, sizeof(int) * B, s->sR));
+        FABM_CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(unsigned int), s->sR));
+        s->sample_now = true;
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
+                                   [&] { return launch_init(s->rhs, bt, s->sR); }));
+        const double flops = 2.0 * (double)Nmax * (double)Nmax * (double)cols;
+        FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, flops, [&] {
+            return launch_persist_fp64(s->rhs, bt, w, s->k, nblk, grid, pchunks, s->ppart.p,
+                                       s->pdone.p, s->prdone.p, s->err.p, s->wait_cycles, s->sR);
+        }));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
+        FABM_CUDA_TRY(collect_timing(s, s->recs));
+        unsigned int tout = 0;
+        FABM_CUDA_TRY(cudaMemcpy(&tout, s->err.p, sizeof tout, cudaMemcpyDeviceToHost));
+        if (tout) return fail(FABM_ETIMEOUT, "the persistent solve gave up waiting on a flag");
+    } else if (!s->use_graphs) {
         s->recs.clear();
         // the side streams start after this solve's inputs are on the device
         FABM_CUDA_TRY(cudaEventRecord(s->evFork, s->sR));
@@ -925,25 +969,24 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoinC, cudaEventDisableTiming);
     if (e == cudaSuccess && precision == FABM_FP64X2) {
-        // double-double weights from binary128 on the host: high parts into
+        // double-double weights on the device (weights_dd.cu): high parts into
         // wB, wA, wD, low parts into wBl, wAl, wDl
         e = s->wBl.ensure(wlen);
         if (e == cudaSuccess) e = s->wAl.ensure(wlen);
         if (e == cudaSuccess) e = s->wDl.ensure(wlen);
-        std::vector<double> hb(wlen), lb(wlen), ha(wlen), la(wlen), hd(wlen), ld(wlen);
+        s->timing = true;  // the weight launch is always timed
+        s->recs.clear();
         for (int q = 0; q < n_sets && e == cudaSuccess; ++q) {
             const size_t o = (size_t)q * (s->w_ext + 1);
-            if (fabm_weights_x2(alpha_c[q], s->w_ext, &hb[o], &lb[o], &ha[o], &la[o], &hd[o], &ld[o]) !=
-                FABM_OK)
-                e = cudaErrorInvalidValue;
+            double g[4];
+            fabm_x2_inv_gammas(alpha_c[q], g);
+            e = timed_launch(s, FABM_KERNEL_WEIGHTS, s->sR, 0.0, [&] {
+                return launch_weights_x2(alpha_c[q], s->w_ext, g[0], g[1], g[2], g[3], s->wB.p + o,
+                                         s->wBl.p + o, s->wA.p + o, s->wAl.p + o, s->wD.p + o,
+                                         s->wDl.p + o, s->sR);
+            });
         }
-        const size_t nb = sizeof(double) * wlen;
-        if (e == cudaSuccess) e = cudaMemcpy(s->wB.p, hb.data(), nb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->wBl.p, lb.data(), nb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->wA.p, ha.data(), nb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->wAl.p, la.data(), nb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->wD.p, hd.data(), nb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->wDl.p, ld.data(), nb, cudaMemcpyHostToDevice);
+        s->timing = false;
     } else if (e == cudaSuccess) {
         s->timing = true;  // the weight launch is always timed
         s->recs.clear();
@@ -991,6 +1034,12 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
             if (e == cudaSuccess) e = launch_ff_weights(s->wA.p, ha, kSplitSeg + 1, s->wAff.p, s->sR);
             if (e == cudaSuccess) e = launch_ff_weights(s->wD.p, ha, s->w_ext + 1, s->wDff.p, s->sR);
         }
+    }
+    if (e == cudaSuccess && precision == FABM_FP64 && !multi) {
+        int coop = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop)
+            s->persist_ctas = std::min(persist_max_ctas(rhs_id, dim), 152);
+        cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->sR);
     if (e == cudaSuccess) e = collect_timing(s, s->recs);
@@ -1093,7 +1142,8 @@ fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
     g_last_error.clear();
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     const bool ok = kernel == FABM_HIST_AUTO ||
-                    (s->precision == FABM_FP64 && kernel == FABM_HIST_FP64) ||
+                    (s->precision == FABM_FP64 &&
+                     (kernel == FABM_HIST_FP64 || kernel == FABM_HIST_FP64_PERSIST)) ||
                     (s->precision == FABM_FP64X2 && kernel == FABM_HIST_X2) ||
                     (s->precision == FABM_SPLIT &&
                      (kernel == FABM_HIST_TENSOR || kernel == FABM_HIST_TENSOR_WIDE ||
@@ -1141,6 +1191,21 @@ fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, d
     return FABM_OK;
 }
 
+fabm_status fabm_copy_weights_lo(fabm_solver *s, int64_t n, double *Bl, double *Al, double *Dl)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (s->precision != FABM_FP64X2) return fail(FABM_EINVAL, "low weight parts exist for FP64X2 only");
+    if (n < 0 || n > s->N + 1) return fail(FABM_EINVAL, "n %lld outside 0..N+1", (long long)n);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    DeviceGuard g(s->device);
+    if (Bl) FABM_CUDA_TRY(cudaMemcpy(Bl, s->wBl.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (Al) FABM_CUDA_TRY(cudaMemcpy(Al, s->wAl.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (Dl) FABM_CUDA_TRY(cudaMemcpy(Dl, s->wDl.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return FABM_OK;
+}
+
 int64_t fabm_last_launch_count(const fabm_solver *s) { return s ? s->launches : 0; }
 
 fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,
@@ -1162,6 +1227,8 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     if (s->precision == FABM_FP64 || s->precision == FABM_FP64X2) {
         const int k = s->precision == FABM_FP64 ? FABM_HIST_FP64 : FABM_HIST_X2;
         for (int c : ctas_opts) cands.push_back({k, c});
+        if (s->precision == FABM_FP64 && s->persist_ctas >= B + 8 && !s->multi)
+            cands.push_back({FABM_HIST_FP64_PERSIST, s->persist_ctas});
     } else {
         // tensor kernels (far history of pairs of blocks with 128 targets per
         // MMA, or of single blocks with 64): "ctas" carries the SM reserve
@@ -1190,6 +1257,8 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         s->hist_kernel = cd.kernel;
         if (cd.kernel == FABM_HIST_TENSOR || cd.kernel == FABM_HIST_TENSOR_WIDE)
             s->sm_reserve = cd.ctas, s->chunk_ctas = keep_ctas;
+        else if (cd.kernel == FABM_HIST_FP64_PERSIST)
+            s->chunk_ctas = keep_ctas, s->sm_reserve = keep_res;
         else
             s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
         double ms = 1e300;
@@ -1216,8 +1285,8 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     }
     s->hist_kernel = pick.kernel;
     const bool tensor = pick.kernel == FABM_HIST_TENSOR || pick.kernel == FABM_HIST_TENSOR_WIDE;
-    if (tensor)
-        s->sm_reserve = pick.ctas, s->chunk_ctas = keep_ctas;
+    if (tensor || pick.kernel == FABM_HIST_FP64_PERSIST)
+        s->sm_reserve = tensor ? pick.ctas : keep_res, s->chunk_ctas = keep_ctas;
     else
         s->chunk_ctas = pick.ctas, s->sm_reserve = keep_res;
     s->L = tensor ? kSplitSeg : kRecurL;

@@ -25,6 +25,9 @@
 
 #include "../../include/fabm.h"
 
+// 1/Gamma(a+1), 1/Gamma(a+2) in binary128 as (hi, lo) pairs (weights_x2.c).
+extern "C" void fabm_x2_inv_gammas(double alpha, double out[4]);
+
 namespace fabm {
 
 constexpr int kWarp = 32;
@@ -133,7 +136,8 @@ cudaError_t launch_hist_split(const __nv_bfloat16 *Fs, const int *Ef, const __nv
                               long long wait_cycles, cudaStream_t st);
 
 // G[kind][t][col] = sum of the float-float partials over chunks, for blocks
-// of L targets: rounded to double, or (_ff) kept as float-float pairs.
+// of L targets: accumulated in double with compensation and rounded once, or
+// (_ff, tensor path) accumulated in compensated float-float and kept as pairs.
 cudaError_t launch_combine_split(const float2 *part, int n_chunks, int cols, int L, double *G,
                                  cudaStream_t st);
 cudaError_t launch_combine_split_ff(const float2 *part, int n_chunks, int cols, int L,
@@ -170,22 +174,28 @@ cudaError_t launch_hist_far(const __nv_bfloat16 *Fs, const int *Ef, const __nv_b
                             const int *Ew, int64_t C, int n_grp, int n_chunks, int n_ct, int cols,
                             float2 *part, unsigned int *err, long long wait_cycles,
                             cudaStream_t st);
-// G[kind][t][col] (64 targets) = far[.][kind][off + t][col] over n_far chunks
-// (off 0 or 64) + near[.][kind][t][col] over n_near chunks, float-float.
-cudaError_t launch_combine_far(const float2 *far, int n_far, int off, const float2 *nearp,
-                               int n_near, int cols, float2 *G, cudaStream_t st);
+// out[kind][t][col] (128 targets) = far[.][kind][t][col] over n_far chunks,
+// float-float, fixed order.
+cudaError_t launch_sum_far(const float2 *far, int n_far, int cols, float2 *out, cudaStream_t st);
 
 // a4 + a5 on the tensor-history path, one lane per column (recurrence_cols.cu):
-// the 64 steps of block c given G, the history of every point k < 64c as
-// float-float pairs [2][64][cols] (NULL for c = 0).  WB, WA: h^a B(d), h^a A(d)
+// the 64 steps of block c given the history of every point k < 64c as
+// float-float pairs: G[kind][g_off + t][col] (rows of g_rows per kind; NULL:
+// none) plus near[ch][kind][t][col] (64 rows per kind) over n_near chunks.  WB, WA: h^a B(d), h^a A(d)
 // for d = 0..64; WD: h^a D(m), m = 0..N; all float-float pairs, one order.
 // warps_per_cta (1..12) warps of 32/dim trajectories per CTA, or 0: one lane
 // per target, a CTA of dim warps per trajectory (narrow batches).  X: the table
 // of the time-only part of f for block c (launch_aux_table), required when
 // rhs_has_forcing(rhs), else ignored.  y's slots receive float-float
 // increments; launch_finish_y turns them into y after the last block.
+struct HistIn {
+    const float2 *G = nullptr;     // [2][g_rows][cols], or NULL
+    int g_rows = 64, g_off = 0;
+    const float2 *near = nullptr;  // [n_near][2][64][cols]
+    int n_near = 0;
+};
 cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, const float2 *WA,
-                              const float2 *WD, const StepConsts &k, int64_t c, const float2 *G,
+                              const float2 *WD, const StepConsts &k, int64_t c, const HistIn &hin,
                               const float2 *X, int warps_per_cta, cudaStream_t st);
 // The right-hand side has a time-dependent part (forcing).
 bool rhs_has_forcing(int rhs, int dim);
@@ -202,6 +212,22 @@ cudaError_t prepare_recur_cols(int rhs, int dim);
 // Warps the column recurrence needs for B trajectories of dimension dim.
 int recur_cols_warps(int dim, int64_t B);
 
+// ---- FP64, persistent (persist_fp64.cu) ----
+
+// CTAs of the persistent FP64 kernel that can be resident at once on the
+// current device (0: cooperative launch unavailable).
+int persist_max_ctas(int rhs, int dim);
+// doubles of the persistent kernel's partial-sum slots.
+size_t persist_part_elems(int max_chunks, int cols);
+// The whole FP64 solve of a batch (after launch_init) as one cooperative
+// launch of `grid` CTAs: bt.B recurrence CTAs and grid - bt.B history CTAs
+// (chunks per block at most max_chunks = grid - bt.B).  done: nblk x
+// ceil(cols/4) ints, r_done: B ints, both zero; err: set on a wait timeout.
+cudaError_t launch_persist_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
+                                const StepConsts &k, int64_t nblk, int grid, int max_chunks,
+                                double *part, int *done, int *r_done, unsigned *err,
+                                long long wait_cycles, cudaStream_t st);
+
 // ---- FP64X2 precision (double-double history) ----
 
 // Low parts of the double-double weights; the high parts are the DevWeights
@@ -211,6 +237,12 @@ struct DevWeightsLo {
     const double *A;
     const double *D;
 };
+
+// a1 in double-double on the device: B, A, D for d = 0..n as (hi, lo) pairs,
+// given 1/Gamma(a+1) and 1/Gamma(a+2) as pairs (weights_dd.cu).
+cudaError_t launch_weights_x2(double alpha, int64_t n, double ig1_hi, double ig1_lo,
+                              double ig2_hi, double ig2_lo, double *Bh, double *Bl, double *Ah,
+                              double *Al, double *Dh, double *Dl, cudaStream_t st);
 
 // a2 in double-double: partial far-history sums of target block c (32 targets)
 // over k < (c-lag)*32 as (hi, lo) pairs, n_chunks x 2 x 32 x cols.

@@ -17,8 +17,10 @@ constexpr int kTile = 256;      // points staged in shared memory at a time
 // [chunk*kc, min((chunk+1)*kc, k_end))) of the far history of block c for the
 // columns col0 .. col0+3.
 // MULTI: one order per component, column col's weights at WB + (col % dim)
-// * wstride (WA likewise), one staged window per warp.
-template <bool MULTI = false>
+// * wstride (WA likewise), one staged window per warp.  CG: read F around L1
+// (ld.global.cg), for callers whose F rows are written by other CTAs of the
+// same launch while it runs.
+template <bool MULTI = false, bool CG = false>
 __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF, int cols,
                                        const double *__restrict__ WB,
                                        const double *__restrict__ WA, int64_t c, int64_t kc,
@@ -57,7 +59,8 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
         }
         for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;
-            sF[i] = j < ncol ? F[(t0 + k) * ldF + col0 + j] : 0.0;
+            const double *src = F + (t0 + k) * ldF + col0 + j;
+            sF[i] = j < ncol ? (CG ? __ldcg(src) : *src) : 0.0;
         }
         __syncthreads();
         if (w < ncol) {

@@ -492,43 +492,21 @@ __device__ __forceinline__ void ff_acc(float &hi, float &lo, float x, float y)
     lo = lo - (hi - s);
 }
 
-// a3 for one block of 64 targets: G[kind][t][col] = sum over the far chunks of
-// far[ch][kind][off + t][col] (128-target rows), then over the near chunks of
-// near[ch][kind][t][col] (64-target rows), in float-float, chunk order fixed:
-// lane r of a group of R sums the far chunks r, r+R, .. and the near chunks
-// likewise, then a fixed xor tree.
-template <int R>
-__global__ void combine_far_kernel(const float2 *__restrict__ far, int n_far, int off,
-                                   const float2 *__restrict__ nearp, int n_near, int cols,
-                                   float2 *__restrict__ G)
+// Sum of the far chunks of one target group: out[kind][t][col] (128 targets)
+// = far[.][kind][t][col] over n_far chunks in float-float, chunk order fixed.
+// Runs after the far kernel on its stream, so that the recurrence of each of
+// the pair's blocks reads one far value per target plus its near partials.
+__global__ void sum_far_kernel(const float2 *__restrict__ far, int n_far, int64_t n_out,
+                               float2 *__restrict__ out)
 {
-    const int64_t n_out = 2LL * 64 * cols;
-    const int64_t far_stride = 2LL * kGrp * cols, near_stride = n_out;
-    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int r = (int)(gtid % R);
-    const int64_t groups = (int64_t)gridDim.x * blockDim.x / R;
-    for (int64_t base = 0; base < n_out; base += groups) {
-        const int64_t o = base + gtid / R;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out;
+         o += (int64_t)gridDim.x * blockDim.x) {
         float hi = 0.f, lo = 0.f;
-        if (o < n_out) {
-            const int64_t kind = o / (64LL * cols), rest = o % (64LL * cols);
-            const int64_t fo = (kind * kGrp + off) * cols + rest;
-            for (int c = r; c < n_far; c += R) {
-                const float2 v = far[(int64_t)c * far_stride + fo];
-                ff_acc(hi, lo, v.x, v.y);
-            }
-            for (int c = r; c < n_near; c += R) {
-                const float2 v = nearp[(int64_t)c * near_stride + o];
-                ff_acc(hi, lo, v.x, v.y);
-            }
+        for (int ch = 0; ch < n_far; ++ch) {
+            const float2 v = far[(int64_t)ch * n_out + o];
+            ff_acc(hi, lo, v.x, v.y);
         }
-#pragma unroll
-        for (int s = R / 2; s > 0; s >>= 1) {
-            const float ohi = __shfl_xor_sync(0xffffffffu, hi, s);
-            const float olo = __shfl_xor_sync(0xffffffffu, lo, s);
-            ff_acc(hi, lo, ohi, olo);
-        }
-        if (r == 0 && o < n_out) G[o] = make_float2(hi, lo);
+        out[o] = make_float2(hi, lo);
     }
 }
 
@@ -583,21 +561,12 @@ cudaError_t launch_hist_far(const __nv_bfloat16 *Fs, const int *Ef, const __nv_b
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine_far(const float2 *far, int n_far, int off, const float2 *nearp,
-                               int n_near, int cols, float2 *G, cudaStream_t st)
+cudaError_t launch_sum_far(const float2 *far, int n_far, int cols, float2 *out, cudaStream_t st)
 {
-    if (off != 0 && off != 64) return cudaErrorInvalidValue;
-    const int64_t n_out = 2LL * 64 * cols;
-    const int threads = 128;
-    const int n = n_far > n_near ? n_far : n_near;
-    auto blocks_for = [&](int R) {
-        int64_t b = (n_out * R + threads - 1) / threads;
-        return (unsigned)(b > 152 * 16 ? 152 * 16 : b);
-    };
-    if (n >= 64)
-        combine_far_kernel<8><<<blocks_for(8), threads, 0, st>>>(far, n_far, off, nearp, n_near, cols, G);
-    else
-        combine_far_kernel<1><<<blocks_for(1), threads, 0, st>>>(far, n_far, off, nearp, n_near, cols, G);
+    const int64_t n_out = 2LL * kGrp * cols;
+    int64_t blocks = (n_out + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    sum_far_kernel<<<(unsigned)blocks, 256, 0, st>>>(far, n_far, n_out, out);
     return cudaGetLastError();
 }
 

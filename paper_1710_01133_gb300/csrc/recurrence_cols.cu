@@ -52,6 +52,16 @@ __device__ __forceinline__ FF ld_ff(const float2 *p)
     return FF(v.x, v.y);
 }
 
+// History of every point before block c for target a of column col, kind k
+// (0 predictor, 1 corrector): the far value plus the near partials.
+__device__ __forceinline__ FF hist_in(const HistIn &h, int k, int a, int64_t col, int cols)
+{
+    FF v = h.G ? ld_ff(h.G + ((int64_t)k * h.g_rows + h.g_off + a) * cols + col) : FF(0);
+    for (int ch = 0; ch < h.n_near; ++ch)
+        v = v + ld_ff(h.near + (((int64_t)ch * 2 + k) * kColL + a) * cols + col);
+    return v;
+}
+
 // Time-only part of f for the 64 targets of block c: X[a][b] = aux(t_m, p_b),
 // m = 64c+1+a, as float-float pairs.
 template <class Rhs>
@@ -95,8 +105,8 @@ __global__ void finish_y_kernel(DevBatch bt, double h, int64_t m_lo, int64_t m_h
 // CTA size is chosen by the host so that the CTAs fill the SMs the tensor
 // history leaves free (a tensor CTA and a recurrence CTA never share an SM).
 // WB, WA: h^a B(d), h^a A(d) for d = 0..64 as float-float pairs; WD: h^a D(m);
-// F: float-float pairs in the double-sized slots of bt.F; G: combined history
-// of block c, [2][64][cols] float-float pairs, or NULL for block 0; X: the
+// F: float-float pairs in the double-sized slots of bt.F; hin: the history of
+// block c (a far value and near partials, float-float pairs); X: the
 // forcing table of block c ([64][B] pairs, aux_kernel) when Rhs::kForcing.
 // Y1: bt.y1 is set (1 < alpha < 2, Taylor part y0 + t y'(0)); a template
 // parameter so that the solves without it carry no FP64 work per step.
@@ -104,7 +114,7 @@ template <class Rhs, int D, bool Y1>
 __global__ void __launch_bounds__(kMaxWarps *kWarp)
     recur_cols_kernel(DevBatch bt, const float2 *__restrict__ WB, const float2 *__restrict__ WA,
                       const float2 *__restrict__ WD, StepConsts kc, int64_t c,
-                      const float2 *__restrict__ G, const float2 *__restrict__ X)
+                      const HistIn hin, const float2 *__restrict__ X)
 {
     constexpr int TPW = kWarp / D;  // trajectories per warp
     extern __shared__ __align__(16) FF smem_ff[];
@@ -156,8 +166,8 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
 #pragma unroll
         for (int r = 0; r < kSub; ++r) {
             const int a = a0 + r;
-            const FF gP = G ? ld_ff(G + (int64_t)a * cols + col) : FF(0);
-            const FF gC = G ? ld_ff(G + (int64_t)(kColL + a) * cols + col) : FF(0);
+            const FF gP = hist_in(hin, 0, a, col, cols);
+            const FF gC = hist_in(hin, 1, a, col, cols);
             bP[r] = ha * gP;
             bC[r] = ff_fma(ld_ff(WD + (m0 + 1 + a)), f0, ha * gC);
             accP[r] = accC[r] = FF(0);
@@ -226,7 +236,7 @@ template <class Rhs, int D>
 __global__ void __launch_bounds__(D *kWarp)
     recur_targets_kernel(DevBatch bt, const float2 *__restrict__ WB, const float2 *__restrict__ WA,
                          const float2 *__restrict__ WD, StepConsts kc, int64_t c,
-                         const float2 *__restrict__ G, const float2 *__restrict__ X)
+                         const HistIn hin, const float2 *__restrict__ X)
 {
     constexpr int TPL = kColL / kWarp;
     __shared__ FF sB[kColL + 1], sA[kColL + 1];
@@ -260,8 +270,8 @@ __global__ void __launch_bounds__(D *kWarp)
         const int a = lane + kWarp * t;
         const int64_t m = m0 + 1 + a;
         T[t] = bt.y1 ? ff_from_double(fma((double)m * kc.h, y1, y0)) : ff_from_double(y0);
-        const FF gP = G ? ld_ff(G + (int64_t)a * bt.cols + col) : FF(0);
-        const FF gC = G ? ld_ff(G + (int64_t)(kColL + a) * bt.cols + col) : FF(0);
+        const FF gP = hist_in(hin, 0, a, col, bt.cols);
+        const FF gC = hist_in(hin, 1, a, col, bt.cols);
         bP[t] = ha * gP;
         bC[t] = ff_fma(ld_ff(WD + m), f0, ha * gC);
         ax[t] = Rhs::kForcing ? ld_ff(X + (int64_t)a * bt.B + b) : aux0;
@@ -359,7 +369,7 @@ cudaError_t prepare_recur_cols(int rhs, int dim)
 int recur_cols_warps(int dim, int64_t B) { return (int)((B + kWarp / dim - 1) / (kWarp / dim)); }
 
 cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, const float2 *WA,
-                              const float2 *WD, const StepConsts &k, int64_t c, const float2 *G,
+                              const float2 *WD, const StepConsts &k, int64_t c, const HistIn &hin,
                               const float2 *X, int warps_per_cta, cudaStream_t st)
 {
     if (warps_per_cta < 0 || warps_per_cta > kMaxWarps) return cudaErrorInvalidValue;
@@ -369,7 +379,7 @@ cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, con
         if (need_x && !X) return;
         if (warps_per_cta == 0) {  // one lane per target
             recur_targets_kernel<R, D><<<(unsigned)bt.B, D * kWarp, 0, st>>>(bt, WB, WA, WD, k, c,
-                                                                             G, X);
+                                                                             hin, X);
             return;
         }
         const int warps = recur_cols_warps(D, bt.B);
@@ -377,10 +387,10 @@ cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, con
         const size_t smem = cols_smem_bytes(D, warps_per_cta);
         if (bt.y1)
             recur_cols_kernel<R, D, true><<<blocks, warps_per_cta * kWarp, smem, st>>>(
-                bt, WB, WA, WD, k, c, G, X);
+                bt, WB, WA, WD, k, c, hin, X);
         else
             recur_cols_kernel<R, D, false><<<blocks, warps_per_cta * kWarp, smem, st>>>(
-                bt, WB, WA, WD, k, c, G, X);
+                bt, WB, WA, WD, k, c, hin, X);
     });
     return ok && !(need_x && !X) ? cudaGetLastError() : cudaErrorInvalidValue;
 }

@@ -79,6 +79,16 @@ static void *run(void *p)
     return 0;
 }
 
+/* 1/Gamma(a+1) and 1/Gamma(a+2) in binary128, as (hi, lo) pairs: out[0..1]
+ * and out[2..3].  Internal: the device computes the FP64x2 weights (weights_dd.cu) and takes
+ * these two constants from here. */
+__attribute__((visibility("hidden"))) void fabm_x2_inv_gammas(double alpha, double out[4])
+{
+    const q_t a = (q_t)alpha;
+    split(1 / tgammaf128(a + 1), &out[0], &out[1]);
+    split(1 / tgammaf128(a + 2), &out[2], &out[3]);
+}
+
 fabm_status fabm_weights_x2(double alpha, int64_t n, double *Bh, double *Bl, double *Ah, double *Al,
                             double *Dh, double *Dl)
 {

@@ -87,3 +87,20 @@ def test_injected_allocation_failure_in_a_server_admission(gpu_lib, parity):
         got = srv.wait(ok)
     parity(rel_err(got, oracle.solve("linear", 0.8, 1e-3, 500, [1.0], params=[1.0])), 1e-12,
            "after-enomem")
+
+
+def test_persistent_fp64_wait_timeout_is_reported_and_the_solver_recovers(gpu_lib, parity):
+    """The persistent FP64 launch's flag waits: with a 16-cycle limit the first
+    wait gives up, every CTA leaves its loop, the solve reports FABM_ETIMEOUT;
+    with the default limit the next solve is correct."""
+    from fabm_workloads import lorenz_single
+    w = lorenz_single(N=3000)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, history="fp64-persist") as s:
+        s.set_wait_limit(16)
+        with pytest.raises(gpu_lib.FabmError) as e:
+            s.solve(w.y0[0])
+        assert e.value.status == gpu_lib.FABM_ETIMEOUT
+        s.set_wait_limit(0)
+        got = s.solve(w.y0[0])
+    ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    parity(rel_err(got, ref), 1e-12, "after-timeout")

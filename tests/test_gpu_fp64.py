@@ -199,3 +199,41 @@ def test_graph_replay_matches_direct_launches(gpu_lib):
         g2 = s.solve_batch(y0b[::-1].copy(), N_each=[999, 1500])
     assert np.array_equal(direct[0], g1[0]) and np.array_equal(direct[1, :1000], g1[1, :1000])
     assert np.array_equal(g2[0, :1000], direct[1, :1000]) and np.array_equal(g2[1], direct[0])
+
+
+@pytest.mark.parametrize("B", [1, 3, 16])
+def test_persistent_solve_matches_the_oracle_and_the_graph_schedule(gpu_lib, parity, B):
+    """The FP64 solve as one persistent cooperative launch (recurrence CTAs and
+    history CTAs handing blocks over through device flags) against the oracle
+    at 1e-12, and against the schedule of one launch per kernel and block;
+    uneven lengths, including one inside the first far block and one on a
+    block edge."""
+    w = lorenz_single(N=6000)
+    y0 = w.y0 + np.linspace(-0.05, 0.05, B)[:, None]
+    ne = np.full(B, w.N, dtype=np.int64)
+    if B > 1:
+        ne[1] = 77
+    if B > 2:
+        ne[-1] = 4096
+    ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, y0, params=w.params, N_each=ne,
+                             threads=min(B, 16))
+    out = {}
+    for hist in ("fp64-persist", "fp64"):
+        with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, history=hist) as s:
+            out[hist] = s.solve_batch(y0, N_each=ne)
+            if hist == "fp64-persist":
+                assert s.last_launch_count <= 3  # initial values + the persistent launch
+    for b in range(B):
+        n = ne[b]
+        for hist, got in out.items():
+            parity(rel_err(got[b, : n + 1], ref[b, : n + 1]), TOL_FP64, f"{hist}-{b}")
+
+
+def test_persistent_solve_scalar_and_manufactured(gpu_lib, parity):
+    """One component (no exchange between warps): the Mittag-Leffler workload
+    through the persistent launch."""
+    w = ml_scalar()
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, history="fp64-persist") as s:
+        got = s.solve(w.y0[0])
+    ref = oracle.solve(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
+    parity(rel_err(got, ref), TOL_FP64, "ml")

@@ -108,3 +108,24 @@ def test_x2_against_the_binary128_oracle(gpu_lib, parity, case):
         got = s.solve(w.y0[0])
     ref = oracle.solve_q(w.rhs, w.alpha, w.h, w.N, w.y0[0], params=w.params)
     parity(rel_err(got, ref), TOL, case)
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.95, 1.5])
+def test_device_double_double_weights_match_binary128(gpu_lib, alpha):
+    """The FP64X2 solver computes its weights on the device in double-double
+    (printed differences up to d = 64, non-cancelling series beyond); they agree
+    with the host's binary128 evaluation of the same weights (pinned against
+    50-digit values on the CPU) to 1e-27 relative, and their high parts are the
+    doubles nearest to them."""
+    N = 70_000
+    with gpu_lib.Solver("linear", 1, alpha, 1e-3, N, [1.0], precision="fp64x2") as s:
+        Bh, Ah, Dh = s.weights(N + 1)
+        Bl, Al, Dl = gpu_lib.fabm_copy_weights_lo(s.handle, N + 1)
+    hb, lb, ha, la, hd, ld = gpu_lib.fabm_weights_x2(alpha, N)
+    for name, dh, dl, rh, rl in (("B", Bh, Bl, hb, lb), ("A", Ah, Al, ha, la),
+                                 ("D", Dh, Dl, hd, ld)):
+        diff = (dh[1:] - rh[1:]) + (dl[1:] - rl[1:])
+        rel = np.abs(diff) / np.abs(rh[1:])
+        assert float(rel.max()) < 1e-27, (name, int(rel.argmax()) + 1, float(rel.max()))
+        assert np.all(np.abs(dl[1:]) <= 0.5 * np.spacing(np.abs(dh[1:]))), name
+        assert dh[0] == 0.0 and dl[0] == 0.0
