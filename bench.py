@@ -499,7 +499,7 @@ def main():
     ap.add_argument("--recurrence", default="auto", choices=["auto", "columns", "targets"],
                     help="split precision, tensor history: layout of the recurrence")
     ap.add_argument("--history", default="auto",
-                    choices=["auto", "tensor", "tensor-wide", "fp32c", "fp64", "x2"],
+                    choices=["auto", "tensor", "tensor-wide", "fp32c", "fp64", "fp64-persist", "x2"],
                     help="history kernel (auto: the library's choice)")
     ap.add_argument("--no-fp64-comparator", action="store_true",
                     help="skip timing the plain FP64 single-trajectory solve (vs_fp64_path)")

@@ -174,8 +174,9 @@ enum {
                               recurrence with weights and the recent window of f in
                               shared memory, the other CTAs sum the far history
                               (as FABM_HIST_FP64) and hand it over through device
-                              flags; automatic choice for FP64 batches of at most 16
-                              single-order trajectories                              */
+                              flags; single-order batches of at most 64 trajectories
+                              (others run FABM_HIST_FP64); timed by fabm_autotune,
+                              not chosen automatically                               */
 };
 
 /* Choose the history kernel (one of FABM_HIST_*; must fit the precision).

@@ -122,6 +122,7 @@ struct fabm_solver {
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     long long wait_cycles = 0;         // tensor kernel's wait limit (0: its default)
     bool wide = false;                 // the solve being set up uses the 128-target far history
+    int near_chunks = 1;               // wide path: CTAs per column tile of a near launch
     int persist_ctas = 0;              // FP64: CTAs of the persistent kernel resident at once
     int L = kRecurL;                   // block length of the last solve
     int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
@@ -162,15 +163,19 @@ struct fabm_solver {
     // sR: recurrence; sG, sG2: far history (the CUDA-core history of odd blocks
     // runs on sG2, so that consecutive blocks' history launches overlap)
     // sC: device-to-host copies of finished rows while the solve goes on
-    // sG3: far history of odd target groups (wide tensor path)
-    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr, sC = nullptr, sG3 = nullptr;
+    // sG3: far history of odd target groups (wide tensor path); sS: the sums of
+    // their chunks, at the recurrence's priority so that they are not queued
+    // behind the next far launch's CTAs
+    cudaStream_t sR = nullptr, sG = nullptr, sG2 = nullptr, sC = nullptr, sG3 = nullptr, sS = nullptr;
     double *out_stream = nullptr;  // pinned host output of the solve being enqueued, or NULL
     int64_t out_group = 1;         // blocks per streamed copy
     // evN: the newest-segment history launch of the tensor path (on sR); evA:
     // the forcing tables (tensor path, on sG2)
     cudaEvent_t evR[kEvRing] = {}, evG[3] = {}, evN[3] = {}, evA[kAuxRing] = {};
-    cudaEvent_t evF[2] = {};  // wide far history of target group C, slot C % 2
-    cudaEvent_t evFork = nullptr, evJoin = nullptr, evJoinC = nullptr, evJoin3 = nullptr;
+    cudaEvent_t evF[2] = {};  // wide far history of target group C summed, slot C % 2
+    cudaEvent_t evFK[2] = {}; // wide far kernel of target group C done, slot C % 2
+    cudaEvent_t evFork = nullptr, evJoin = nullptr, evJoinC = nullptr, evJoin3 = nullptr,
+                evJoinS = nullptr;
     std::mutex busy;
     int64_t launches = 0;
     // per-launch timing (fabm_set_timing)
@@ -215,6 +220,9 @@ struct fabm_solver {
             if (e) cudaEventDestroy(e);
         for (auto &e : evF)
             if (e) cudaEventDestroy(e);
+        for (auto &e : evFK)
+            if (e) cudaEventDestroy(e);
+        if (evJoinS) cudaEventDestroy(evJoinS);
         if (evJoin3) cudaEventDestroy(evJoin3);
         if (evFork) cudaEventDestroy(evFork);
         if (evJoin) cudaEventDestroy(evJoin);
@@ -226,6 +234,7 @@ struct fabm_solver {
         if (sG2) cudaStreamDestroy(sG2);
         if (sC) cudaStreamDestroy(sC);
         if (sG3) cudaStreamDestroy(sG3);
+        if (sS) cudaStreamDestroy(sS);
     }
 };
 
@@ -336,12 +345,11 @@ cudaError_t collect_timing(fabm_solver *s, const std::vector<fabm_solver::Rec> &
 int resolve_hist_kernel(const fabm_solver *s, int64_t cols)
 {
     if (s->precision == FABM_FP64) {
-        // one persistent launch per solve for narrow single-order batches: the
-        // recurrence CTAs take B SMs, the rest sum the history
+        // one persistent launch per solve on request (narrow single-order
+        // batches): the recurrence CTAs take B SMs, the rest sum the history
         const int64_t B = cols / s->dim;
         const bool fits = !s->multi && s->persist_ctas >= B + 8 && B <= 64;
         if (s->hist_kernel == FABM_HIST_FP64_PERSIST) return fits ? FABM_HIST_FP64_PERSIST : FABM_HIST_FP64;
-        if (s->hist_kernel == FABM_HIST_AUTO && fits && B <= 16) return FABM_HIST_FP64_PERSIST;
         return FABM_HIST_FP64;
     }
     if (s->precision == FABM_FP64X2) return FABM_HIST_X2;
@@ -441,17 +449,20 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                                            (int)(C - 1), n_far, n_ct, (int)cols, fw, s->err.p,
                                            s->wait_cycles, fs);
                 }));
-                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, fs, 0.0, [&] {
-                    return launch_sum_far(fw, n_far, (int)cols, fsw, fs);
+                FABM_CUDA_TRY(cudaEventRecord(s->evFK[C & 1], fs));
+                FABM_CUDA_TRY(cudaStreamWaitEvent(s->sS, s->evFK[C & 1], 0));
+                FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_COMBINE, s->sS, 0.0, [&] {
+                    return launch_sum_far(fw, n_far, (int)cols, fsw, s->sS);
                 }));
-                FABM_CUDA_TRY(cudaEventRecord(s->evF[C & 1], fs));
+                FABM_CUDA_TRY(cudaEventRecord(s->evF[C & 1], s->sS));
             }
             const int64_t lo = std::max<int64_t>(0, 2 * C - 2);
             const int n_near = (int)(c - lo);
             const double nflops = 4.0 * L * (double)(n_near * L) * (double)cols;
+            const int n_nc = std::min(n_near, s->near_chunks);
             FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, nflops, [&] {
                 return launch_hist_split(s->Fs.p, s->Fe.p, s->wH.p, s->wHe.p, c, (int)lo, n_near,
-                                         0, n_near, n_ct, (int)cols, s->spart.p, s->err.p,
+                                         0, n_nc, n_ct, (int)cols, s->spart.p, s->err.p,
                                          s->wait_cycles, s->sR);
             }));
             if (C >= 2) {
@@ -461,7 +472,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
                 hin.g_off = 64 * t;
             }
             hin.near = s->spart.p;
-            hin.n_near = n_near;
+            hin.n_near = n_nc;
         } else if (split && c >= 1) {
             // far part (segments 0 .. c-2) on sG beside the recurrence of block
             // c-1; the newest segment c-1 on sR once it is sliced; the combine
@@ -663,6 +674,11 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         s->wide = s->G_max >= 2 && (s->hist_kernel == FABM_HIST_TENSOR_WIDE ||
                                     s->hist_kernel == FABM_HIST_AUTO);
         far_chunks = std::max(1, (148 - reserve) / (2 * n_ct));
+        // a near launch (on the serial chain) takes whole SMs: as many CTAs per
+        // column tile as the SMs the far kernel leaves free allow, so that it
+        // does not wait for far CTAs to retire (one CTA sums its segments in turn)
+        const int far_free = 152 - 2 * n_ct * far_chunks;
+        s->near_chunks = std::clamp(far_free / n_ct, 1, 3);
         // column layout: CTAs sized to fill the SMs the tensor CTAs leave free
         const int free_sms = std::max(4, 152 - n_ct * split_chunks);
         s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 12) : 0;
@@ -748,7 +764,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
         (uintptr_t)s->out_stream, (uintptr_t)s->out_group, (uintptr_t)s->wait_cycles,
         (uintptr_t)s->wide, (uintptr_t)far_chunks, (uintptr_t)s->Fs2.p, (uintptr_t)s->Fe2.p,
-        (uintptr_t)s->fpart.p, (uintptr_t)s->fsum.p};
+        (uintptr_t)s->fpart.p, (uintptr_t)s->fsum.p, (uintptr_t)s->near_chunks};
     auto enqueue = [&]() -> fabm_status {
         return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk, far_chunks);
     };
@@ -756,7 +772,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         // one cooperative launch runs every block (after the initial values);
         // its flags start at zero
         const int grid = s->persist_ctas;
-        const int pchunks = grid - (int)B;
+        const int pchunks = persist_workers(grid, (int)B);
         const int ncg = (int)((cols + 3) / 4);
         FABM_CUDA_TRY(s->ppart.ensure(persist_part_elems(pchunks, (int)cols)));
         FABM_CUDA_TRY(s->pdone.ensure((size_t)nblk * ncg));
@@ -787,9 +803,11 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG2, s->evFork, 0));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sC, s->evFork, 0));
         FABM_CUDA_TRY(cudaStreamWaitEvent(s->sG3, s->evFork, 0));
+        FABM_CUDA_TRY(cudaStreamWaitEvent(s->sS, s->evFork, 0));
         fabm_status est = enqueue();
         if (est != FABM_OK) return est;
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG3));
+        FABM_CUDA_TRY(cudaStreamSynchronize(s->sS));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sG2));
@@ -808,6 +826,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG2, s->evFork, 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sC, s->evFork, 0);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sG3, s->evFork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sS, s->evFork, 0);
             fabm_status est = e == cudaSuccess ? enqueue() : FABM_ECUDA;
             if (est == FABM_OK) {
                 e = cudaEventRecord(s->evFork, s->sG);
@@ -818,6 +837,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoinC, 0);
                 if (e == cudaSuccess) e = cudaEventRecord(s->evJoin3, s->sG3);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoin3, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(s->evJoinS, s->sS);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->sR, s->evJoinS, 0);
             }
             cudaError_t e2 = cudaStreamEndCapture(s->sR, &graph);
             s->capturing = false;
@@ -954,8 +975,12 @@ fabm_status create_solver(int dim, const double *alpha_c, double h, int64_t N, i
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sC, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sG3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->sS, cudaStreamNonBlocking, prio_hi);
     for (auto &ev : s->evF)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (auto &ev : s->evFK)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoinS, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evJoin3, cudaEventDisableTiming);
     for (auto &ev : s->evR)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);

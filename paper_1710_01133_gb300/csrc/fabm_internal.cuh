@@ -217,11 +217,14 @@ int recur_cols_warps(int dim, int64_t B);
 // CTAs of the persistent FP64 kernel that can be resident at once on the
 // current device (0: cooperative launch unavailable).
 int persist_max_ctas(int rhs, int dim);
+// History workers of a persistent launch of `grid` CTAs for B trajectories
+// (the most chunks per block it uses).
+int persist_workers(int grid, int B);
 // doubles of the persistent kernel's partial-sum slots.
 size_t persist_part_elems(int max_chunks, int cols);
 // The whole FP64 solve of a batch (after launch_init) as one cooperative
 // launch of `grid` CTAs: bt.B recurrence CTAs and grid - bt.B history CTAs
-// (chunks per block at most max_chunks = grid - bt.B).  done: nblk x
+// (chunks per block at most max_chunks, e.g. persist_workers(grid, B)).  done: nblk x
 // ceil(cols/4) ints, r_done: B ints, both zero; err: set on a wait timeout.
 cudaError_t launch_persist_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
                                 const StepConsts &k, int64_t nblk, int grid, int max_chunks,

@@ -13,28 +13,29 @@ constexpr int kL = kRecurL;     // targets per block (one per lane)
 namespace f64 {
 constexpr int kTile = 256;      // points staged in shared memory at a time
 
-// One CTA of 32 * kHistCols threads: chunk `chunk` (points k in
-// [chunk*kc, min((chunk+1)*kc, k_end))) of the far history of block c for the
-// columns col0 .. col0+3.
+// The points k in [k0, k1) of the far history of block c for the columns
+// col0 .. col0+3, by 32 * kColsPerCta threads (tid = 0 .. 127 among them) that
+// share the tiles sF[kTile * kColsPerCta], sB, sA[NW][kTile + kL] and
+// synchronise with sync(); the sums go to out[(kind * kL + a) * out_ld + w],
+// kind 0 predictor, 1 corrector, a the target, w < 4 the column after col0.
 // MULTI: one order per component, column col's weights at WB + (col % dim)
 // * wstride (WA likewise), one staged window per warp.  CG: read F around L1
 // (ld.global.cg), for callers whose F rows are written by other CTAs of the
 // same launch while it runs.
-template <bool MULTI = false, bool CG = false>
-__device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF, int cols,
+template <bool MULTI, bool CG, class Sync>
+__device__ inline void hist_fp64_chunk(const double *__restrict__ F, int64_t ldF, int cols,
                                        const double *__restrict__ WB,
-                                       const double *__restrict__ WA, int64_t c, int64_t kc,
-                                       int64_t k_end, double *__restrict__ part, int64_t chunk,
-                                       int col0, int64_t wstride = 0, int dim = 1)
+                                       const double *__restrict__ WA, int64_t c, int64_t k0,
+                                       int64_t k1, double *__restrict__ out, int64_t out_ld,
+                                       int col0, int64_t wstride, int dim, int tid, double *sF,
+                                       double (*sB)[kTile + kL], double (*sA)[kTile + kL],
+                                       Sync sync)
 {
     constexpr int NW = MULTI ? kColsPerCta : 1;  // weight windows
-    __shared__ double sF[kTile * kColsPerCta];
-    __shared__ double sB[NW][kTile + kL], sA[NW][kTile + kL];
-    const int64_t k0 = chunk * kc;
-    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
+    constexpr int nthr = kWarp * kColsPerCta;
     const int ncol = min(kColsPerCta, cols - col0);
-    const int w = threadIdx.x / kWarp;
-    const int a = threadIdx.x % kWarp;  // target m = cL+1+a
+    const int w = tid / kWarp;
+    const int a = tid % kWarp;  // target m = cL+1+a
     double sp = 0.0, sc = 0.0;
 
     for (int64_t t0 = k0; t0 < k1; t0 += kTile) {
@@ -45,24 +46,24 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
         const int64_t d_min = c * kL + 2 - t1;
         const int nwin = nk + kL - 1;
         if constexpr (MULTI) {
-            for (int i = threadIdx.x; i < NW * nwin; i += blockDim.x) {
+            for (int i = tid; i < NW * nwin; i += nthr) {
                 const int v = i / nwin, ii = i % nwin;
                 const int64_t o = (int64_t)((col0 + v) % dim) * wstride;
                 sB[v][ii] = WB[o + d_min + ii];
                 sA[v][ii] = WA[o + d_min + ii];
             }
         } else {
-            for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
+            for (int i = tid; i < nwin; i += nthr) {
                 sB[0][i] = WB[d_min + i];
                 sA[0][i] = WA[d_min + i];
             }
         }
-        for (int i = threadIdx.x; i < nk * kColsPerCta; i += blockDim.x) {
+        for (int i = tid; i < nk * kColsPerCta; i += nthr) {
             const int k = i / kColsPerCta, j = i % kColsPerCta;
             const double *src = F + (t0 + k) * ldF + col0 + j;
             sF[i] = j < ncol ? (CG ? __ldcg(src) : *src) : 0.0;
         }
-        __syncthreads();
+        sync();
         if (w < ncol) {
             // d - d_min = (cL+1+a - (t0+j)) - (cL+2-t1) = a + nk-1-j
             const double *fb = sF + w;
@@ -75,13 +76,33 @@ __device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF
                 sc = fma(wa[base - j], f, sc);
             }
         }
-        __syncthreads();
+        sync();
     }
     if (w < ncol) {
-        double *out = part + ((chunk * 2) * kL + a) * (int64_t)cols + col0 + w;
-        out[0] = sp;
-        out[(int64_t)kL * cols] = sc;
+        out[(int64_t)a * out_ld + w] = sp;
+        out[(int64_t)(kL + a) * out_ld + w] = sc;
     }
+}
+
+// One CTA of 32 * kColsPerCta threads: chunk `chunk` (points k in
+// [chunk*kc, min((chunk+1)*kc, k_end))) of the far history of block c for the
+// columns col0 .. col0+3 into part[chunk][2][kL][cols] (hist_fp64_chunk with
+// the CTA's own tiles and barrier).
+template <bool MULTI = false>
+__device__ inline void hist_fp64_block(const double *__restrict__ F, int64_t ldF, int cols,
+                                       const double *__restrict__ WB,
+                                       const double *__restrict__ WA, int64_t c, int64_t kc,
+                                       int64_t k_end, double *__restrict__ part, int64_t chunk,
+                                       int col0, int64_t wstride = 0, int dim = 1)
+{
+    constexpr int NW = MULTI ? kColsPerCta : 1;
+    __shared__ double sF[kTile * kColsPerCta];
+    __shared__ double sB[NW][kTile + kL], sA[NW][kTile + kL];
+    const int64_t k0 = chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
+    hist_fp64_chunk<MULTI, false>(F, ldF, cols, WB, WA, c, k0, k1,
+                                  part + (chunk * 2) * kL * (int64_t)cols + col0, cols, col0,
+                                  wstride, dim, threadIdx.x, sF, sB, sA, [] { __syncthreads(); });
 }
 
 }  // namespace f64

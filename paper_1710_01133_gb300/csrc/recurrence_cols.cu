@@ -53,13 +53,21 @@ __device__ __forceinline__ FF ld_ff(const float2 *p)
 }
 
 // History of every point before block c for target a of column col, kind k
-// (0 predictor, 1 corrector): the far value plus the near partials.
+// (0 predictor, 1 corrector): the far value plus the near partials (at most
+// kMaxNear), all loads issued before the additions.
+constexpr int kMaxNear = 3;
 __device__ __forceinline__ FF hist_in(const HistIn &h, int k, int a, int64_t col, int cols)
 {
-    FF v = h.G ? ld_ff(h.G + ((int64_t)k * h.g_rows + h.g_off + a) * cols + col) : FF(0);
-    for (int ch = 0; ch < h.n_near; ++ch)
-        v = v + ld_ff(h.near + (((int64_t)ch * 2 + k) * kColL + a) * cols + col);
-    return v;
+    float2 v[kMaxNear + 1];
+    v[0] = h.G ? h.G[((int64_t)k * h.g_rows + h.g_off + a) * cols + col] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ch = 0; ch < kMaxNear; ++ch)
+        v[ch + 1] = ch < h.n_near ? h.near[(((int64_t)ch * 2 + k) * kColL + a) * cols + col]
+                                  : make_float2(0.f, 0.f);
+    FF s(v[0].x, v[0].y);
+#pragma unroll
+    for (int ch = 1; ch <= kMaxNear; ++ch) s = s + FF(v[ch].x, v[ch].y);
+    return s;
 }
 
 // Time-only part of f for the 64 targets of block c: X[a][b] = aux(t_m, p_b),
@@ -373,6 +381,7 @@ cudaError_t launch_recur_cols(int rhs, const DevBatch &bt, const float2 *WB, con
                               const float2 *X, int warps_per_cta, cudaStream_t st)
 {
     if (warps_per_cta < 0 || warps_per_cta > kMaxWarps) return cudaErrorInvalidValue;
+    if (hin.n_near < 0 || hin.n_near > kMaxNear) return cudaErrorInvalidValue;
     bool need_x = false;
     const bool ok = dispatch_rhs(rhs, bt.dim, [&]<class R, int D>() {
         need_x = R::kForcing;

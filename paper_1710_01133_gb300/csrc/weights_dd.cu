@@ -10,14 +10,17 @@
 // written as s <- s (s + 2) on s = e^r - 1, and ln x from the double log by
 // one Newton step on exp (which doubles its ~53 correct bits).
 //
-// The printed formulas cancel: B by ~log2 d bits, A and C by ~2 log2 d bits.
-// Up to d = 64 they are evaluated as printed (at most 12 of 106 bits lost);
-// beyond, from series in u = 1/d whose terms do not cancel the result:
+// The printed formulas cancel: B by ~log2 d bits, A and C by ~2 log2 d bits,
+// which multiplies the pow errors.  Up to d = 4 they are evaluated as printed
+// (at most 4 bits lost); beyond, from series in u = 1/d (u <= 1/5) whose terms
+// do not cancel the result:
 //   B(d) = d^a  sum_{k>=1} (-1)^(k+1) binom(a, k) u^k           / Gamma(a+1)
 //   A(d) = 2 d^p sum_{k>=1} binom(p, 2k) u^(2k)                 / Gamma(a+2)
 //   C(n) = n^p  sum_{k>=2} (a binom(a, k-1) - binom(a, k)) u^k  / Gamma(a+2)
 // with p = a + 1 (the expansions of 1 - (1 - u)^a, (1+u)^p - 2 + (1-u)^p and
 // 1 - (1 - a u)(1 + u)^a), summed until a term is below 2^-110 of the sum.
+// p = a + 1 is not a double in general (a = 0.3 loses its last bits), so it is
+// kept as an exact pair for the binomial coefficients and x^p is x x^a.
 // 1/Gamma(a+1) and 1/Gamma(a+2) come from the host as double-double pairs.
 #include "fabm_internal.cuh"
 
@@ -121,14 +124,17 @@ __device__ dd dd_pow(double x, double a)
     return dd_exp(dd_mul_d(dd_log(x), a));
 }
 
-// binom(a, k) from binom(a, k-1): times (a - k + 1) / k, with a - k + 1 exact
-// as a pair.
-__device__ __forceinline__ dd binom_next(dd c, double a, int k)
+// binom(a, k) from binom(a, k-1): times (a - k + 1) / k, with a - k + 1 a
+// pair (a itself a pair: p = a + 1 does not fit a double).
+__device__ __forceinline__ dd binom_next(dd c, dd a, int k)
 {
-    return dd_div_d(dd_mul(c, two_sum(a, -(double)(k - 1))), (double)k);
+    return dd_div_d(dd_mul(c, dd_add(a, dd{-(double)(k - 1), 0.0})), (double)k);
 }
 
-constexpr int kDirect = 64;  // distances up to here: the printed differences
+// x^(a+1) = x x^a for an integer x >= 1.
+__device__ __forceinline__ dd dd_pow1(double x, double a) { return dd_mul_d(dd_pow(x, a), x); }
+
+constexpr int kDirect = 4;  // distances up to here: the printed differences
 
 __device__ dd weight_B(int64_t d, double a, dd ig1)
 {
@@ -137,9 +143,10 @@ __device__ dd weight_B(int64_t d, double a, dd ig1)
     const double x = (double)d;
     if (d <= kDirect) return dd_mul(dd_sub(dd_pow(x, a), dd_pow(x - 1.0, a)), ig1);
     const dd u = dd_div_d(dd{1.0, 0.0}, x);
-    dd c = {a, 0.0}, uk = u, sum = dd_mul(c, u);  // k = 1: binom(a, 1) u
-    for (int k = 2; k < 64; ++k) {
-        c = binom_next(c, a, k);
+    const dd ad = {a, 0.0};
+    dd c = ad, uk = u, sum = dd_mul(c, u);  // k = 1: binom(a, 1) u
+    for (int k = 2; k < 80; ++k) {
+        c = binom_next(c, ad, k);
         uk = dd_mul(uk, u);
         const dd t = dd_mul(c, uk);
         sum = (k & 1) ? dd_add(sum, t) : dd_sub(sum, t);  // (-1)^(k+1) binom(a, k) u^k
@@ -151,19 +158,20 @@ __device__ dd weight_B(int64_t d, double a, dd ig1)
 __device__ dd weight_A(int64_t d, double a, dd ig2)
 {
     if (d <= 0) return {0.0, 0.0};
-    const double p = a + 1.0;  // exact: 0 < a < 2
-    if (d == 1) return dd_mul(dd_sub(dd_pow(2.0, p), dd{2.0, 0.0}), ig2);
+    const dd p = two_sum(a, 1.0);  // a + 1 exactly
+    // A(1) = (2^p - 2) / Gamma(a+2) = 2 (2^a - 1) / Gamma(a+2)
+    if (d == 1) return dd_mul(dd_mul_d(dd_sub(dd_pow(2.0, a), dd{1.0, 0.0}), 2.0), ig2);
     const double x = (double)d;
     if (d <= kDirect) {
-        const dd s = dd_add(dd_sub(dd_pow(x + 1.0, p), dd_mul_d(dd_pow(x, p), 2.0)),
-                            dd_pow(x - 1.0, p));
+        const dd s = dd_add(dd_sub(dd_pow1(x + 1.0, a), dd_mul_d(dd_pow1(x, a), 2.0)),
+                            dd_pow1(x - 1.0, a));
         return dd_mul(s, ig2);
     }
     const dd u = dd_div_d(dd{1.0, 0.0}, x);
     const dd u2 = dd_mul(u, u);
-    dd c = {p, 0.0};  // binom(p, 1); each round advances it to binom(p, 2k), then 2k+1
+    dd c = p;  // binom(p, 1); each round advances it to binom(p, 2k), then 2k+1
     dd u2k = {1.0, 0.0}, sum = {0.0, 0.0};
-    for (int k = 1; k < 40; ++k) {
+    for (int k = 1; k < 60; ++k) {
         c = binom_next(c, p, 2 * k);
         u2k = dd_mul(u2k, u2);
         const dd t = dd_mul(c, u2k);
@@ -171,29 +179,30 @@ __device__ dd weight_A(int64_t d, double a, dd ig2)
         if (fabs(t.hi) < 0x1p-110 * fabs(sum.hi)) break;
         c = binom_next(c, p, 2 * k + 1);
     }
-    return dd_mul(dd_mul_d(dd_mul(dd_pow(x, p), sum), 2.0), ig2);
+    return dd_mul(dd_mul_d(dd_mul(dd_pow1(x, a), sum), 2.0), ig2);
 }
 
 __device__ dd weight_C(int64_t n, double a, dd ig2)
 {
     if (n <= 0) return dd_mul(dd{a, 0.0}, ig2);
-    const double x = (double)n, p = a + 1.0;
+    const double x = (double)n;
     if (n <= kDirect) {
         // n^p - (n - a) (n + 1)^a with n - a as an exact pair
-        const dd s = dd_sub(dd_pow(x, p), dd_mul(two_sum(x, -a), dd_pow(x + 1.0, a)));
+        const dd s = dd_sub(dd_pow1(x, a), dd_mul(two_sum(x, -a), dd_pow(x + 1.0, a)));
         return dd_mul(s, ig2);
     }
     const dd u = dd_div_d(dd{1.0, 0.0}, x);
-    dd cprev = {a, 0.0}, uk = u, sum = {0.0, 0.0};  // binom(a, 1), u^1
-    for (int k = 2; k < 64; ++k) {
-        const dd ck = binom_next(cprev, a, k);
+    const dd ad = {a, 0.0};
+    dd cprev = ad, uk = u, sum = {0.0, 0.0};  // binom(a, 1), u^1
+    for (int k = 2; k < 80; ++k) {
+        const dd ck = binom_next(cprev, ad, k);
         uk = dd_mul(uk, u);
         const dd t = dd_mul(dd_sub(dd_mul_d(cprev, a), ck), uk);
         sum = dd_add(sum, t);
         if (fabs(t.hi) < 0x1p-110 * fabs(sum.hi)) break;
         cprev = ck;
     }
-    return dd_mul(dd_mul(dd_pow(x, p), sum), ig2);
+    return dd_mul(dd_mul(dd_pow1(x, a), sum), ig2);
 }
 
 __global__ void weights_x2_kernel(double a, int64_t n, dd ig1, dd ig2, double *Bh, double *Bl,
