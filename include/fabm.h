@@ -351,7 +351,7 @@ typedef struct fabm_server fabm_server;
 
 typedef struct {
     int dim;               /* 1..FABM_MAX_DIM, matching rhs_id */
-    double alpha;          /* 0 < alpha < 1 */
+    double alpha;          /* 0 < alpha < 2 (y'(0) = 0 for alpha > 1 unless given) */
     double h;              /* step size > 0 */
     int64_t N;             /* steps, 1..2^31 */
     int rhs_id;            /* FABM_RHS_* */
@@ -366,8 +366,14 @@ enum { FABM_REQ_WAITING = 0, FABM_REQ_RUNNING = 1, FABM_REQ_DONE = 2, FABM_REQ_F
  * max_slots: most requests in flight at once. */
 fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots,
                                fabm_server **out);
-/* Queue a request (copied); *ticket identifies it. */
+/* Queue a request (copied); *ticket identifies it.  For 1 < alpha < 2 the
+ * Taylor part of the initial data is y0 alone (y'(0) = 0). */
 fabm_status fabm_server_submit(fabm_server *s, const fabm_request *req, int64_t *ticket);
+/* As fabm_server_submit with y'(0) for 1 < alpha < 2 (Sec. 2: the Taylor part
+ * y0 + t y'(0)).  y1: dim doubles (host, copied); NULL means zero.
+ * FABM_EINVAL if y1 is given for alpha <= 1 or holds a non-finite value. */
+fabm_status fabm_server_submit_ic(fabm_server *s, const fabm_request *req, const double *y1,
+                                  int64_t *ticket);
 /* One scheduling step (synchronous): admit, advance all admitted requests by
  * one block, retire finished ones.  Reports the requests in flight and waiting. */
 fabm_status fabm_server_step(fabm_server *s, int *n_active, int *n_waiting);

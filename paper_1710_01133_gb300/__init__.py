@@ -35,7 +35,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
             "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
             "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures",
-            "fabm_copy_weights_lo")
+            "fabm_copy_weights_lo", "fabm_server_submit_ic")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
     lib.fabm_set_graphs.argtypes = [vp, i]
     lib.fabm_server_create.argtypes = [ctypes.c_size_t, i, i, P(vp)]
     lib.fabm_server_submit.argtypes = [vp, P(fabm_request), P(i64)]
+    lib.fabm_server_submit_ic.argtypes = [vp, P(fabm_request), P(d), P(i64)]
     lib.fabm_server_step.argtypes = [vp, P(i), P(i)]
     lib.fabm_server_poll.argtypes = [vp, i64, P(i)]
     lib.fabm_server_result.argtypes = [vp, i64, P(d)]
@@ -102,7 +103,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_server_cancel.argtypes = [vp, i64]
     lib.fabm_server_shape.argtypes = [vp, i64, P(i64), P(i)]
     lib.fabm_server_finished.argtypes = [vp, P(i64), i, P(i)]
-    for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_step", "fabm_server_poll",
+    for f in ("fabm_server_create", "fabm_server_submit", "fabm_server_submit_ic",
+              "fabm_server_step", "fabm_server_poll",
               "fabm_server_result", "fabm_server_wait", "fabm_server_stats", "fabm_server_destroy",
               "fabm_server_checkpoint", "fabm_server_resume", "fabm_server_cancel",
               "fabm_server_shape", "fabm_server_finished"):
@@ -470,14 +472,22 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    def submit(self, rhs, dim, alpha, h, N, y0, params=None) -> int:
+    def submit(self, rhs, dim, alpha, h, N, y0, params=None, y1=None) -> int:
+        """Queue a request; y1 = y'(0) (dim values) for 1 < alpha < 2."""
         rid = RHS[rhs] if isinstance(rhs, str) else int(rhs)
         p = _f64(params if params is not None else []).reshape(-1)
         y = _f64(y0).reshape(-1)
         req = fabm_request(int(dim), float(alpha), float(h), int(N), rid,
                            _dp(p) if p.size else None, int(p.size), _dp(y))
         t = ctypes.c_int64()
-        _check(load().fabm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        if y1 is None:
+            _check(load().fabm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        else:
+            v = _f64(y1).reshape(-1)
+            if v.size != int(dim):
+                raise ValueError("y1 needs dim values")
+            _check(load().fabm_server_submit_ic(self.handle, ctypes.byref(req), _dp(v),
+                                                ctypes.byref(t)))
         return t.value
 
     def step(self):

@@ -46,6 +46,7 @@ struct SlotDev {
     int64_t N, w_ext;
     int64_t *Nb;  // device copy of N (read by the recurrence)
     double *F, *Y, *y0, *params, *WB, *WA, *WD, *G;
+    double *y1;  // y'(0) (dim doubles) for 1 < alpha < 2, or NULL: Taylor part y0
     float *WBf, *WAf, *Ff;  // split slots: fp32 weights and f rounded to float
     void *part;  // double (FP64) or float2 (split) partials
     StepConsts kc;
@@ -71,6 +72,7 @@ __device__ inline DevBatch slot_batch(const SlotDev &s)
     bt.N = s.N;
     bt.N_each = s.Nb;
     bt.y0 = s.y0;
+    bt.y1 = s.y1;
     bt.params = s.params;
     bt.F = s.F;
     bt.Ff = s.Ff;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerHistCta)
 }
 
 // One CTA per slot: G[gbuf][kind][t][col] = sum over the chunks in ascending
-// order (double, or float-float rounded once to double).
+// order (compensated double, or float-float rounded once to double).
 __global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
 {
     const Item it = items[blockIdx.x];
@@ -292,10 +294,18 @@ __global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const It
             }
             G[o] = (double)hi + (double)lo;
         } else {
+            // Neumaier: the rounding error of every addition (TwoSum) is kept
+            // in a second sum, added once at the end; chunk order fixed
             const double *p = static_cast<const double *>(s.part);
-            double acc = 0.0;
-            for (int ch = 0; ch < it.chunk; ++ch) acc += p[(int64_t)ch * n_out + o];
-            G[o] = acc;
+            double acc = 0.0, err = 0.0;
+            for (int ch = 0; ch < it.chunk; ++ch) {
+                const double v = p[(int64_t)ch * n_out + o];
+                const double t = acc + v;
+                const double bv = t - acc;
+                err += (acc - (t - bv)) + (v - bv);
+                acc = t;
+            }
+            G[o] = acc + err;
         }
     }
 }
@@ -354,7 +364,7 @@ struct Ckpt {
 
 // Layout of a serialized checkpoint: this header, then F and Y (rows x dim
 // each) and G (2 x 2 x kSL x dim), doubles in the host's byte order.
-constexpr char kCkptMagic[8] = {'F', 'A', 'B', 'M', 'C', 'K', 'P', '1'};
+constexpr char kCkptMagic[8] = {'F', 'A', 'B', 'M', 'C', 'K', 'P', '2'};
 struct CkptHead {
     char magic[8];
     int32_t precision, dim, rhs, n_params;
@@ -363,6 +373,8 @@ struct CkptHead {
     unsigned long long status;
     double params[kMaxParams];
     double y0[FABM_MAX_DIM];
+    int32_t has_y1, pad;
+    double y1[FABM_MAX_DIM];  // y'(0) when has_y1 (1 < alpha < 2)
 };
 
 struct Req {
@@ -373,6 +385,8 @@ struct Req {
     double params[kMaxParams];
     int n_params;
     double y0[FABM_MAX_DIM];
+    double y1[FABM_MAX_DIM];  // y'(0), used when has_y1 (1 < alpha < 2)
+    int has_y1;
     std::shared_ptr<const Ckpt> ckpt;  // set for a resumed request
 };
 
@@ -402,6 +416,7 @@ size_t slot_bytes(const Req &r, int hk, int64_t *w_ext_out)
     add(sizeof(int64_t));                                   // Nb
     add(sizeof(unsigned long long));                        // status
     add(sizeof(double) * FABM_MAX_DIM);                     // y0
+    add(sizeof(double) * FABM_MAX_DIM);                     // y1
     add(sizeof(double) * kMaxParams);                       // params
     for (int i = 0; i < 3; ++i) add(sizeof(double) * (w_ext + 1));  // WB WA WD
     if (hk == FABM_HIST_FP32C) {
@@ -430,6 +445,8 @@ void slot_layout(Slot &s, int hk, int64_t w_ext)
     d.Nb = reinterpret_cast<int64_t *>(take(sizeof(int64_t)));
     d.status = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
     d.y0 = reinterpret_cast<double *>(take(sizeof(double) * FABM_MAX_DIM));
+    double *y1 = reinterpret_cast<double *>(take(sizeof(double) * FABM_MAX_DIM));
+    d.y1 = r.has_y1 ? y1 : nullptr;
     d.params = reinterpret_cast<double *>(take(sizeof(double) * kMaxParams));
     d.WB = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
     d.WA = reinterpret_cast<double *>(take(sizeof(double) * (w_ext + 1)));
@@ -599,6 +616,8 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
             double par[kMaxParams] = {};
             for (int q = 0; q < s.req.n_params; ++q) par[q] = s.req.params[q];
             SRV_TRY(cudaMemcpyAsync(s.dev.y0, s.req.y0, sizeof(double) * s.req.dim, cudaMemcpyHostToDevice, S->sR));
+            if (s.dev.y1)
+                SRV_TRY(cudaMemcpyAsync(s.dev.y1, s.req.y1, sizeof(double) * s.req.dim, cudaMemcpyHostToDevice, S->sR));
             SRV_TRY(cudaMemcpyAsync(s.dev.params, par, sizeof par, cudaMemcpyHostToDevice, S->sR));
             SRV_TRY(cudaMemcpyAsync(s.dev.Nb, &s.req.N, sizeof(int64_t), cudaMemcpyHostToDevice, S->sR));
             if (const Ckpt *k = s.req.ckpt.get()) {  // resumed: the saved state
@@ -704,12 +723,15 @@ fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots
     return FABM_OK;
 }
 
-fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *ticket)
+static fabm_status server_submit(fabm_server *S, const fabm_request *q, const double *y1,
+                                 int64_t *ticket)
 {
     set_last_error("");
     if (!S || !q || !ticket) return srv_fail(FABM_EINVAL, "NULL argument");
     if (q->dim < 1 || q->dim > FABM_MAX_DIM) return srv_fail(FABM_EINVAL, "dim %d", q->dim);
-    if (!(q->alpha > 0.0 && q->alpha < 1.0)) return srv_fail(FABM_EINVAL, "alpha %g", q->alpha);
+    if (!(q->alpha > 0.0 && q->alpha < 2.0)) return srv_fail(FABM_EINVAL, "alpha %g", q->alpha);
+    if (y1 && !(q->alpha > 1.0))
+        return srv_fail(FABM_EINVAL, "y'(0) given for alpha %g <= 1", q->alpha);
     if (!(q->h > 0.0) || !std::isfinite(q->h)) return srv_fail(FABM_EINVAL, "h %g", q->h);
     if (q->N < 1 || q->N > (1LL << 31)) return srv_fail(FABM_EINVAL, "N %lld", (long long)q->N);
     const int np = rhs_n_params(q->rhs_id);
@@ -726,6 +748,13 @@ fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *t
         if (!std::isfinite(q->y0[i])) return srv_fail(FABM_EINVAL, "y0 not finite");
         r.y0[i] = q->y0[i];
     }
+    if (y1) {
+        r.has_y1 = 1;
+        for (int i = 0; i < q->dim; ++i) {
+            if (!std::isfinite(y1[i])) return srv_fail(FABM_EINVAL, "y'(0) not finite");
+            r.y1[i] = y1[i];
+        }
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     r.ticket = S->next_ticket++;
     S->queue.push_back(r);
@@ -733,6 +762,17 @@ fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *t
     S->shapes[r.ticket] = {r.N, r.dim};
     *ticket = r.ticket;
     return FABM_OK;
+}
+
+fabm_status fabm_server_submit(fabm_server *S, const fabm_request *q, int64_t *ticket)
+{
+    return server_submit(S, q, nullptr, ticket);
+}
+
+fabm_status fabm_server_submit_ic(fabm_server *S, const fabm_request *q, const double *y1,
+                                  int64_t *ticket)
+{
+    return server_submit(S, q, y1, ticket);
 }
 
 fabm_status fabm_server_step(fabm_server *S, int *n_active, int *n_waiting)
@@ -824,7 +864,8 @@ fabm_status fabm_server_checkpoint(fabm_server *S, int64_t ticket, void *buf, si
     hd.alpha = r->alpha, hd.h = r->h, hd.N = r->N, hd.c = c, hd.rows = rows;
     hd.status = ~0ull;
     for (int i = 0; i < kMaxParams; ++i) hd.params[i] = r->params[i];
-    for (int i = 0; i < FABM_MAX_DIM; ++i) hd.y0[i] = r->y0[i];
+    for (int i = 0; i < FABM_MAX_DIM; ++i) hd.y0[i] = r->y0[i], hd.y1[i] = r->y1[i];
+    hd.has_y1 = r->has_y1;
     uint8_t *p = static_cast<uint8_t *>(buf);
     double *F = reinterpret_cast<double *>(p + sizeof hd);
     double *Y = F + rows * r->dim;
@@ -860,7 +901,8 @@ fabm_status fabm_server_resume(fabm_server *S, const void *buf, size_t size, int
                         hd.precision, S->precision);
     if (hd.dim < 1 || hd.dim > FABM_MAX_DIM || !rhs_supports_dim(hd.rhs, hd.dim) ||
         hd.n_params < rhs_n_params(hd.rhs) || hd.n_params > kMaxParams ||
-        !(hd.alpha > 0.0 && hd.alpha < 1.0) || !(hd.h > 0.0) || hd.N < 1 || hd.N > (1LL << 31))
+        !(hd.alpha > 0.0 && hd.alpha < 2.0) || !(hd.h > 0.0) || hd.N < 1 || hd.N > (1LL << 31) ||
+        (hd.has_y1 != 0 && hd.has_y1 != 1) || (hd.has_y1 && !(hd.alpha > 1.0)))
         return srv_fail(FABM_EINVAL, "checkpoint header is invalid");
     const int64_t nblk = (hd.N + kSL - 1) / kSL;
     const int64_t rows = hd.c == 0 ? 0 : std::min<int64_t>(hd.N, hd.c * kSL) + 1;
@@ -872,7 +914,8 @@ fabm_status fabm_server_resume(fabm_server *S, const void *buf, size_t size, int
     r.dim = hd.dim, r.rhs = hd.rhs, r.alpha = hd.alpha, r.h = hd.h, r.N = hd.N;
     r.n_params = hd.n_params;
     for (int i = 0; i < kMaxParams; ++i) r.params[i] = hd.params[i];
-    for (int i = 0; i < FABM_MAX_DIM; ++i) r.y0[i] = hd.y0[i];
+    for (int i = 0; i < FABM_MAX_DIM; ++i) r.y0[i] = hd.y0[i], r.y1[i] = hd.y1[i];
+    r.has_y1 = hd.has_y1;
     if (hd.c > 0) {
         auto k = std::make_shared<Ckpt>();
         const double *F = reinterpret_cast<const double *>(static_cast<const uint8_t *>(buf) + sizeof hd);

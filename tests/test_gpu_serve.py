@@ -238,3 +238,48 @@ def test_finished_lists_each_request_once(gpu_lib):
         assert sorted(seen) == sorted(tickets)
         assert all(srv.poll(t) == gpu_lib.FABM_REQ_DONE for t in tickets)
         assert srv.finished() == []
+
+
+# 1 < alpha < 2 (Sec. 2: the Taylor part y0 + t y'(0)); y1 None means y'(0) = 0
+HIGH = [
+    ("linear", 2, 1.5, 1e-3, 2000, [1.0, -0.5], (1.0,), [0.3, 0.2]),
+    ("duffing", 2, 1.8, 1e-3, 1500, [0.2, 0.0], (0.1, 1.2, 0.7), [0.0, 0.1]),
+    ("lorenz", 3, 1.2, 5e-4, 1200, [1.0, 1.0, 1.0], LORENZ_PARAMS, None),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_orders_between_one_and_two_against_the_oracle(gpu_lib, parity, precision):
+    with gpu_lib.Server(8 << 30, precision=precision) as srv:
+        tickets = [srv.submit(r, d, a, h, N, y0, p, y1=y1) for r, d, a, h, N, y0, p, y1 in HIGH]
+        other = srv.submit(*MIX[1][:5], MIX[1][5], MIX[1][6])
+        run_to_completion(srv, tickets + [other])
+        results = [srv.result(t) for t in tickets]
+    bar = 1e-12 if precision == "fp64" else 1e-6
+    for (rhs, dim, a, h, N, y0, p, y1), got in zip(HIGH, results):
+        assert got.shape == (N + 1, dim)
+        ref = oracle.solve(rhs, a, h, N, y0, params=p, y1=y1)
+        parity(rel_err(got, ref), bar, f"{rhs}-alpha{a}")
+
+
+def test_orders_between_one_and_two_checkpoint_keeps_y1(gpu_lib):
+    r, d, a, h, N, y0, p, y1 = HIGH[0]
+    with gpu_lib.Server(8 << 30) as first:
+        t = first.submit(r, d, a, h, N, y0, p, y1=y1)
+        for _ in range(5):
+            first.step()
+        state = first.checkpoint(t)
+        run_to_completion(first, [t])
+        ref = first.result(t)
+    with gpu_lib.Server(8 << 30) as second:
+        t2 = second.resume(state)
+        run_to_completion(second, [t2])
+        assert np.array_equal(second.result(t2), ref)
+
+
+def test_order_and_y1_checks_at_submission(gpu_lib):
+    with gpu_lib.Server(1 << 30) as srv:
+        for alpha, y1 in ((0.8, [0.1]), (2.0, None), (1.5, [float("nan")])):
+            with pytest.raises(gpu_lib.FabmError) as e:
+                srv.submit("linear", 1, alpha, 1e-3, 100, [1.0], (1.0,), y1=y1)
+            assert e.value.status == gpu_lib.FABM_EINVAL
