@@ -50,6 +50,10 @@ WORKLOADS = {
     "lcr-sweep": lambda: _lcr_sweep(),
 }
 DEFAULT_WORKLOAD = "lorenz-long"
+# arithmetic of the history sum, by the kernel a solve ran: three-term bf16
+# split on tensor cores, compensated fp32, double, double-double
+DTYPE_OF_HISTORY = {"tensor": "bf16x3", "tensor-wide": "bf16x3", "fp32c": "f32c",
+                    "fp64": "f64", "fp64-persist": "f64", "x2": "f64x2"}
 
 
 def _lorenz_long():
@@ -161,6 +165,8 @@ KERNEL_SOURCES = {
     "history_fp64": ["history_fp64.cu", "history_blocks.cuh", "fabm_internal.cuh"],
     "history_split": ["history_far.cu", "history_split.cu", "sm100_ptx.cuh", "fabm_internal.cuh"],
     "recurrence": ["recurrence.cu", "recurrence.cuh", "rhs.cuh", "fabm_internal.cuh"],
+    "recurrence_split": ["recurrence_cols.cu", "recurrence.cuh", "rhs.cuh", "ff.cuh",
+                         "fabm_internal.cuh"],
 }
 
 
@@ -283,7 +289,7 @@ def roofline(kind, ks, precision, clocks, workload, w=None, step_ms=None):
                     "frac": in_launch / peak if peak else None,
                     "achieved_over": out["in_launch"]["over"]})
     key = {"history": f"history_{'split' if precision == 'split' else 'fp64'}",
-           "recurrence": "recurrence"}.get(kind)
+           "recurrence": "recurrence_split" if precision == "split" else "recurrence"}.get(kind)
     # profiles/<kernel class>_<precision>_<workload>.md, e.g. history_fp64_lorenz-single.md
     traffic = _profile_traffic(key, f"{kind}_{precision}_{workload}") if key else None
     out["traffic"] = traffic
@@ -457,7 +463,8 @@ def run_served(args):
     line = {
         "metric": "steps_traj_per_s", "value": timed["steps_traj_per_s"], "unit": "steps*traj/s",
         "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": timed["wall_s"] * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32c" if args.precision == "split" else "f64",
         "data": "synthetic",
         "config": {"workload": f"served-mix-{n}req-k12..{k_hi}", "precision": args.precision,
                    "requests": n, "arrival_rate_per_s": rate, "hbm_budget_gb": 120},
@@ -633,7 +640,7 @@ def main():
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64x2": "f64x2", "split": "bf16x3"}.get(args.precision, "f64"),
+            "dtype": DTYPE_OF_HISTORY.get(solver.last_history_kernel, "f64"),
             "data": "synthetic",
             "config": _config(w, args),
             "history_gmac_s": w.history_macs() * ws / (step_ms * 1e-3) / 1e9,

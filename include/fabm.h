@@ -168,7 +168,8 @@ enum {
                               of blocks with 128 targets per MMA (one weight kind per
                               CTA, exact per 128-point group), the latest two or three
                               64-point segments per block with 64; automatic choice
-                              on the tensor path from N >= 384 on                     */
+                              on the tensor path from N >= 257 on (the first pair of
+                              blocks with a group two groups back)                   */
     FABM_HIST_FP64_PERSIST = 6 /* FP64 precision, the whole solve as one persistent
                               cooperative launch: one CTA per trajectory runs its
                               recurrence with weights and the recent window of f in
@@ -185,6 +186,10 @@ enum {
  * and sets the fastest. */
 fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel);
 int fabm_get_history_kernel(const fabm_solver *s);
+/* History kernel the last solve ran (FABM_HIST_*, after the automatic choice;
+ * FABM_HIST_TENSOR_WIDE where its far history used 128 targets per MMA), or -1
+ * before the first solve or for a NULL solver. */
+int fabm_last_history_kernel(const fabm_solver *s);
 
 /* Step layouts of the split-precision recurrence on the tensor-history path
  * (fabm_set_recurrence_layout); both compute the same steps in float-float. */

@@ -35,7 +35,7 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
             "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
             "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures",
-            "fabm_copy_weights_lo", "fabm_server_submit_ic")
+            "fabm_copy_weights_lo", "fabm_server_submit_ic", "fabm_last_history_kernel")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
     lib.fabm_autotune.restype = i
     lib.fabm_set_history_kernel.argtypes = [vp, i]
     lib.fabm_get_history_kernel.argtypes = [vp]
+    lib.fabm_last_history_kernel.argtypes = [vp]
     lib.fabm_set_recurrence_layout.argtypes = [vp, i]
     lib.fabm_weights_x2.argtypes = [d, i64] + [P(d)] * 6
     lib.fabm_weights_x2.restype = i
@@ -133,7 +134,7 @@ def load(build_if_missing: bool = True):
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
               "fabm_get_history_kernel", "fabm_set_recurrence_layout",
-              "fabm_get_recurrence_layout"):
+              "fabm_get_recurrence_layout", "fabm_last_history_kernel"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -274,6 +275,11 @@ def fabm_get_history_kernel(handle) -> int:
     return load().fabm_get_history_kernel(handle)
 
 
+def fabm_last_history_kernel(handle) -> int:
+    """FABM_HIST_* that the last solve ran (-1 before the first)."""
+    return load().fabm_last_history_kernel(handle)
+
+
 def fabm_set_recurrence_layout(handle, layout):
     """Recurrence layout of the tensor-history path: "auto", "columns" or "targets"."""
     k = RECURRENCE[layout] if isinstance(layout, str) else int(layout)
@@ -368,6 +374,12 @@ class Solver:
     @property
     def last_launch_count(self) -> int:
         return fabm_last_launch_count(self.handle)
+
+    @property
+    def last_history_kernel(self) -> str:
+        """Name (as in HIST) of the history kernel the last solve ran, or None."""
+        k = fabm_last_history_kernel(self.handle)
+        return next((n for n, v in HIST.items() if v == k and n != "auto"), None)
 
     def autotune(self, y0, traj_params=None, n_probe=4096):
         """Time truncated solves of this batch for each candidate setting, keep

@@ -118,6 +118,7 @@ struct fabm_solver {
     double params[kMaxParams] = {};
     int precision = FABM_FP64;
     int hist_kernel = FABM_HIST_AUTO;  // requested
+    int last_hk = -1;                  // run by the last solve (fabm_last_history_kernel)
     int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     long long wait_cycles = 0;         // tensor kernel's wait limit (0: its default)
@@ -603,6 +604,7 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
     const int64_t N = s->N;
     const int hk = resolve_hist_kernel(s, cols);
     const int L = hk == FABM_HIST_TENSOR ? kSplitSeg : kRecurL;
+    s->last_hk = hk;
     s->L = L;
     s->launches = 0;
 
@@ -674,14 +676,17 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         s->wide = s->G_max >= 2 && (s->hist_kernel == FABM_HIST_TENSOR_WIDE ||
                                     s->hist_kernel == FABM_HIST_AUTO);
         far_chunks = std::max(1, (148 - reserve) / (2 * n_ct));
+        if (s->wide) s->last_hk = FABM_HIST_TENSOR_WIDE;
         // a near launch (on the serial chain) takes whole SMs: as many CTAs per
         // column tile as the SMs the far kernel leaves free allow, so that it
         // does not wait for far CTAs to retire (one CTA sums its segments in turn)
         const int far_free = 152 - 2 * n_ct * far_chunks;
         s->near_chunks = std::clamp(far_free / n_ct, 1, 3);
-        // column layout: CTAs sized to fill the SMs the tensor CTAs leave free
+        // column layout: CTAs sized to fill the SMs the tensor CTAs leave free,
+        // at most 4 warps each, so that a CTA fits beside others on an SM that
+        // is partly free (Duffing 4096 x 2^16: 4 warps 323 ms, 11 warps 340)
         const int free_sms = std::max(4, 152 - n_ct * split_chunks);
-        s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 12) : 0;
+        s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 4) : 0;
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
         // far chunks and one chunk for the newest segment; with the wide far
@@ -1185,6 +1190,8 @@ fabm_status fabm_set_history_kernel(fabm_solver *s, int kernel)
 }
 
 int fabm_get_history_kernel(const fabm_solver *s) { return s ? s->hist_kernel : -1; }
+
+int fabm_last_history_kernel(const fabm_solver *s) { return s ? s->last_hk : -1; }
 
 fabm_status fabm_set_recurrence_layout(fabm_solver *s, int layout)
 {

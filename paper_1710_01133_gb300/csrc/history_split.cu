@@ -478,16 +478,6 @@ __global__ void __launch_bounds__(kThreads, 1) hist_split_kernel(const SplitArgs
     if (!ok) atomicOr(a.err, 1u);
 }
 
-// (s, c) += v in double with compensation: TwoSum's rounding error of every
-// addition collects in c (Neumaier's compensated summation).
-__device__ __forceinline__ void comp_add_d(double &s, double &c, double v)
-{
-    const double t = s + v;
-    const double bp = t - s;
-    c += (s - (t - bp)) + (v - bp);
-    s = t;
-}
-
 // float-float (hi, lo) += (x, y): two-sum of the high parts, low parts folded
 // in, renormalized.
 __device__ __forceinline__ void ff_add(float &hi, float &lo, float x, float y)
@@ -501,14 +491,13 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float x, float y)
 }
 
 // a3: G[kind][t][col] = sum over chunks of the float-float partials, R lanes
-// per output, each summing chunks r, r+R, ... in ascending order, then a fixed
-// xor tree.  Out = double (the CUDA-core paths): each partial hi + lo exactly
-// in double, accumulated in double with compensation, rounded once.  Out =
-// float2 (tensor path, where the combine runs on the few SMs the tensor CTAs
-// leave free and FP64 issues at 1/64 of the fp32 rate): accumulated in
-// compensated float-float (~48 bits, 2^24 finer than the fp32 partials) and
-// kept as the pair.  Every thread runs the same number of rounds, so the
-// shuffles always see full warps.
+// per output, each summing chunks r, r+R, ... in ascending order (four loads
+// in flight), then a fixed xor tree, in compensated float-float (~48 bits,
+// 2^24 finer than the fp32 partials).  Out = float2 (tensor path) keeps the
+// pair; Out = double (compensated-fp32 history) rounds hi + lo once.  The
+// combine sits on the serial chain of every block and FP64 issues at 1/64 of
+// the fp32 rate on this part, so the accumulation stays in fp32 pairs.  Every
+// thread runs the same number of rounds, so the shuffles always see full warps.
 template <int R, class Out>
 __global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chunks, int64_t n_out,
                                      Out *__restrict__ G)
@@ -518,35 +507,35 @@ __global__ void combine_split_kernel(const float2 *__restrict__ part, int n_chun
     const int64_t groups = (int64_t)gridDim.x * blockDim.x / R;
     for (int64_t base = 0; base < n_out; base += groups) {
         const int64_t o = base + gtid / R;
-        if constexpr (std::is_same_v<Out, double>) {
-            double s = 0.0, c = 0.0;
-            if (o < n_out)
-                for (int ch = r; ch < n_chunks; ch += R) {
-                    const float2 v = part[(int64_t)ch * n_out + o];
-                    comp_add_d(s, c, (double)v.x + (double)v.y);
-                }
-#pragma unroll
-            for (int off = R / 2; off > 0; off >>= 1) {
-                const double os = __shfl_xor_sync(0xffffffffu, s, off);
-                const double oc = __shfl_xor_sync(0xffffffffu, c, off);
-                comp_add_d(s, c, os);
-                c += oc;
+        float hi = 0.f, lo = 0.f;
+        if (o < n_out) {
+            int ch = r;
+            for (; ch + 3 * R < n_chunks; ch += 4 * R) {
+                const float2 v0 = part[(int64_t)ch * n_out + o];
+                const float2 v1 = part[(int64_t)(ch + R) * n_out + o];
+                const float2 v2 = part[(int64_t)(ch + 2 * R) * n_out + o];
+                const float2 v3 = part[(int64_t)(ch + 3 * R) * n_out + o];
+                ff_add(hi, lo, v0.x, v0.y);
+                ff_add(hi, lo, v1.x, v1.y);
+                ff_add(hi, lo, v2.x, v2.y);
+                ff_add(hi, lo, v3.x, v3.y);
             }
-            if (r == 0 && o < n_out) G[o] = s + c;
-        } else {
-            float hi = 0.f, lo = 0.f;
-            if (o < n_out)
-                for (int ch = r; ch < n_chunks; ch += R) {
-                    const float2 v = part[(int64_t)ch * n_out + o];
-                    ff_add(hi, lo, v.x, v.y);
-                }
-#pragma unroll
-            for (int off = R / 2; off > 0; off >>= 1) {
-                const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-                const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-                ff_add(hi, lo, ohi, olo);
+            for (; ch < n_chunks; ch += R) {
+                const float2 v = part[(int64_t)ch * n_out + o];
+                ff_add(hi, lo, v.x, v.y);
             }
-            if (r == 0 && o < n_out) G[o] = make_float2(hi, lo);  // normalised by ff_add
+        }
+#pragma unroll
+        for (int off = R / 2; off > 0; off >>= 1) {
+            const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+            ff_add(hi, lo, ohi, olo);
+        }
+        if (r == 0 && o < n_out) {
+            if constexpr (std::is_same_v<Out, double>)
+                G[o] = (double)hi + (double)lo;
+            else
+                G[o] = make_float2(hi, lo);  // normalised by ff_add
         }
     }
 }

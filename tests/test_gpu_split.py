@@ -159,15 +159,22 @@ def test_recurrence_layout_rejects_unknown(gpu_lib):
 def test_auto_history_kernel_choice(gpu_lib):
     """Split precision picks tensor cores for wide batches (64+ columns) and the
     compensated fp32 kernel for narrow ones; the block length follows."""
-    w = duffing_sweep(B=40, N=300)
+    w = duffing_sweep(B=40, N=256)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        assert s.last_history_kernel is None
         s.solve_batch(w.y0[:2], traj_params=w.traj_params[:2])
-        assert s.block == 32
+        assert s.block == 32 and s.last_history_kernel == "fp32c"
         s.solve_batch(w.y0, traj_params=w.traj_params)
-        assert s.block == 64
+        assert s.block == 64 and s.last_history_kernel == "tensor"  # N <= 256: no far group
+    w = duffing_sweep(B=40, N=257)
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+        s.solve_batch(w.y0, traj_params=w.traj_params)
+        assert s.last_history_kernel == "tensor-wide"
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
         with pytest.raises(gpu_lib.FabmError):
             gpu_lib.fabm_set_history_kernel(s.handle, "tensor")
+        s.solve_batch(w.y0[:1], traj_params=w.traj_params[:1])
+        assert s.last_history_kernel == "fp64"
 
 
 def test_autotune_picks_a_candidate_and_stays_correct(gpu_lib, parity):
