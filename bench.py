@@ -662,7 +662,8 @@ def main():
             "clocks": clocks,
             "autotune": None if tuned is None else {
                 "n_probe": args.autotune,
-                "candidates_ms_kernel_setting": [[round(m, 3), k, c] for m, k, c in tuned]},
+                "candidates_predicted_ms_kernel_setting": [[round(m, 3), k, c] for m, k, c in tuned],
+                "recurrence_warps": fabm.fabm_get_recurrence_warps(solver.handle)},
             "output_finite": finite,
         }
         if comparator is not None:

@@ -35,7 +35,8 @@ _EXPORTS = ("fabm_create", "fabm_solve", "fabm_solve_batch", "fabm_destroy",
             "fabm_create_multi", "fabm_server_finished", "fabm_kernel_busy",
             "fabm_set_recurrence_layout", "fabm_get_recurrence_layout", "fabm_weights_x2",
             "fabm_server_wait", "fabm_set_wait_limit", "fabm_inject_alloc_failures",
-            "fabm_copy_weights_lo", "fabm_server_submit_ic", "fabm_last_history_kernel")
+            "fabm_copy_weights_lo", "fabm_server_submit_ic", "fabm_last_history_kernel",
+            "fabm_set_recurrence_warps", "fabm_get_recurrence_warps")
 FABM_REQ_WAITING, FABM_REQ_RUNNING, FABM_REQ_DONE, FABM_REQ_FAILED = range(4)
 
 
@@ -114,6 +115,8 @@ def load(build_if_missing: bool = True):
     lib.fabm_set_history_kernel.argtypes = [vp, i]
     lib.fabm_get_history_kernel.argtypes = [vp]
     lib.fabm_last_history_kernel.argtypes = [vp]
+    lib.fabm_set_recurrence_warps.argtypes = [vp, i]
+    lib.fabm_get_recurrence_warps.argtypes = [vp]
     lib.fabm_set_recurrence_layout.argtypes = [vp, i]
     lib.fabm_weights_x2.argtypes = [d, i64] + [P(d)] * 6
     lib.fabm_weights_x2.restype = i
@@ -134,7 +137,8 @@ def load(build_if_missing: bool = True):
               "fabm_get_block", "fabm_copy_weights", "fabm_set_timing", "fabm_kernel_stats",
               "fabm_set_graphs", "fabm_solve_noalloc", "fabm_set_history_kernel",
               "fabm_get_history_kernel", "fabm_set_recurrence_layout",
-              "fabm_get_recurrence_layout", "fabm_last_history_kernel"):
+              "fabm_get_recurrence_layout", "fabm_last_history_kernel",
+              "fabm_set_recurrence_warps", "fabm_get_recurrence_warps"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib
@@ -273,6 +277,15 @@ def fabm_set_history_kernel(handle, kernel):
 
 def fabm_get_history_kernel(handle) -> int:
     return load().fabm_get_history_kernel(handle)
+
+
+def fabm_set_recurrence_warps(handle, warps: int):
+    """Warps per CTA of the lane-per-column recurrence (0: automatic, 1..12)."""
+    _check(load().fabm_set_recurrence_warps(handle, int(warps)))
+
+
+def fabm_get_recurrence_warps(handle) -> int:
+    return load().fabm_get_recurrence_warps(handle)
 
 
 def fabm_last_history_kernel(handle) -> int:

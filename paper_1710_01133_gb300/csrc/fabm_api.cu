@@ -127,6 +127,7 @@ struct fabm_solver {
     int persist_ctas = 0;              // FP64: CTAs of the persistent kernel resident at once
     int L = kRecurL;                   // block length of the last solve
     int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
+    int rec_warps = 0;                 // column recurrence: warps per CTA (0: automatic)
     int cols_warps = 1;                // tensor path: warps per CTA of the column recurrence,
                                        // or 0 for the lane-per-target layout
     StepConsts k{};
@@ -155,8 +156,9 @@ struct fabm_solver {
     DevBuf<int> Fe2;           // wide far history: exponents per group
     DevBuf<float2> fpart;      // wide far history: partials of two target groups
     DevBuf<float2> fsum;       // wide far history: their chunk sums, [C % 2][2][128][cols]
-    DevBuf<double> ppart;      // persistent FP64 solve: partial-sum slots
-    DevBuf<int> pdone, prdone; // persistent FP64 solve: chunks done per block, blocks done per trajectory
+    DevBuf<double> ppart, pspart;  // persistent FP64 solve: chunk and super-group partial slots
+    DevBuf<int> psg, pdone, prdone; // persistent FP64 solve: chunks done per super-group,
+                                    // super-groups done per block, blocks done per trajectory
     DevBuf<float2> auxb;       // tensor path: forcing tables of kAuxRing blocks
     DevBuf<unsigned int> err;  // split: timeout flag
     DevBuf<int64_t> nEach;
@@ -686,7 +688,9 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         // at most 4 warps each, so that a CTA fits beside others on an SM that
         // is partly free (Duffing 4096 x 2^16: 4 warps 323 ms, 11 warps 340)
         const int free_sms = std::max(4, 152 - n_ct * split_chunks);
-        s->cols_warps = columns ? std::clamp((cwarps + free_sms - 1) / free_sms, 1, 4) : 0;
+        s->cols_warps = !columns        ? 0
+                        : s->rec_warps > 0 ? s->rec_warps
+                                           : std::clamp((cwarps + free_sms - 1) / free_sms, 1, 4);
         FABM_CUDA_TRY(s->Fs.ensure((size_t)nblk * n_ct * 3 * 128 * 64));
         FABM_CUDA_TRY(s->Fe.ensure((size_t)nblk * n_ct * 128));
         // far chunks and one chunk for the newest segment; with the wide far
@@ -779,11 +783,15 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         const int grid = s->persist_ctas;
         const int pchunks = persist_workers(grid, (int)B);
         const int ncg = (int)((cols + 3) / 4);
+        const size_t n_sg = (size_t)nblk * ncg * persist_max_sg(pchunks);
         FABM_CUDA_TRY(s->ppart.ensure(persist_part_elems(pchunks, (int)cols)));
+        FABM_CUDA_TRY(s->pspart.ensure(persist_spart_elems(pchunks, (int)cols)));
+        FABM_CUDA_TRY(s->psg.ensure(n_sg));
         FABM_CUDA_TRY(s->pdone.ensure((size_t)nblk * ncg));
         FABM_CUDA_TRY(s->prdone.ensure((size_t)B));
         FABM_CUDA_TRY(s->err.ensure(1));
         s->recs.clear();
+        FABM_CUDA_TRY(cudaMemsetAsync(s->psg.p, 0, sizeof(int) * n_sg, s->sR));
         FABM_CUDA_TRY(cudaMemsetAsync(s->pdone.p, 0, sizeof(int) * nblk * ncg, s->sR));
         FABM_CUDA_TRY(cudaMemsetAsync(s->prdone.p, 0, sizeof(int) * B, s->sR));
         FABM_CUDA_TRY(cudaMemsetAsync(s->err.p, 0, sizeof(unsigned int), s->sR));
@@ -793,7 +801,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         const double flops = 2.0 * (double)Nmax * (double)Nmax * (double)cols;
         FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_HISTORY, s->sR, flops, [&] {
             return launch_persist_fp64(s->rhs, bt, w, s->k, nblk, grid, pchunks, s->ppart.p,
-                                       s->pdone.p, s->prdone.p, s->err.p, s->wait_cycles, s->sR);
+                                       s->pspart.p, s->psg.p, s->pdone.p, s->prdone.p, s->err.p,
+                                       s->wait_cycles, s->sR);
         }));
         FABM_CUDA_TRY(cudaStreamSynchronize(s->sR));
         FABM_CUDA_TRY(collect_timing(s, s->recs));
@@ -1207,6 +1216,19 @@ fabm_status fabm_set_recurrence_layout(fabm_solver *s, int layout)
 
 int fabm_get_recurrence_layout(const fabm_solver *s) { return s ? s->rec_layout : -1; }
 
+fabm_status fabm_set_recurrence_warps(fabm_solver *s, int warps)
+{
+    g_last_error.clear();
+    if (!s) return fail(FABM_EINVAL, "solver is NULL");
+    if (warps < 0 || warps > 12) return fail(FABM_EINVAL, "recurrence warps %d: 0 (automatic) or 1..12", warps);
+    std::unique_lock<std::mutex> lk(s->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(FABM_EBUSY, "solver in use by another thread");
+    s->rec_warps = warps;
+    return FABM_OK;
+}
+
+int fabm_get_recurrence_warps(const fabm_solver *s) { return s ? s->rec_warps : -1; }
+
 int fabm_get_block(const fabm_solver *s) { return s ? s->L : 0; }
 
 fabm_status fabm_copy_weights(fabm_solver *s, int64_t n, double *B, double *A, double *D)
@@ -1249,7 +1271,10 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     if (B < 1 || !y0) return fail(FABM_EINVAL, "autotune needs B >= 1 and y0");
     if (n_probe < 1) return fail(FABM_EINVAL, "n_probe %lld < 1", (long long)n_probe);
-    const int64_t np = std::min<int64_t>(n_probe, s->N);
+    // two probe lengths: a solve takes about alpha n (the per-step chain) +
+    // beta n^2 (the history), so two truncated solves predict the full one
+    const int64_t n1 = std::min<int64_t>(n_probe, s->N);
+    const int64_t n2 = std::min<int64_t>(2 * n_probe, s->N);
     struct Cand {
         int kernel, ctas;
     };
@@ -1277,14 +1302,40 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         cudaError_t e = cudaMalloc(&dout, sizeof(double) * (size_t)B * (s->N + 1) * s->dim);
         if (e != cudaSuccess) return fail(FABM_ENOMEM, "autotune output: %s", cudaGetErrorString(e));
     }
-    std::vector<int64_t> ne((size_t)B, np);
+    std::vector<int64_t> ne((size_t)B, n1);
     const int keep_kernel = s->hist_kernel, keep_ctas = s->chunk_ctas, keep_res = s->sm_reserve;
+    const int keep_L = s->L;
     const bool keep_timing = s->timing;
     s->timing = false;
     double best = 1e300;
     Cand pick{keep_kernel, keep_ctas};
     int nr = 0;
     fabm_status st = FABM_OK;
+    // milliseconds of a solve of n steps (second of two runs: the first
+    // records the graph), and the prediction for all N steps
+    auto time_n = [&](int64_t n) {
+        std::fill(ne.begin(), ne.end(), n);
+        double ms = 1e300;
+        for (int rep = 0; rep < 2 && st == FABM_OK; ++rep) {
+            const auto t0 = std::chrono::steady_clock::now();
+            st = run_batch(s, B, y0, nullptr, traj_params, ne.data(), dout, 1);
+            const auto t1 = std::chrono::steady_clock::now();
+            ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        }
+        return ms;
+    };
+    auto predict = [&]() {
+        const double t1 = time_n(n1);
+        if (st != FABM_OK || n2 == n1) return t1;
+        const double t2 = time_n(n2);
+        if (st != FABM_OK) return t2;
+        const double x1 = (double)n1, x2 = (double)n2, N = (double)s->N;
+        double beta = (t2 * x1 - t1 * x2) / (x1 * x2 * (x2 - x1));
+        double alpha = (t1 - beta * x1 * x1) / x1;
+        if (beta < 0.0) beta = 0.0, alpha = t2 / x2;
+        if (alpha < 0.0) alpha = 0.0, beta = t2 / (x2 * x2);
+        return alpha * N + beta * N * N;
+    };
     for (const Cand &cd : cands) {
         s->hist_kernel = cd.kernel;
         if (cd.kernel == FABM_HIST_TENSOR || cd.kernel == FABM_HIST_TENSOR_WIDE)
@@ -1293,13 +1344,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
             s->chunk_ctas = keep_ctas, s->sm_reserve = keep_res;
         else
             s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
-        double ms = 1e300;
-        for (int rep = 0; rep < 2 && st == FABM_OK; ++rep) {  // first run records the graph
-            const auto t0 = std::chrono::steady_clock::now();
-            st = run_batch(s, B, y0, nullptr, traj_params, ne.data(), dout, 1);
-            const auto t1 = std::chrono::steady_clock::now();
-            ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-        }
+        const double ms = predict();
         if (st != FABM_OK) break;
         if (nr < max_report) {
             if (ms_report) ms_report[nr] = ms;
@@ -1309,19 +1354,40 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         ++nr;
         if (ms < best) best = ms, pick = cd;
     }
+    auto apply = [&](const Cand &cd) {
+        s->hist_kernel = cd.kernel;
+        const bool tensor = cd.kernel == FABM_HIST_TENSOR || cd.kernel == FABM_HIST_TENSOR_WIDE;
+        if (tensor || cd.kernel == FABM_HIST_FP64_PERSIST)
+            s->sm_reserve = tensor ? cd.ctas : keep_res, s->chunk_ctas = keep_ctas;
+        else
+            s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
+        s->L = tensor ? kSplitSeg : kRecurL;
+    };
+    // second stage, tensor path with the lane-per-column recurrence: the warps
+    // per recurrence CTA (how the recurrence shares the SMs the tensor CTAs
+    // leave free), the caller's setting against 1, 2, 4 and 8
+    if (st == FABM_OK && (pick.kernel == FABM_HIST_TENSOR || pick.kernel == FABM_HIST_TENSOR_WIDE)) {
+        apply(pick);
+        const int keep_warps = s->rec_warps;
+        int best_w = keep_warps;
+        for (int w : {1, 2, 4, 8}) {
+            if (w == keep_warps) continue;
+            s->rec_warps = w;
+            const double ms = predict();
+            if (st != FABM_OK) break;
+            if (s->cols_warps == 0) break;  // lane-per-target layout: the width does not apply
+            if (ms < best) best = ms, best_w = w;
+        }
+        s->rec_warps = st == FABM_OK ? best_w : keep_warps;
+    }
     cudaFree(dout);
     s->timing = keep_timing;
     if (st != FABM_OK) {
         s->hist_kernel = keep_kernel, s->chunk_ctas = keep_ctas, s->sm_reserve = keep_res;
+        s->L = keep_L;
         return st;
     }
-    s->hist_kernel = pick.kernel;
-    const bool tensor = pick.kernel == FABM_HIST_TENSOR || pick.kernel == FABM_HIST_TENSOR_WIDE;
-    if (tensor || pick.kernel == FABM_HIST_FP64_PERSIST)
-        s->sm_reserve = tensor ? pick.ctas : keep_res, s->chunk_ctas = keep_ctas;
-    else
-        s->chunk_ctas = pick.ctas, s->sm_reserve = keep_res;
-    s->L = tensor ? kSplitSeg : kRecurL;
+    apply(pick);
     if (n_report) *n_report = nr;
     return FABM_OK;
 }

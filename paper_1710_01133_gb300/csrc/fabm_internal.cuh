@@ -220,16 +220,21 @@ int persist_max_ctas(int rhs, int dim);
 // History workers of a persistent launch of `grid` CTAs for B trajectories
 // (the most chunks per block it uses).
 int persist_workers(int grid, int B);
-// doubles of the persistent kernel's partial-sum slots.
+// doubles of the persistent kernel's chunk-partial slots and super-group
+// (16 chunks) partial slots; super-groups per (block, column group) at most.
 size_t persist_part_elems(int max_chunks, int cols);
+size_t persist_spart_elems(int max_chunks, int cols);
+int persist_max_sg(int max_chunks);
 // The whole FP64 solve of a batch (after launch_init) as one cooperative
 // launch of `grid` CTAs: bt.B recurrence CTAs and grid - bt.B history CTAs
-// (chunks per block at most max_chunks, e.g. persist_workers(grid, B)).  done: nblk x
-// ceil(cols/4) ints, r_done: B ints, both zero; err: set on a wait timeout.
+// (chunks per block at most max_chunks, e.g. persist_workers(grid, B)).
+// sg_cnt: nblk x ceil(cols/4) x persist_max_sg(max_chunks) ints, done: nblk x
+// ceil(cols/4) ints, r_done: B ints, all zero; err: set on a wait timeout.
 cudaError_t launch_persist_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
                                 const StepConsts &k, int64_t nblk, int grid, int max_chunks,
-                                double *part, int *done, int *r_done, unsigned *err,
-                                long long wait_cycles, cudaStream_t st);
+                                double *part, double *spart, int *sg_cnt, int *done,
+                                int *r_done, unsigned *err, long long wait_cycles,
+                                cudaStream_t st);
 
 // ---- FP64X2 precision (double-double history) ----
 

@@ -26,10 +26,17 @@
 //                      (hist_fp64_chunk, f read around L1 since other SMs
 //                      write it during the launch; several chunks' warps in
 //                      flight hide the FP64 pipe's latency), adds the four
-//                      sums in a fixed order and counts the chunk done.
-// The recurrence of block c waits for all chunks of its block.  Lag 2: block
-// c's far history starts once block c-3 is finished, so the recurrences of
-// blocks c-2 and c-1 hide it.
+//                      sums in a fixed order and counts the chunk done in
+//                      its super-group (16 consecutive chunks); the worker
+//                      that finishes a super-group's last chunk adds the
+//                      group's chunk partials in chunk order, compensated,
+//                      and counts the super-group done.
+// The recurrence of block c waits for every super-group of its block and adds
+// their ~10 partials, not the ~150 chunk partials: on GB300 a warp FP64
+// instruction costs ~16 cycles of an SM's FP64 pipe, and the chunk-level sum
+// on the recurrence's one SM had put ~35 us on the serial chain of every
+// block.  Lag 2: block c's far history starts once block c-3 is finished, so
+// the recurrences of blocks c-2 and c-1 hide it.
 //
 // Every wait polls a flag for at most the launch's wait limit; on timeout the
 // CTA sets the error word and leaves its loop, and the CTAs waiting on it
@@ -43,6 +50,7 @@ namespace {
 
 constexpr int kPL = kRecurL;                       // targets per block (32)
 constexpr int kLag = 2;                            // far history of block c: k < (c - kLag) L
+constexpr int kSG = 16;                            // chunks per super-group
 constexpr int kSlots = kLag + 2;                   // blocks whose partials are in flight
 constexpr int kSubThreads = kWarp * hist::kColsPerCta;  // 128: the stepping warps, a point group
 constexpr int kSubs = 4;                                // point groups per history CTA
@@ -64,8 +72,11 @@ struct PersistArgs {
     int n_hist;       // history CTAs
     int ncg;          // column groups of hist::kColsPerCta
     int max_chunks;   // chunks per (block, column group) at most
-    double *part;     // [kSlots][max_chunks][2][32][cols]
-    int *done;        // [nblk][ncg] chunks finished, zero at launch
+    int max_sg;       // super-groups per (block, column group) at most
+    double *part;     // [kSlots][max_chunks][2][32][cols] chunk partials
+    double *spart;    // [kSlots][max_sg][2][32][cols] super-group partials
+    int *sg_cnt;      // [nblk][ncg][max_sg] chunks finished, zero at launch
+    int *done;        // [nblk][ncg] super-groups finished, zero at launch
     int *r_done;      // [B] blocks finished per trajectory, zero at launch
     unsigned *err;
     long long wait;   // clock cycles a wait may take
@@ -177,15 +188,16 @@ __device__ void recurrence_cta(const PersistArgs &a, int b, double *smem, int *f
             int nch;
             int64_t kc;
             plan(a, c, &nch, &kc);
+            const int nsg = (nch + kSG - 1) / kSG;
             if (threadIdx.x == 0) {
                 bool ok = true;
                 for (int g = cg_lo; g <= cg_hi && ok; ++g)
-                    ok = wait_geq(a.done + c * a.ncg + g, nch, a.wait);
+                    ok = wait_geq(a.done + c * a.ncg + g, nsg, a.wait);
                 *flag = ok;
             }
             all_sync();
             if (!*flag) break;
-            const double *slot = a.part + (size_t)(c % kSlots) * a.max_chunks * 2 * kPL * bt.cols;
+            const double *slot = a.spart + (size_t)(c % kSlots) * a.max_sg * 2 * kPL * bt.cols;
             const int v = threadIdx.x / R, r = threadIdx.x % R;
             double s = 0.0, cmp = 0.0;
             if (v < kVals) {
@@ -193,7 +205,7 @@ __device__ void recurrence_cta(const PersistArgs &a, int b, double *smem, int *f
                 const double *src = slot + ((int64_t)kind * kPL + t) * bt.cols + (int64_t)b * D + q;
                 const int64_t cs = 2LL * kPL * bt.cols;  // chunk stride
                 int ch = r;
-                for (; ch + 7 * R < nch; ch += 8 * R) {
+                for (; ch + 7 * R < nsg; ch += 8 * R) {
                     double x[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) x[u] = __ldcg(src + (int64_t)(ch + u * R) * cs);
@@ -205,7 +217,7 @@ __device__ void recurrence_cta(const PersistArgs &a, int b, double *smem, int *f
                         s = t2;
                     }
                 }
-                for (; ch < nch; ch += R) {
+                for (; ch < nsg; ch += R) {
                     const double xv = __ldcg(src + (int64_t)ch * cs);
                     const double t2 = s + xv;
                     const double bp = t2 - s;
@@ -309,7 +321,7 @@ __device__ void recurrence_cta(const PersistArgs &a, int b, double *smem, int *f
 // split over kSubs point groups of four warps (group `sub`, thread tid in it,
 // tiles at `tiles`); scr: kSubs x 256 doubles for the groups' sums.
 __device__ void history_cta(const PersistArgs &a, int w, int sub, int tid, double *tiles,
-                            double *scr, int *flag)
+                            double *scr, int *flag, int *last)
 {
     using namespace hist::f64;
     const DevBatch &bt = a.bt;
@@ -373,9 +385,41 @@ __device__ void history_cta(const PersistArgs &a, int w, int sub, int tid, doubl
                 slot[((int64_t)ch * 2 * kPL + kt) * bt.cols + g * hist::kColsPerCta + wc] = s + cmp;
             }
             all_sync();
+            // count the chunk in its super-group; the worker that completes
+            // the super-group adds its chunk partials (in chunk order,
+            // compensated) into the super-group's partial
+            const int sg = ch / kSG, sg_lo = sg * kSG;
+            const int sg_n = nch - sg_lo < kSG ? nch - sg_lo : kSG;
             if (threadIdx.x == 0) {
                 __threadfence();
-                atomicAdd(a.done + c * a.ncg + g, 1);
+                const int before = atomicAdd(a.sg_cnt + (c * a.ncg + g) * a.max_sg + sg, 1);
+                *last = before == sg_n - 1;
+                if (*last) __threadfence();
+            }
+            all_sync();
+            if (*last) {
+                double *sslot = a.spart + (size_t)(c % kSlots) * a.max_sg * 2 * kPL * bt.cols;
+                const int64_t cs = 2LL * kPL * bt.cols;  // chunk stride
+                for (int o = threadIdx.x; o < 2 * kPL * hist::kColsPerCta; o += kThreads) {
+                    const int wc = o % hist::kColsPerCta;
+                    if (wc >= ncol) continue;
+                    const int kt = o / hist::kColsPerCta;
+                    const int64_t off = (int64_t)kt * bt.cols + g * hist::kColsPerCta + wc;
+                    double s = 0.0, cmp = 0.0;
+                    for (int u = 0; u < sg_n; ++u) {
+                        const double xv = __ldcg(slot + (int64_t)(sg_lo + u) * cs + off);
+                        const double t2 = s + xv;
+                        const double bp = t2 - s;
+                        cmp += (s - (t2 - bp)) + (xv - bp);
+                        s = t2;
+                    }
+                    sslot[(int64_t)sg * cs + off] = s + cmp;
+                }
+                all_sync();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    atomicAdd(a.done + c * a.ncg + g, 1);
+                }
             }
         }
     }
@@ -385,8 +429,8 @@ template <class Rhs, int D>
 __global__ void __launch_bounds__(kThreads, 1) persist_fp64_kernel(const PersistArgs a)
 {
     extern __shared__ __align__(16) double psmem[];
-    __shared__ int flag;
-    if (threadIdx.x == 0) flag = 1;
+    __shared__ int flag, last;
+    if (threadIdx.x == 0) flag = 1, last = 0;
     __syncthreads();
     if ((int)blockIdx.x < a.n_rec) {
         recurrence_cta<Rhs, D>(a, blockIdx.x, psmem, &flag);
@@ -394,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_fp64_kernel(const Persist
     }
     const int sub = threadIdx.x / kSubThreads, tid = threadIdx.x % kSubThreads;
     history_cta(a, (int)blockIdx.x - a.n_rec, sub, tid, psmem + (size_t)sub * kTileDoubles,
-                psmem + (size_t)kSubs * kTileDoubles, &flag);
+                psmem + (size_t)kSubs * kTileDoubles, &flag, &last);
 }
 
 template <int D>
@@ -432,10 +476,18 @@ size_t persist_part_elems(int max_chunks, int cols)
     return (size_t)kSlots * max_chunks * 2 * kPL * cols;
 }
 
+int persist_max_sg(int max_chunks) { return (max_chunks + kSG - 1) / kSG; }
+
+size_t persist_spart_elems(int max_chunks, int cols)
+{
+    return (size_t)kSlots * persist_max_sg(max_chunks) * 2 * kPL * cols;
+}
+
 cudaError_t launch_persist_fp64(int rhs, const DevBatch &bt, const DevWeights &w,
                                 const StepConsts &k, int64_t nblk, int grid, int max_chunks,
-                                double *part, int *done, int *r_done, unsigned *err,
-                                long long wait_cycles, cudaStream_t st)
+                                double *part, double *spart, int *sg_cnt, int *done,
+                                int *r_done, unsigned *err, long long wait_cycles,
+                                cudaStream_t st)
 {
     if (w.stride != 0 || grid <= bt.B || max_chunks < 1) return cudaErrorInvalidValue;
     PersistArgs a{};
@@ -447,7 +499,10 @@ cudaError_t launch_persist_fp64(int rhs, const DevBatch &bt, const DevWeights &w
     a.n_hist = grid - bt.B;
     a.ncg = (bt.cols + hist::kColsPerCta - 1) / hist::kColsPerCta;
     a.max_chunks = max_chunks;
+    a.max_sg = persist_max_sg(max_chunks);
     a.part = part;
+    a.spart = spart;
+    a.sg_cnt = sg_cnt;
     a.done = done;
     a.r_done = r_done;
     a.err = err;

@@ -186,10 +186,39 @@ def test_autotune_picks_a_candidate_and_stays_correct(gpu_lib, parity):
                                           gpu_lib.FABM_HIST_FP32C}
         best = min(rep)[1]
         assert gpu_lib.fabm_get_history_kernel(s.handle) == best
+        assert gpu_lib.fabm_get_recurrence_warps(s.handle) in (0, 1, 2, 4, 8)
         got = s.solve_batch(w.y0[:4], traj_params=w.traj_params[:4])
     ref = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[:4], params=w.params,
                              traj_params=w.traj_params[:4])
     parity(rel_err(got, ref), TOL_SPLIT, "")
+
+
+def test_recurrence_width_leaves_the_results_bit_for_bit(gpu_lib, parity):
+    """Warps per CTA of the column recurrence, automatic or set (a partial last
+    CTA included), change the launch only; after the autotuner (which may also
+    move the SM reserve, hence the far chunking) the solve still meets the
+    oracle."""
+    w = duffing_sweep(B=200, N=700)  # 400 columns: 13 warps, the last one partial
+    with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split",
+                        history="tensor-wide", recurrence="columns") as s:
+        assert gpu_lib.fabm_get_recurrence_warps(s.handle) == 0
+        ref = s.solve_batch(w.y0, traj_params=w.traj_params)
+        for wp in (1, 3, 12):
+            gpu_lib.fabm_set_recurrence_warps(s.handle, wp)
+            assert gpu_lib.fabm_get_recurrence_warps(s.handle) == wp
+            assert np.array_equal(s.solve_batch(w.y0, traj_params=w.traj_params), ref)
+        for bad in (-1, 13):
+            with pytest.raises(gpu_lib.FabmError) as e:
+                gpu_lib.fabm_set_recurrence_warps(s.handle, bad)
+            assert e.value.status == gpu_lib.FABM_EINVAL
+        gpu_lib.fabm_set_recurrence_warps(s.handle, 0)
+        s.autotune(w.y0, traj_params=w.traj_params, n_probe=700)
+        assert gpu_lib.fabm_get_recurrence_warps(s.handle) in (0, 1, 2, 4, 8)
+        got = s.solve_batch(w.y0, traj_params=w.traj_params)
+    idx = np.array([0, 101, 199])
+    orc = oracle.solve_batch(w.rhs, w.alpha, w.h, w.N, w.y0[idx], params=w.params,
+                             traj_params=w.traj_params[idx])
+    parity(rel_err(got[idx], orc), TOL_SPLIT, "after-autotune")
 
 
 @pytest.mark.parametrize("N", [255, 256, 257, 383, 384, 385, 511, 512, 513, 767, 769, 1025])
