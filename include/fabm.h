@@ -213,16 +213,17 @@ int fabm_get_recurrence_layout(const fabm_solver *s);
  * solves: 0 chooses automatically (CTAs sized to fill the SMs the tensor CTAs
  * leave free, at most 4 warps each), 1..12 fixes it; the arithmetic and the
  * results do not depend on it.  FABM_EINVAL outside 0..12, FABM_EBUSY while
- * another thread uses the solver.  fabm_autotune may change it. */
+ * another thread uses the solver. */
 fabm_status fabm_set_recurrence_warps(fabm_solver *s, int warps);
 /* The width set on the solver (0: automatic), or -1 for NULL. */
 int fabm_get_recurrence_warps(const fabm_solver *s);
 
 /* Autotuner: for each candidate setting, times solves of the caller's batch
- * (B, y0, traj_params as for fabm_solve_batch) truncated to n_probe and
- * 2 n_probe steps, fits alpha n + beta n^2 (the per-step chain and the O(n^2)
- * history) to the two, and keeps the setting whose prediction for all N steps
- * is smallest (with n_probe >= N it times the full solve once per candidate).
+ * (B, y0, traj_params as for fabm_solve_batch) truncated to n_probe, 2 n_probe
+ * and 4 n_probe steps, fits c + alpha n + beta n^2 (fixed costs, the per-step
+ * chain, the O(n^2) history) to the three, and keeps the setting whose
+ * prediction for all N steps is smallest (a probe that reaches N is timed
+ * as it is).
  * Longer probes predict better where the history only dominates late in a
  * long solve.  Candidates: for FABM_FP64 and FABM_FP64X2
  * (with its double-double kernel), the split-k CTA target of the history kernel
@@ -233,11 +234,9 @@ int fabm_get_recurrence_warps(const fabm_solver *s);
  * at 304 and 608 CTAs.  Up to max_report
  * candidates are reported (predicted milliseconds per full solve, history
  * kernel FABM_HIST_*, CTA target or SM reserve); *n_report receives the number
- * tried.
- * When a tensor-core tiling wins and the solve runs the lane-per-column
- * recurrence, a second stage times the warps per recurrence CTA (the solver's
- * setting against 1, 2, 4 and 8; not reported) and keeps the fastest
- * (fabm_get_recurrence_warps).
+ * tried.  The warps per recurrence CTA (fabm_set_recurrence_warps) are not
+ * tuned: truncated probes run the recurrence-dominated early blocks and favour
+ * wider CTAs than a full solve does.
  * Any report pointer may be NULL.  Allocates a device output buffer of
  * B x (N+1) x dim doubles for the duration of the call. */
 fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const double *traj_params,

@@ -128,6 +128,8 @@ struct fabm_solver {
     int L = kRecurL;                   // block length of the last solve
     int rec_layout = FABM_REC_AUTO;    // recurrence layout on the tensor path (requested)
     int rec_warps = 0;                 // column recurrence: warps per CTA (0: automatic)
+    int64_t plan_N = 0;                // > 0: schedule choices (lag, layout) as for this many
+                                       // steps (the autotuner's truncated probes of a longer solve)
     int cols_warps = 1;                // tensor path: warps per CTA of the column recurrence,
                                        // or 0 for the lane-per-target layout
     StepConsts k{};
@@ -397,7 +399,7 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
     const int L = s->L;
     const int64_t cols = bt.cols;
     const bool split = hk == FABM_HIST_TENSOR;
-    const int lag = history_lag(hk, Nmax, cols);
+    const int lag = history_lag(hk, s->plan_N > 0 ? s->plan_N : Nmax, cols);
     const int n_gbuf = lag + 1;  // G of block c is read by R(c) until H(c + lag + 1) starts
     s->sample_now = true;
     FABM_CUDA_TRY(timed_launch(s, FABM_KERNEL_INIT, s->sR, 0.0,
@@ -661,7 +663,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         const int cwarps = recur_cols_warps(dim, B);
         const bool columns =
             s->rec_layout == FABM_REC_COLUMNS ||
-            (s->rec_layout == FABM_REC_AUTO && (cwarps >= 96 || (double)Nmax * cols >= 0x1p28));
+            (s->rec_layout == FABM_REC_AUTO &&
+             (cwarps >= 96 || (double)(s->plan_N > 0 ? s->plan_N : Nmax) * cols >= 0x1p28));
         // leave SMs for the recurrence that runs beside the tensor kernel (one
         // tensor CTA fills an SM's register file), only where the column tiles
         // do not need every SM: one SM per 8 column warps, or per 12
@@ -773,7 +776,8 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         (uintptr_t)s->nEach.p, (uintptr_t)s->status.p, (uintptr_t)s->err.p, (uintptr_t)s->auxb.p,
         (uintptr_t)s->out_stream, (uintptr_t)s->out_group, (uintptr_t)s->wait_cycles,
         (uintptr_t)s->wide, (uintptr_t)far_chunks, (uintptr_t)s->Fs2.p, (uintptr_t)s->Fe2.p,
-        (uintptr_t)s->fpart.p, (uintptr_t)s->fsum.p, (uintptr_t)s->near_chunks};
+        (uintptr_t)s->fpart.p, (uintptr_t)s->fsum.p, (uintptr_t)s->near_chunks,
+        (uintptr_t)s->plan_N};
     auto enqueue = [&]() -> fabm_status {
         return enqueue_solve(s, bt, w, nblk, Nmax, max_chunks, n_ct, split_chunks, hk, far_chunks);
     };
@@ -1271,10 +1275,10 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     if (!s) return fail(FABM_EINVAL, "solver is NULL");
     if (B < 1 || !y0) return fail(FABM_EINVAL, "autotune needs B >= 1 and y0");
     if (n_probe < 1) return fail(FABM_EINVAL, "n_probe %lld < 1", (long long)n_probe);
-    // two probe lengths: a solve takes about alpha n (the per-step chain) +
-    // beta n^2 (the history), so two truncated solves predict the full one
+    // probe lengths n_probe, 2 n_probe, 4 n_probe (at most N): a solve takes
+    // about c + alpha n + beta n^2 (fixed costs, the per-step chain, the
+    // history), so three truncated solves predict the full one
     const int64_t n1 = std::min<int64_t>(n_probe, s->N);
-    const int64_t n2 = std::min<int64_t>(2 * n_probe, s->N);
     struct Cand {
         int kernel, ctas;
     };
@@ -1307,6 +1311,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
     const int keep_L = s->L;
     const bool keep_timing = s->timing;
     s->timing = false;
+    s->plan_N = s->N;  // the probes take the full solve's lag and recurrence layout
     double best = 1e300;
     Cand pick{keep_kernel, keep_ctas};
     int nr = 0;
@@ -1325,16 +1330,21 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         return ms;
     };
     auto predict = [&]() {
-        const double t1 = time_n(n1);
-        if (st != FABM_OK || n2 == n1) return t1;
-        const double t2 = time_n(n2);
-        if (st != FABM_OK) return t2;
-        const double x1 = (double)n1, x2 = (double)n2, N = (double)s->N;
-        double beta = (t2 * x1 - t1 * x2) / (x1 * x2 * (x2 - x1));
-        double alpha = (t1 - beta * x1 * x1) / x1;
-        if (beta < 0.0) beta = 0.0, alpha = t2 / x2;
-        if (alpha < 0.0) alpha = 0.0, beta = t2 / (x2 * x2);
-        return alpha * N + beta * N * N;
+        double x[3], t[3];
+        for (int i = 0; i < 3; ++i) {
+            const int64_t n = std::min<int64_t>(n1 << i, s->N);
+            x[i] = (double)n;
+            t[i] = time_n(n);
+            if (st != FABM_OK || n == s->N) return t[i];  // the full solve was timed
+        }
+        // the quadratic through the three points (Newton's divided
+        // differences), evaluated at N; a negative n^2 coefficient (noise)
+        // falls back to the line through the two longer probes
+        const double N = (double)s->N;
+        const double d01 = (t[1] - t[0]) / (x[1] - x[0]), d12 = (t[2] - t[1]) / (x[2] - x[1]);
+        const double beta = (d12 - d01) / (x[2] - x[0]);
+        if (beta < 0.0) return t[2] + d12 * (N - x[2]);
+        return t[0] + d01 * (N - x[0]) + beta * (N - x[0]) * (N - x[1]);
     };
     for (const Cand &cd : cands) {
         s->hist_kernel = cd.kernel;
@@ -1363,25 +1373,9 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
             s->chunk_ctas = cd.ctas, s->sm_reserve = keep_res;
         s->L = tensor ? kSplitSeg : kRecurL;
     };
-    // second stage, tensor path with the lane-per-column recurrence: the warps
-    // per recurrence CTA (how the recurrence shares the SMs the tensor CTAs
-    // leave free), the caller's setting against 1, 2, 4 and 8
-    if (st == FABM_OK && (pick.kernel == FABM_HIST_TENSOR || pick.kernel == FABM_HIST_TENSOR_WIDE)) {
-        apply(pick);
-        const int keep_warps = s->rec_warps;
-        int best_w = keep_warps;
-        for (int w : {1, 2, 4, 8}) {
-            if (w == keep_warps) continue;
-            s->rec_warps = w;
-            const double ms = predict();
-            if (st != FABM_OK) break;
-            if (s->cols_warps == 0) break;  // lane-per-target layout: the width does not apply
-            if (ms < best) best = ms, best_w = w;
-        }
-        s->rec_warps = st == FABM_OK ? best_w : keep_warps;
-    }
     cudaFree(dout);
     s->timing = keep_timing;
+    s->plan_N = 0;
     if (st != FABM_OK) {
         s->hist_kernel = keep_kernel, s->chunk_ctas = keep_ctas, s->sm_reserve = keep_res;
         s->L = keep_L;
