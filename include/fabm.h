@@ -168,8 +168,8 @@ enum {
                               of blocks with 128 targets per MMA (one weight kind per
                               CTA, exact per 128-point group), the latest two or three
                               64-point segments per block with 64; automatic choice
-                              on the tensor path from N >= 257 on (the first pair of
-                              blocks with a group two groups back)                   */
+                              on the tensor path where N^2 x columns >= 2^40 (the
+                              measured crossover) and N >= 257                       */
     FABM_HIST_FP64_PERSIST = 6 /* FP64 precision, the whole solve as one persistent
                               cooperative launch: one CTA per trajectory runs its
                               recurrence with weights and the recent window of f in

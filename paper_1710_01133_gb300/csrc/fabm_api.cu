@@ -668,18 +668,24 @@ fabm_status run_batch(fabm_solver *s, int64_t B, const double *y0, const double 
         // leave SMs for the recurrence that runs beside the tensor kernel (one
         // tensor CTA fills an SM's register file), only where the column tiles
         // do not need every SM: one SM per 8 column warps, or per 12
-        // trajectories of the lane-per-target layout
+        // trajectories of the lane-per-target layout up to 16 SMs (LCR 1024 x
+        // 2^14: reserves of 40, 16 and 0 SMs predicted 25.3, 23.5, 23.1 ms)
         int reserve = s->sm_reserve;
         if (reserve < 0) {
             const int64_t want = columns ? std::clamp<int64_t>((cwarps + 7) / 8, 4, 40)
-                                         : std::min<int64_t>((B + 11) / 12, 40);
+                                         : std::min<int64_t>((B + 11) / 12, 16);
             reserve = n_ct <= 16 ? (int)want : 0;
         }
         split_chunks = std::max(1, (148 - reserve) / n_ct);
         // far history with 128 targets per MMA (pairs of blocks): requested,
-        // or automatic once there are groups to sum
-        s->wide = s->G_max >= 2 && (s->hist_kernel == FABM_HIST_TENSOR_WIDE ||
-                                    s->hist_kernel == FABM_HIST_AUTO);
+        // or automatic where the far history is large enough to pay for its
+        // extra launches: N^2 x columns >= 2^40 (measured: the 64-target
+        // tiling is faster up to 2^39, e.g. LCR 1024 x 2^14 25.4 vs 27.0 ms;
+        // the wide one from 2^41, Duffing 1024 x 2^15 57.6 vs 71.2 ms)
+        const double nplan = (double)(s->plan_N > 0 ? s->plan_N : Nmax);
+        s->wide = s->G_max >= 2 &&
+                  (s->hist_kernel == FABM_HIST_TENSOR_WIDE ||
+                   (s->hist_kernel == FABM_HIST_AUTO && nplan * nplan * (double)cols >= 0x1p40));
         far_chunks = std::max(1, (148 - reserve) / (2 * n_ct));
         if (s->wide) s->last_hk = FABM_HIST_TENSOR_WIDE;
         // a near launch (on the serial chain) takes whole SMs: as many CTAs per

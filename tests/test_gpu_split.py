@@ -158,7 +158,8 @@ def test_recurrence_layout_rejects_unknown(gpu_lib):
 
 def test_auto_history_kernel_choice(gpu_lib):
     """Split precision picks tensor cores for wide batches (64+ columns) and the
-    compensated fp32 kernel for narrow ones; the block length follows."""
+    compensated fp32 kernel for narrow ones; the block length follows; the
+    128-target far tiling where N^2 x columns reaches 2^40."""
     w = duffing_sweep(B=40, N=256)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
         assert s.last_history_kernel is None
@@ -166,10 +167,19 @@ def test_auto_history_kernel_choice(gpu_lib):
         assert s.block == 32 and s.last_history_kernel == "fp32c"
         s.solve_batch(w.y0, traj_params=w.traj_params)
         assert s.block == 64 and s.last_history_kernel == "tensor"  # N <= 256: no far group
+    # the 128-target far tiling from N^2 x columns >= 2^40 on
     w = duffing_sweep(B=40, N=257)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
         s.solve_batch(w.y0, traj_params=w.traj_params)
+        assert s.last_history_kernel == "tensor"
+        gpu_lib.fabm_set_history_kernel(s.handle, "tensor-wide")
+        s.solve_batch(w.y0, traj_params=w.traj_params)
         assert s.last_history_kernel == "tensor-wide"
+    for B, N, kernel in ((512, 32767, "tensor"), (512, 32768, "tensor-wide")):
+        w = duffing_sweep(B=B, N=N)  # 1024 columns: N^2 x 1024 just below / at 2^40
+        with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="split") as s:
+            s.solve_batch(w.y0[:B], traj_params=w.traj_params[:B])
+            assert s.last_history_kernel == kernel, (B, N)
     with gpu_lib.Solver(w.rhs, w.dim, w.alpha, w.h, w.N, w.params, precision="fp64") as s:
         with pytest.raises(gpu_lib.FabmError):
             gpu_lib.fabm_set_history_kernel(s.handle, "tensor")
