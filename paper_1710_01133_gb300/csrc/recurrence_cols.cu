@@ -168,8 +168,14 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
     const int cols = bt.cols;
     __syncwarp();
 
-    FF accP[kSub], accC[kSub], bP[kSub], bC[kSub], rcs[kSub];
+    FF accP[kSub], accC[kSub], bP[kSub], bC[kSub], rcs[kSub], axs[kSub];
     for (int a0 = 0; a0 < wsteps; a0 += kSub) {
+        // the sub-block's forcing values, loaded before the work that does not
+        // need them (rows a0 .. a0+7 < 64 of the [64][B] table: in range even
+        // past the last step), so the steps do not wait on them
+#pragma unroll
+        for (int r = 0; r < kSub; ++r)
+            axs[r] = Rhs::kForcing ? ld_ff(X + (int64_t)(a0 + r) * bt.B + bb) : aux0;
         // bases from the history of the points k < cL
 #pragma unroll
         for (int r = 0; r < kSub; ++r) {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kMaxWarps *kWarp)
 #pragma unroll
         for (int r = 0; r < kSub; ++r) {
             if (a0 + r < wsteps) {  // uniform over the warp
-                const FF ax = Rhs::kForcing ? ld_ff(X + (int64_t)(a0 + r) * bt.B + bb) : aux0;
+                const FF ax = axs[r];
                 // Taylor part of the initial data: y0, or y0 + t y'(0) for 1 < alpha < 2
                 FF T = T0;
                 if constexpr (Y1) T = ff_from_double(fma((double)(m0 + 1 + a0 + r) * kc.h, y1, y0));
