@@ -227,7 +227,7 @@ int fabm_get_recurrence_warps(const fabm_solver *s);
  * Longer probes predict better where the history only dominates late in a
  * long solve.  Candidates: for FABM_FP64 and FABM_FP64X2
  * (with its double-double kernel), the split-k CTA target of the history kernel
- * (304, 608, 1216 CTAs); for FABM_SPLIT, the two tensor-core far-history
+ * (152, 304, 608, 1216 CTAs); for FABM_SPLIT, the two tensor-core far-history
  * tilings (FABM_HIST_TENSOR_WIDE: 128 targets per MMA and per far launch;
  * FABM_HIST_TENSOR: 64) each with 0 or 16 SMs (or an automatic number) kept
  * free for the recurrence running beside it, and the compensated-fp32 kernel

@@ -1289,7 +1289,7 @@ fabm_status fabm_autotune(fabm_solver *s, int64_t B, const double *y0, const dou
         int kernel, ctas;
     };
     std::vector<Cand> cands;
-    const int ctas_opts[] = {152 * 2, 152 * 4, 152 * 8};
+    const int ctas_opts[] = {152, 152 * 2, 152 * 4, 152 * 8};
     // at most 8 candidates are reported
     if (s->precision == FABM_FP64 || s->precision == FABM_FP64X2) {
         const int k = s->precision == FABM_FP64 ? FABM_HIST_FP64 : FABM_HIST_X2;

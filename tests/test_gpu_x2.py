@@ -88,7 +88,7 @@ def test_x2_history_kernel_and_autotune(gpu_lib, parity):
             gpu_lib.fabm_set_history_kernel(s.handle, "fp64")
         gpu_lib.fabm_set_history_kernel(s.handle, "x2")
         rep = s.autotune(w.y0, n_probe=1000)
-        assert len(rep) == 3 and all(k == gpu_lib.HIST["x2"] for _, k, _ in rep)
+        assert len(rep) == 4 and all(k == gpu_lib.HIST["x2"] for _, k, _ in rep)
         got = s.solve(w.y0[0])
         B, A, D = gpu_lib.fabm_copy_weights(s.handle, 100)
     Bh, _, Ah, _, Dh, _ = gpu_lib.fabm_weights_x2(w.alpha, 99)
