@@ -69,3 +69,13 @@ def test_headline_is_the_solve_work_over_the_uninstrumented_step():
     fp64 = bench.roofline("history", STATS, "fp64", {"sm_max_mhz": 2070.0}, "lorenz-single",
                           w, 100.0)
     assert fp64["achieved"] == pytest.approx(2 * macs / 0.1 / 1e9)
+
+
+def test_dtype_names_every_history_kernel():
+    """The bench line's dtype comes from the kernel a solve ran: every history
+    kernel name of the binding maps to the arithmetic it computes in."""
+    import paper_1710_01133_gb300 as fabm
+    assert set(bench.DTYPE_OF_HISTORY) == set(fabm.HIST) - {"auto"}
+    assert bench.DTYPE_OF_HISTORY["tensor-wide"] == "bf16x3"
+    assert bench.DTYPE_OF_HISTORY["fp32c"] == "f32c"
+    assert bench.DTYPE_OF_HISTORY["x2"] == "f64x2"
