@@ -119,7 +119,7 @@ struct fabm_solver {
     int precision = FABM_FP64;
     int hist_kernel = FABM_HIST_AUTO;  // requested
     int last_hk = -1;                  // run by the last solve (fabm_last_history_kernel)
-    int chunk_ctas = 152 * 4;          // split-k CTA target of the CUDA-core history kernels
+    int chunk_ctas = 0;                // split-k CTA target of the CUDA-core history kernels (0: auto)
     int sm_reserve = -1;               // SMs kept free of tensor-history CTAs (-1: automatic)
     long long wait_cycles = 0;         // tensor kernel's wait limit (0: its default)
     bool wide = false;                 // the solve being set up uses the 128-target far history
@@ -246,6 +246,21 @@ struct fabm_solver {
 namespace {
 
 // Chunking of the far history of block c over the points k < (c-1)L.
+// Automatic split-k CTA target of the CUDA-core history kernels: more CTAs
+// (warps to hide the FP64 latency) the more column groups of 4 there are.
+// Measured with the autotuner (predicted full solves, ms for 152/304/608/1216
+// CTAs): Lorenz 2^18 FP64, 3 columns: 499/381/419/710; 4 trajectories x 2^16,
+// 12 columns: 117/103/108/122; 16 x 2^15, 48 columns: 115/114/109/99; Duffing
+// 64 x 2^14, 128 columns: 106/106/94/83; LCR 256 x 2^13, 512 columns:
+// 256/173/107/68.  FP64X2 (10 FP64 operations per term) is best at 608 for 3
+// columns.
+int auto_chunk_ctas(int hk, int64_t cols)
+{
+    if (hk == FABM_HIST_X2) return 152 * 4;
+    const int64_t col_tiles = (cols + 3) / 4;
+    return col_tiles <= 4 ? 152 * 2 : (col_tiles >= 8 ? 152 * 8 : 152 * 4);
+}
+
 void plan_chunks(int64_t k_end, int cols, int64_t max_chunks, int want_ctas, int *n_chunks,
                  int64_t *kc)
 {
@@ -518,7 +533,9 @@ fabm_status enqueue_solve(fabm_solver *s, const DevBatch &bt, const DevWeights &
             // algorithmic work: 2 sums x L targets x k_end points x cols, 2 flops each
             const double flops = 4.0 * L * (double)k_end * (double)cols;
             FABM_CUDA_TRY(cudaStreamWaitEvent(gs, s->evR[(c - lag - 1) % kEvRing], 0));
-            plan_chunks(k_end, (int)cols, max_chunks, s->chunk_ctas, &n_chunks, &kc);
+            plan_chunks(k_end, (int)cols, max_chunks,
+                        s->chunk_ctas > 0 ? s->chunk_ctas : auto_chunk_ctas(hk, cols), &n_chunks,
+                        &kc);
             if (hk == FABM_HIST_X2) {
                 double2 *xp = reinterpret_cast<double2 *>(s->part.p) + poff;
                 const DevWeightsLo wl{s->wBl.p, s->wAl.p, s->wDl.p};
