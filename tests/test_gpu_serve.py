@@ -283,3 +283,20 @@ def test_order_and_y1_checks_at_submission(gpu_lib):
             with pytest.raises(gpu_lib.FabmError) as e:
                 srv.submit("linear", 1, alpha, 1e-3, 100, [1.0], (1.0,), y1=y1)
             assert e.value.status == gpu_lib.FABM_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_orders_between_one_and_two_long_request(gpu_lib, parity, precision):
+    """A served request with 1 < alpha < 2 over 2^15 steps (1024 blocks, the far
+    history in many chunks) beside shorter ones, against the oracle over the
+    whole run: D^1.6 y = -y with y'(0) given, a decaying oscillation."""
+    N = 1 << 15
+    y0, y1, p = [1.0, -0.5], [0.3, 0.2], (1.0,)
+    with gpu_lib.Server(8 << 30, precision=precision) as srv:
+        t = srv.submit("linear", 2, 1.6, 1e-4, N, y0, p, y1=y1)
+        others = [srv.submit(*MIX[1][:5], MIX[1][5], MIX[1][6]),
+                  srv.submit(*HIGH[1][:5], HIGH[1][5], HIGH[1][6], y1=HIGH[1][7])]
+        run_to_completion(srv, [t] + others)
+        got = srv.result(t)
+    ref = oracle.solve("linear", 1.6, 1e-4, N, y0, params=p, y1=y1)
+    parity(rel_err(got, ref), 1e-12 if precision == "fp64" else 1e-6, f"linear-a1.6-N{N}")
