@@ -4,15 +4,18 @@
 // device memory they need (weights, history, output, partials) fits in the
 // server's HBM budget.  Each fabm_server_step advances every admitted slot by
 // one block of 32 steps with shared launches over tables of slots:
-//   stream G: far history of block c+1 of every slot (one launch over a list
-//             of (slot, chunk) items), then the fixed-order combine
+//   stream G: far history of block c+1 of every slot (one launch whose CTAs
+//             derive their (slot, chunk, column) items from each slot's block
+//             index, so the host builds no work list), then the fixed-order
+//             combine
 //   stream R: weights and initial values of newly admitted slots, then the
 //             recurrence of block c of every slot (one CTA per slot, the
 //             right-hand side dispatched at run time)
 // which is the two-stream schedule of a single solve, run for all slots at
 // once.  Finished slots are copied to host memory and their device memory is
 // returned to the stream-ordered pool; the freed budget admits waiting
-// requests at the next step.  A slot's chunking depends on its own block index
+// requests at the next step.  Per step the host uploads one block index per
+// slot, and the slot table only when slots were admitted or retired.  A slot's chunking depends on its own block index
 // only, so its result does not depend on the other requests in flight.
 #include <cuda_runtime.h>
 
@@ -54,14 +57,19 @@ struct SlotDev {
     unsigned long long *status;
 };
 
-struct Item {
-    int slot;
-    int chunk;     // history: chunk index; combine: number of chunks
-    int64_t c;     // block index (history/combine: target block; recurrence: block to run)
-    int64_t kc;    // history: points per chunk
-    int gbuf;      // G buffer (c % 2) the item reads or writes; -1: none
-    int pad;       // history: column of the request
-};
+// Chunking of block c's far history for one slot: depends on c only, so a
+// request's partial sums do not depend on the other requests in flight.
+__host__ __device__ inline void slot_chunks(int64_t c, int64_t *kc, int *n)
+{
+    const int64_t k_end = (c - 1) * kSL;
+    int64_t pts = (k_end + kMaxChunksSlot - 1) / kMaxChunksSlot;
+    if (pts < kMinChunkPts) pts = kMinChunkPts;
+    pts = (pts + 31) / 32 * 32;
+    *kc = pts;
+    *n = (int)((k_end + pts - 1) / pts);
+}
+
+__host__ __device__ inline int64_t slot_blocks(int64_t N) { return (N + kSL - 1) / kSL; }
 
 __device__ inline DevBatch slot_batch(const SlotDev &s)
 {
@@ -147,19 +155,20 @@ __global__ void init_slots_kernel(const SlotDev *__restrict__ slots, const int *
 // depend on which items share its CTA.
 constexpr int kWarpsPerHistCta = 4;
 
-__device__ void hist_warp_f64(const SlotDev &s, const Item &it, double *sF, double *sB, double *sA)
+__device__ void hist_warp_f64(const SlotDev &s, int64_t c, int chunk, int64_t kc, int q,
+                              double *sF, double *sB, double *sA)
 {
     using hist::kL;
     constexpr int kT = hist::f64::kTile;
-    const int a = threadIdx.x % kWarp, q = it.pad, dim = s.dim;
-    const int64_t k_end = (it.c - 1) * kSL;
-    const int64_t k0 = (int64_t)it.chunk * it.kc;
-    const int64_t k1 = k0 + it.kc < k_end ? k0 + it.kc : k_end;
+    const int a = threadIdx.x % kWarp, dim = s.dim;
+    const int64_t k_end = (c - 1) * kSL;
+    const int64_t k0 = (int64_t)chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
     double sp = 0.0, sc = 0.0;
     for (int64_t t0 = k0; t0 < k1; t0 += kT) {
         const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
         const int nk = (int)(t1 - t0);
-        const int64_t d_min = it.c * kL + 2 - t1;
+        const int64_t d_min = c * kL + 2 - t1;
         for (int i = a; i < nk + kL - 1; i += kWarp) sB[i] = s.WB[d_min + i], sA[i] = s.WA[d_min + i];
         for (int i = a; i < nk; i += kWarp) sF[i] = s.F[(t0 + i) * dim + q];
         __syncwarp();
@@ -172,20 +181,21 @@ __device__ void hist_warp_f64(const SlotDev &s, const Item &it, double *sF, doub
         }
         __syncwarp();
     }
-    double *out = static_cast<double *>(s.part) + ((int64_t)(it.chunk * 2) * kL + a) * dim + q;
+    double *out = static_cast<double *>(s.part) + ((int64_t)(chunk * 2) * kL + a) * dim + q;
     out[0] = sp;
     out[(int64_t)kL * dim] = sc;
 }
 
-__device__ void hist_warp_f32c(const SlotDev &s, const Item &it, float *sF, float *sB, float *sA)
+__device__ void hist_warp_f32c(const SlotDev &s, int64_t c, int chunk, int64_t kc, int q,
+                               float *sF, float *sB, float *sA)
 {
     using hist::kL;
     constexpr int kT = hist::f32c::kTile, kG = hist::f32c::kGroup;
     constexpr int kRF = kT / kWarp, kRW = (kT + kL + kWarp - 1) / kWarp;
-    const int a = threadIdx.x % kWarp, q = it.pad, dim = s.dim;
-    const int64_t k_end = (it.c - 1) * kSL;
-    const int64_t k0 = (int64_t)it.chunk * it.kc;
-    const int64_t k1 = k0 + it.kc < k_end ? k0 + it.kc : k_end;
+    const int a = threadIdx.x % kWarp, dim = s.dim;
+    const int64_t k_end = (c - 1) * kSL;
+    const int64_t k0 = (int64_t)chunk * kc;
+    const int64_t k1 = k0 + kc < k_end ? k0 + kc : k_end;
     float sp = 0.f, cp = 0.f, sc = 0.f, cc = 0.f;
     // the next tile's f (the recurrence's float copy) and weights are loaded
     // into registers while the current tile is summed
@@ -193,7 +203,7 @@ __device__ void hist_warp_f32c(const SlotDev &s, const Item &it, float *sF, floa
     auto fetch = [&](int64_t t0) {
         const int64_t t1 = t0 + kT < k1 ? t0 + kT : k1;
         const int nk = (int)(t1 - t0);
-        const int64_t d_min = it.c * kL + 2 - t1;
+        const int64_t d_min = c * kL + 2 - t1;
 #pragma unroll
         for (int u = 0; u < kRW; ++u) {
             const int i = a + u * kWarp;
@@ -242,48 +252,62 @@ __device__ void hist_warp_f32c(const SlotDev &s, const Item &it, float *sF, floa
         hist::f32c::kahan_add(sc, cc, gc);
         __syncwarp();
     }
-    float2 *out = static_cast<float2 *>(s.part) + ((int64_t)(it.chunk * 2) * kL + a) * dim + q;
+    float2 *out = static_cast<float2 *>(s.part) + ((int64_t)(chunk * 2) * kL + a) * dim + q;
     out[0] = make_float2(sp, -cp);
     out[(int64_t)kL * dim] = make_float2(sc, -cc);
 }
 
-// n items; CTA x takes items 4x .. 4x+3, one per warp.
+// Slots blockIdx.y, blockIdx.y + gridDim.y, ...: the slot's items are
+// (chunk, column) pairs in chunk-major order, warp w of CTA x taking item
+// 4x + w; the item list is derived here from the slot's block index cs[slot],
+// so the host uploads no work list.
 __global__ void __launch_bounds__(kWarp *kWarpsPerHistCta)
-    hist_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items, int n)
+    hist_slots_kernel(const SlotDev *__restrict__ slots, const int64_t *__restrict__ cs, int ns)
 {
     constexpr int kBytesF64 = (hist::f64::kTile + 2 * (hist::f64::kTile + hist::kL)) * 8;
     constexpr int kBytesF32 = (hist::f32c::kTile + 2 * (hist::f32c::kTile + hist::kL)) * 4;
     constexpr int kWarpBytes = kBytesF64 > kBytesF32 ? kBytesF64 : kBytesF32;
     __shared__ __align__(16) unsigned char smem[kWarpsPerHistCta][kWarpBytes];
     const int w = threadIdx.x / kWarp;
-    const int64_t g = (int64_t)blockIdx.x * kWarpsPerHistCta + w;
-    if (g >= n) return;  // uniform over the warp; warps never synchronize with each other
-    const Item it = items[g];
-    const SlotDev s = slots[it.slot];
-    if (s.hk == FABM_HIST_FP32C) {
-        float *sF = reinterpret_cast<float *>(smem[w]);
-        float *sB = sF + hist::f32c::kTile;
-        hist_warp_f32c(s, it, sF, sB, sB + hist::f32c::kTile + hist::kL);
-    } else {
-        double *sF = reinterpret_cast<double *>(smem[w]);
-        double *sB = sF + hist::f64::kTile;
-        hist_warp_f64(s, it, sF, sB, sB + hist::f64::kTile + hist::kL);
+    for (int slot = blockIdx.y; slot < ns; slot += gridDim.y) {
+        const SlotDev s = slots[slot];
+        const int64_t cn = cs[slot] + 1;  // far history of the slot's next block
+        if (cn < 2 || cn >= slot_blocks(s.N)) continue;
+        int64_t kc;
+        int n;
+        slot_chunks(cn, &kc, &n);
+        const int g = (int)blockIdx.x * kWarpsPerHistCta + w;
+        if (g >= n * s.dim) continue;  // uniform over the warp; warps never synchronize
+        const int chunk = g / s.dim, q = g % s.dim;
+        if (s.hk == FABM_HIST_FP32C) {
+            float *sF = reinterpret_cast<float *>(smem[w]);
+            float *sB = sF + hist::f32c::kTile;
+            hist_warp_f32c(s, cn, chunk, kc, q, sF, sB, sB + hist::f32c::kTile + hist::kL);
+        } else {
+            double *sF = reinterpret_cast<double *>(smem[w]);
+            double *sB = sF + hist::f64::kTile;
+            hist_warp_f64(s, cn, chunk, kc, q, sF, sB, sB + hist::f64::kTile + hist::kL);
+        }
     }
 }
 
 // One CTA per slot: G[gbuf][kind][t][col] = sum over the chunks in ascending
 // order (compensated double, or float-float rounded once to double).
-__global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+__global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const int64_t *__restrict__ cs)
 {
-    const Item it = items[blockIdx.x];
-    const SlotDev s = slots[it.slot];
+    const SlotDev s = slots[blockIdx.x];
+    const int64_t cn = cs[blockIdx.x] + 1;
+    if (cn < 2 || cn >= slot_blocks(s.N)) return;  // no far history this step (uniform)
+    int64_t kc;
+    int n_chunks;
+    slot_chunks(cn, &kc, &n_chunks);
     const int n_out = 2 * kSL * s.dim;
-    double *G = s.G + (int64_t)it.gbuf * n_out;
+    double *G = s.G + (int64_t)(cn % 2) * n_out;
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
         if (s.hk == FABM_HIST_FP32C) {
             const float2 *p = static_cast<const float2 *>(s.part);
             float hi = 0.f, lo = 0.f;
-            for (int ch = 0; ch < it.chunk; ++ch) {
+            for (int ch = 0; ch < n_chunks; ++ch) {
                 const float2 v = p[(int64_t)ch * n_out + o];
                 const float t = hi + v.x;
                 const float bb = t - hi;
@@ -298,7 +322,7 @@ __global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const It
             // in a second sum, added once at the end; chunk order fixed
             const double *p = static_cast<const double *>(s.part);
             double acc = 0.0, err = 0.0;
-            for (int ch = 0; ch < it.chunk; ++ch) {
+            for (int ch = 0; ch < n_chunks; ++ch) {
                 const double v = p[(int64_t)ch * n_out + o];
                 const double t = acc + v;
                 const double bv = t - acc;
@@ -310,25 +334,25 @@ __global__ void combine_slots_kernel(const SlotDev *__restrict__ slots, const It
     }
 }
 
-// One CTA of 4 warps per slot: block it.c of the recurrence (the split
+// One CTA of 4 warps per slot: block cs[slot] of the recurrence (the split
 // recurrence for split slots).
 __global__ void __launch_bounds__(kWarp *FABM_MAX_DIM)
-    recur_slots_kernel(const SlotDev *__restrict__ slots, const Item *__restrict__ items)
+    recur_slots_kernel(const SlotDev *__restrict__ slots, const int64_t *__restrict__ cs)
 {
     static_assert(recur_split_smem_floats<FABM_MAX_DIM, 1>() <=
                   2 * recur_smem_doubles<FABM_MAX_DIM, 1>());
     __shared__ double smem[recur_smem_doubles<FABM_MAX_DIM, 1>()];
-    const Item it = items[blockIdx.x];
-    const SlotDev s = slots[it.slot];
+    const SlotDev s = slots[blockIdx.x];
+    const int64_t c = cs[blockIdx.x];  // the block this step runs
     const DevBatch bt = slot_batch(s);
     const DevWeights w{s.WB, s.WA, s.WD, s.w_ext};
-    const double *G = it.gbuf >= 0 ? s.G + (int64_t)it.gbuf * 2 * kSL * s.dim : nullptr;
+    const double *G = c >= 2 ? s.G + (c % 2) * 2 * kSL * s.dim : nullptr;
     const bool split = s.hk == FABM_HIST_FP32C;
     slot_dispatch(s.rhs, s.dim, [&]<class R, int D>() {
         if (split)
-            recur_block_split<R, D, 1>(bt, 0, w, s.kc, it.c, G, reinterpret_cast<float *>(smem));
+            recur_block_split<R, D, 1>(bt, 0, w, s.kc, c, G, reinterpret_cast<float *>(smem));
         else
-            recur_block<R, D, 1>(bt, 0, w, s.kc, it.c, G, smem);
+            recur_block<R, D, 1>(bt, 0, w, s.kc, c, G, smem);
     });
 }
 
@@ -470,15 +494,6 @@ void slot_layout(Slot &s, int hk, int64_t w_ext)
     d.inv_g1 = 1.0 / std::tgamma(r.alpha + 1.0);
 }
 
-// Chunking of block c's far history for one slot: depends on c only.
-void slot_chunks(int64_t c, int64_t *kc, int *n)
-{
-    const int64_t k_end = (c - 1) * kSL;
-    int64_t pts = std::max<int64_t>(kMinChunkPts, (k_end + kMaxChunksSlot - 1) / kMaxChunksSlot);
-    pts = (pts + 31) / 32 * 32;
-    *kc = pts;
-    *n = (int)((k_end + pts - 1) / pts);
-}
 
 }  // namespace
 
@@ -495,13 +510,13 @@ struct fabm_server {
     int64_t next_ticket = 1;
     cudaStream_t sR = nullptr, sG = nullptr;
     cudaEvent_t evUp = nullptr;
-    SlotDev *d_slots = nullptr;  // device tables
-    Item *d_items = nullptr;
-    int *d_idx = nullptr;
+    SlotDev *d_slots = nullptr;  // device tables: the slots, uploaded when they change,
+    int64_t *d_c = nullptr;      // each slot's block index, uploaded every step,
+    int *d_idx = nullptr;        // and the indices of newly admitted slots
     SlotDev *h_slots = nullptr;  // pinned staging
-    Item *h_items = nullptr;
+    int64_t *h_c = nullptr;
     int *h_idx = nullptr;
-    int64_t item_cap = 0;
+    bool table_dirty = true;     // the slot table changed since its last upload
     int64_t steps_done = 0, launches = 0;
     std::mutex mu;
 
@@ -511,10 +526,10 @@ struct fabm_server {
             if (s.mem) cudaFreeAsync(s.mem, sR);
         if (sR) cudaStreamSynchronize(sR);
         if (d_slots) cudaFree(d_slots);
-        if (d_items) cudaFree(d_items);
+        if (d_c) cudaFree(d_c);
         if (d_idx) cudaFree(d_idx);
         if (h_slots) cudaFreeHost(h_slots);
-        if (h_items) cudaFreeHost(h_items);
+        if (h_c) cudaFreeHost(h_c);
         if (h_idx) cudaFreeHost(h_idx);
         if (evUp) cudaEventDestroy(evUp);
         if (sR) cudaStreamDestroy(sR);
@@ -575,39 +590,29 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     *n_active = ns;
     if (ns == 0) return FABM_OK;
 
-    // 2. tables: slots, new-slot indices, items (history, combine, recurrence)
-    std::vector<Item> hist, comb, rec;
+    // 2. tables: the slots (when they changed), each slot's block index (its
+    // history, combine and recurrence items follow from it on the device) and
+    // the indices of new slots
+    if (!fresh.empty()) S->table_dirty = true;
+    if (S->table_dirty) {
+        for (int i = 0; i < ns; ++i) S->h_slots[i] = S->slots[i].dev;
+        SRV_TRY(cudaMemcpyAsync(S->d_slots, S->h_slots, sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, S->sR));
+        S->table_dirty = false;
+    }
+    int max_items = 0;  // history items of the busiest slot
     for (int i = 0; i < ns; ++i) {
-        Slot &s = S->slots[i];
-        S->h_slots[i] = s.dev;
-        const int64_t cn = s.c + 1;  // far history of the next block
+        const Slot &s = S->slots[i];
+        S->h_c[i] = s.c;
+        const int64_t cn = s.c + 1;
         if (cn >= 2 && cn < s.nblk) {
             int64_t kc;
             int n;
             slot_chunks(cn, &kc, &n);
-            for (int ch = 0; ch < n; ++ch)
-                for (int q = 0; q < s.req.dim; ++q) hist.push_back({i, ch, cn, kc, (int)(cn % 2), q});
-            comb.push_back({i, n, cn, 0, (int)(cn % 2), 0});
+            max_items = std::max(max_items, n * s.req.dim);
         }
-        rec.push_back({i, 0, s.c, 0, s.c >= 2 ? (int)(s.c % 2) : -1, 0});
     }
-    const int64_t n_items = (int64_t)hist.size() + (int64_t)comb.size() + (int64_t)rec.size();
-    if (n_items > S->item_cap) {
-        if (S->d_items) cudaFree(S->d_items);
-        if (S->h_items) cudaFreeHost(S->h_items);
-        S->d_items = nullptr, S->h_items = nullptr;
-        S->item_cap = std::max<int64_t>(n_items, 2 * S->item_cap);
-        SRV_TRY(cudaMalloc(&S->d_items, sizeof(Item) * S->item_cap));
-        SRV_TRY(cudaMallocHost(&S->h_items, sizeof(Item) * S->item_cap));
-    }
-    std::copy(hist.begin(), hist.end(), S->h_items);
-    std::copy(comb.begin(), comb.end(), S->h_items + hist.size());
-    std::copy(rec.begin(), rec.end(), S->h_items + hist.size() + comb.size());
     for (size_t j = 0; j < fresh.size(); ++j) S->h_idx[j] = fresh[j];
-    Item *dH = S->d_items, *dC = dH + hist.size(), *dRc = dC + comb.size();
-
-    SRV_TRY(cudaMemcpyAsync(S->d_slots, S->h_slots, sizeof(SlotDev) * ns, cudaMemcpyHostToDevice, S->sR));
-    SRV_TRY(cudaMemcpyAsync(S->d_items, S->h_items, sizeof(Item) * n_items, cudaMemcpyHostToDevice, S->sR));
+    SRV_TRY(cudaMemcpyAsync(S->d_c, S->h_c, sizeof(int64_t) * ns, cudaMemcpyHostToDevice, S->sR));
     // 3. new slots: inputs, weights, initial values (stream R)
     if (!fresh.empty()) {
         SRV_TRY(cudaMemcpyAsync(S->d_idx, S->h_idx, sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, S->sR));
@@ -648,33 +653,31 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     SRV_TRY(cudaEventRecord(S->evUp, S->sR));
     SRV_TRY(cudaStreamWaitEvent(S->sG, S->evUp, 0));
     // 4. shared launches
-    if (!hist.empty()) {
-        const unsigned hblocks = (unsigned)((hist.size() + kWarpsPerHistCta - 1) / kWarpsPerHistCta);
-        hist_slots_kernel<<<hblocks, kWarp * kWarpsPerHistCta, 0, S->sG>>>(S->d_slots, dH,
-                                                                           (int)hist.size());
+    if (max_items > 0) {
+        const unsigned hx = (unsigned)((max_items + kWarpsPerHistCta - 1) / kWarpsPerHistCta);
+        const unsigned hy = (unsigned)std::min(ns, 65535);
+        hist_slots_kernel<<<dim3(hx, hy), kWarp * kWarpsPerHistCta, 0, S->sG>>>(S->d_slots, S->d_c, ns);
         SRV_TRY(cudaGetLastError());
-        combine_slots_kernel<<<(unsigned)comb.size(), 256, 0, S->sG>>>(S->d_slots, dC);
+        combine_slots_kernel<<<(unsigned)ns, 256, 0, S->sG>>>(S->d_slots, S->d_c);
         SRV_TRY(cudaGetLastError());
         S->launches += 2;
     }
-    recur_slots_kernel<<<(unsigned)rec.size(), kWarp * FABM_MAX_DIM, 0, S->sR>>>(S->d_slots, dRc);
+    recur_slots_kernel<<<(unsigned)ns, kWarp * FABM_MAX_DIM, 0, S->sR>>>(S->d_slots, S->d_c);
     SRV_TRY(cudaGetLastError());
     ++S->launches;
     SRV_TRY(cudaStreamSynchronize(S->sG));
     SRV_TRY(cudaStreamSynchronize(S->sR));
     ++S->steps_done;
 
-    // 5. advance; finished slots to host, memory back to the pool
-    std::vector<Slot> keep;
-    keep.reserve(ns);
+    // 5. advance; finished slots to host, memory back to the pool; the table
+    // is compacted (and uploaded at the next step) only when a slot finished
+    bool retired = false;
     for (int i = 0; i < ns; ++i) {
         Slot &s = S->slots[i];
         s.req.ckpt.reset();  // restored on the device by now
         s.c += 1;
-        if (s.c < s.nblk) {
-            keep.push_back(s);
-            continue;
-        }
+        if (s.c < s.nblk) continue;
+        retired = true;
         Result &res = S->results[s.req.ticket];
         res.y.resize((size_t)(s.req.N + 1) * s.req.dim);
         unsigned long long st = 0;
@@ -686,7 +689,12 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
         SRV_TRY(cudaFreeAsync(s.mem, S->sR));
         S->in_use -= s.bytes;
     }
-    S->slots.swap(keep);
+    if (retired) {
+        S->slots.erase(std::remove_if(S->slots.begin(), S->slots.end(),
+                                      [](const Slot &s) { return s.c >= s.nblk; }),
+                       S->slots.end());
+        S->table_dirty = true;
+    }
     *n_active = (int)S->slots.size();
     return FABM_OK;
 }
@@ -713,6 +721,8 @@ fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->evUp, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_slots, sizeof(SlotDev) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_idx, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_c, sizeof(int64_t) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_c, sizeof(int64_t) * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_slots, sizeof(SlotDev) * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_idx, sizeof(int) * max_slots);
     if (e != cudaSuccess) {
@@ -967,6 +977,7 @@ fabm_status fabm_server_cancel(fabm_server *S, int64_t ticket)
             SRV_TRY(cudaFreeAsync(S->slots[i].mem, S->sR));
             S->in_use -= S->slots[i].bytes;
             S->slots.erase(S->slots.begin() + (std::ptrdiff_t)i);
+            S->table_dirty = true;
             return FABM_OK;
         }
     return FABM_OK;  // finished: its result is dropped
