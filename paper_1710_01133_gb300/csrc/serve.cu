@@ -8,9 +8,10 @@
 //             derive their (slot, chunk, column) items from each slot's block
 //             index, so the host builds no work list), then the fixed-order
 //             combine
-//   stream R: weights and initial values of newly admitted slots, then the
-//             recurrence of block c of every slot (one CTA per slot, the
-//             right-hand side dispatched at run time)
+//   stream R: the recurrence of block c of every slot (one CTA per slot,
+//             the right-hand side dispatched at run time)
+//   stream W: weights and initial values of newly admitted slots, beside the
+//             step's launches; new slots run their first block at the next step
 // which is the two-stream schedule of a single solve, run for all slots at
 // once.  Finished slots are copied to host memory and their device memory is
 // returned to the stream-ordered pool; the freed budget admits waiting
@@ -343,7 +344,8 @@ __global__ void __launch_bounds__(kWarp *FABM_MAX_DIM)
                   2 * recur_smem_doubles<FABM_MAX_DIM, 1>());
     __shared__ double smem[recur_smem_doubles<FABM_MAX_DIM, 1>()];
     const SlotDev s = slots[blockIdx.x];
-    const int64_t c = cs[blockIdx.x];  // the block this step runs
+    const int64_t c = cs[blockIdx.x];  // the block this step runs; -1: none (new slot)
+    if (c < 0) return;
     const DevBatch bt = slot_batch(s);
     const DevWeights w{s.WB, s.WA, s.WD, s.w_ext};
     const double *G = c >= 2 ? s.G + (c % 2) * 2 * kSL * s.dim : nullptr;
@@ -420,7 +422,7 @@ struct Slot {
     size_t bytes = 0;
     void *mem = nullptr;
     SlotDev dev{};
-    bool fresh = true;
+    bool pending = false;  // admitted at this step: weights being computed, no block run yet
 };
 
 struct Result {
@@ -508,8 +510,8 @@ struct fabm_server {
     std::unordered_map<int64_t, std::pair<int64_t, int>> shapes;  // ticket -> (N, dim)
     std::vector<int64_t> finished;  // finished since the last fabm_server_finished
     int64_t next_ticket = 1;
-    cudaStream_t sR = nullptr, sG = nullptr;
-    cudaEvent_t evUp = nullptr;
+    cudaStream_t sR = nullptr, sG = nullptr, sW = nullptr;
+    cudaEvent_t evUp = nullptr, evIn = nullptr;
     SlotDev *d_slots = nullptr;  // device tables: the slots, uploaded when they change,
     int64_t *d_c = nullptr;      // each slot's block index, uploaded every step,
     int *d_idx = nullptr;        // and the indices of newly admitted slots
@@ -531,9 +533,12 @@ struct fabm_server {
         if (h_slots) cudaFreeHost(h_slots);
         if (h_c) cudaFreeHost(h_c);
         if (h_idx) cudaFreeHost(h_idx);
+        if (sW) cudaStreamSynchronize(sW);
         if (evUp) cudaEventDestroy(evUp);
+        if (evIn) cudaEventDestroy(evIn);
         if (sR) cudaStreamDestroy(sR);
         if (sG) cudaStreamDestroy(sG);
+        if (sW) cudaStreamDestroy(sW);
     }
 };
 
@@ -577,6 +582,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
         S->queue.pop_front();
         S->in_use += bytes;
         S->results[r.ticket] = {FABM_REQ_RUNNING, FABM_OK, {}};
+        s.pending = true;
         fresh.push_back((int)S->slots.size());
         S->slots.push_back(s);
     }
@@ -602,7 +608,8 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     int max_items = 0;  // history items of the busiest slot
     for (int i = 0; i < ns; ++i) {
         const Slot &s = S->slots[i];
-        S->h_c[i] = s.c;
+        S->h_c[i] = s.pending ? -1 : s.c;  // -1: the device skips the slot this step
+        if (s.pending) continue;
         const int64_t cn = s.c + 1;
         if (cn >= 2 && cn < s.nblk) {
             int64_t kc;
@@ -613,7 +620,10 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     }
     for (size_t j = 0; j < fresh.size(); ++j) S->h_idx[j] = fresh[j];
     SRV_TRY(cudaMemcpyAsync(S->d_c, S->h_c, sizeof(int64_t) * ns, cudaMemcpyHostToDevice, S->sR));
-    // 3. new slots: inputs, weights, initial values (stream R)
+    // 3. new slots: inputs (stream R), then weights and initial values on
+    // stream W beside this step's launches (they take ~0.1-0.2 ms of FP64
+    // work, which had delayed the whole step whenever requests arrived); the
+    // new slots run their first block at the next step
     if (!fresh.empty()) {
         SRV_TRY(cudaMemcpyAsync(S->d_idx, S->h_idx, sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, S->sR));
         for (int i : fresh) {
@@ -637,14 +647,16 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
                 SRV_TRY(cudaMemsetAsync(s.dev.status, 0xff, sizeof(unsigned long long), S->sR));
             }
         }
+        SRV_TRY(cudaEventRecord(S->evIn, S->sR));
+        SRV_TRY(cudaStreamWaitEvent(S->sW, S->evIn, 0));
         int64_t wmax = 0;
         for (int i : fresh) wmax = std::max(wmax, S->slots[i].dev.w_ext);
         const unsigned gx = (unsigned)std::min<int64_t>((wmax + 256) / 256, 64);
-        weights_slots_kernel<<<dim3(gx, (unsigned)fresh.size()), 256, 0, S->sR>>>(S->d_slots, S->d_idx);
+        weights_slots_kernel<<<dim3(gx, (unsigned)fresh.size()), 256, 0, S->sW>>>(S->d_slots, S->d_idx);
         SRV_TRY(cudaGetLastError());
         S->launches += 1;
         if (n_init > 0) {
-            init_slots_kernel<<<(unsigned)((n_init + 127) / 128), 128, 0, S->sR>>>(
+            init_slots_kernel<<<(unsigned)((n_init + 127) / 128), 128, 0, S->sW>>>(
                 S->d_slots, S->d_idx, n_init);
             SRV_TRY(cudaGetLastError());
             S->launches += 1;
@@ -667,6 +679,7 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     ++S->launches;
     SRV_TRY(cudaStreamSynchronize(S->sG));
     SRV_TRY(cudaStreamSynchronize(S->sR));
+    SRV_TRY(cudaStreamSynchronize(S->sW));
     ++S->steps_done;
 
     // 5. advance; finished slots to host, memory back to the pool; the table
@@ -675,6 +688,10 @@ fabm_status server_step(fabm_server *S, int *n_active, int *n_waiting)
     for (int i = 0; i < ns; ++i) {
         Slot &s = S->slots[i];
         s.req.ckpt.reset();  // restored on the device by now
+        if (s.pending) {  // weights and initial values are in place: run from the next step
+            s.pending = false;
+            continue;
+        }
         s.c += 1;
         if (s.c < s.nblk) continue;
         retired = true;
@@ -718,7 +735,9 @@ fabm_status fabm_server_create(size_t budget_bytes, int precision, int max_slots
     cudaError_t e = cudaGetDevice(&S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->sR, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->sG, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->sW, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->evUp, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->evIn, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_slots, sizeof(SlotDev) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_idx, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_c, sizeof(int64_t) * max_slots);
