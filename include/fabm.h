@@ -363,7 +363,8 @@ fabm_status fabm_kernel_busy(const fabm_solver *s, int kind, double *busy_ms);
  * fabm_server_step advances every admitted request by one block of 32 steps
  * with launches shared by all of them (the history of each request's next
  * block beside the recurrence of its current block), frees finished requests
- * and admits waiting ones.  A request's result does not depend on the other
+ * and admits waiting ones; a request's weights and initial values are computed
+ * during the step that admits it, and it runs its first block at the next.  A request's result does not depend on the other
  * requests in flight.  Precision FABM_FP64 sums the history in double,
  * FABM_SPLIT in compensated fp32 (requests have few columns, so tensor tiles
  * would be mostly padding); per-step updates and accumulators are double in
@@ -395,8 +396,9 @@ fabm_status fabm_server_submit(fabm_server *s, const fabm_request *req, int64_t 
  * FABM_EINVAL if y1 is given for alpha <= 1 or holds a non-finite value. */
 fabm_status fabm_server_submit_ic(fabm_server *s, const fabm_request *req, const double *y1,
                                   int64_t *ticket);
-/* One scheduling step (synchronous): admit, advance all admitted requests by
- * one block, retire finished ones.  Reports the requests in flight and waiting. */
+/* One scheduling step (synchronous): admit, advance all requests admitted at
+ * earlier steps by one block, retire finished ones.  Reports the requests in
+ * flight and waiting. */
 fabm_status fabm_server_step(fabm_server *s, int *n_active, int *n_waiting);
 /* State of a request: FABM_REQ_*. */
 fabm_status fabm_server_poll(fabm_server *s, int64_t ticket, int *state);
