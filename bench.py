@@ -167,6 +167,7 @@ KERNEL_SOURCES = {
     "recurrence": ["recurrence.cu", "recurrence.cuh", "rhs.cuh", "fabm_internal.cuh"],
     "recurrence_split": ["recurrence_cols.cu", "recurrence.cuh", "rhs.cuh", "ff.cuh",
                          "fabm_internal.cuh"],
+    "history_served": ["serve.cu", "history_blocks.cuh", "recurrence.cuh", "fabm_internal.cuh"],
 }
 
 
